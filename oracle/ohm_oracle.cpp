@@ -1,0 +1,513 @@
+// OHM occupancy-map oracle: TEST INFRASTRUCTURE ONLY.
+//
+// A plain, slow, sequential CPU implementation of the ray-integration path of
+// "OHM: GPU Based Occupancy Map Generation" (arxiv 2206.06079).  Only the test
+// suite, the smoke check and the CPU-baseline leg of the benchmark may load it.
+// It shares no code, header or constant with the CUDA library: it has its own
+// parameter struct, its own quantiser, its own line walk and its own storage.
+//
+// What it computes, and where each step comes from:
+//   * Map storage: space is cut into regions of 32^3 voxels kept in an ordered
+//     map keyed by region coordinates (Sec. III-A, "Memory Layout"; 3.2 m
+//     regions at 0.1 m voxels, Sec. III-B).
+//   * Quantisation: world points become fixed-point coordinates with F
+//     fractional bits per voxel, q = rint((x - origin) * 2^F / voxel_size),
+//     evaluated in IEEE double without contraction.  Rays longer than the
+//     maximum range are truncated to that range and become miss-only (Sec. IV-A
+//     truncates rays at 20 m; reading: a truncated ray carries no sample).
+//   * Line walk: the 3D voxel traversal of Amanatides & Woo cited in Sec. III-B.
+//     Each iteration steps exactly one axis: the one whose next voxel boundary
+//     is reached first along the ray.  Ties (paper silent) step z before y
+//     before x.  Times are compared exactly as integer cross products.
+//   * Occupancy: log-odds additive update l <- l + delta (Eq. 2, 3) with the
+//     clamp of Sec. II-B, applied one observation at a time.  Within one
+//     integrate call all misses are applied first and all samples second (the
+//     two-phase order of Sec. III-C).  An unknown voxel starts at l = 0.
+//   * Hit / miss counts H_i, M_i per voxel (Sec. II-D, NDT-TM permeability).
+//   * NDT-OM: per-voxel count, sum and outer-product sum of the sample positions
+//     (Sec. II-D, III-C), from which mean and covariance are the sample
+//     statistics of the points that fell in the voxel.
+//   * TSDF: projective signed distance s = d - (c - o).u along the ray,
+//     truncated to [-tau, tau], for the voxels the walk visits between ranges
+//     max(0, d - tau) and d + tau; per call the voxel keeps the running
+//     weighted average D <- (W D + sum s) / (W + count) (Sec. II-F; the paper
+//     gives no formula, this is the Curless-Levoy average it cites).
+//
+// Build: g++ -std=c++17 -O2 -ffp-contract=off -fPIC -shared (oracle/build.py).
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <tuple>
+#include <unordered_map>
+#include <vector>
+
+namespace {
+
+constexpr int kRegionDim = 32;                       // voxels per region edge
+constexpr int kRegionVoxels = kRegionDim * kRegionDim * kRegionDim;
+
+constexpr int kLayerOccupancy = 1;
+constexpr int kLayerNdt = 2;
+constexpr int kLayerTsdf = 4;
+constexpr int kLayerCounts = 8;
+
+constexpr uint8_t kFlagNoReturn = 1;
+
+}  // namespace
+
+extern "C" {
+
+// Parameters of an oracle map.  All lengths are metres.
+struct OracleParams {
+  double voxel_size;     // voxel edge length
+  double map_origin[3];  // world position of voxel (0,0,0)'s lower corner
+  int32_t frac_bits;     // F: fixed-point fraction bits per voxel
+  int32_t layers;        // bit mask of kLayer*
+  float hit;             // log-odds increment for a sample (Eq. 3)
+  float miss;            // log-odds increment for a pass-through (Eq. 3)
+  float l_min;           // lower clamp (Sec. II-B)
+  float l_max;           // upper clamp (Sec. II-B)
+  double max_range;      // truncation length (Sec. IV-A)
+  double min_range;      // TSDF: samples at or below this range are ignored
+  double tsdf_trunc;     // TSDF truncation distance tau
+  double tsdf_wmax;      // TSDF weight cap
+};
+
+}  // extern "C"
+
+namespace {
+
+// floor(a / b) for b > 0, written out so negative numerators round down.
+int64_t floor_div(int64_t a, int64_t b) {
+  int64_t q = a / b;
+  if ((a % b) != 0 && (a < 0)) q -= 1;
+  return q;
+}
+
+struct Voxel {
+  int64_t v[3];
+};
+
+struct RegionKey {
+  int64_t r[3];
+  bool operator<(const RegionKey& o) const {
+    return std::tie(r[0], r[1], r[2]) < std::tie(o.r[0], o.r[1], o.r[2]);
+  }
+};
+
+struct Region {
+  std::vector<float> occupancy;     // log-odds, NaN = unknown
+  std::vector<uint32_t> hits;       // H_i
+  std::vector<uint32_t> misses;     // M_i
+  std::vector<__int128> ndt;        // 10 per voxel: n, Sx, Sy, Sz, Sxx, Sxy, Sxz, Syy, Syz, Szz
+  std::vector<double> tsdf_d;       // running signed distance
+  std::vector<double> tsdf_w;       // running weight
+};
+
+struct Map {
+  OracleParams p;
+  double scale;  // 2^F / voxel_size
+  int64_t unit;  // 2^F
+  std::map<RegionKey, Region> regions;
+};
+
+RegionKey region_of(const Voxel& v) {
+  RegionKey k;
+  for (int a = 0; a < 3; ++a) k.r[a] = floor_div(v.v[a], kRegionDim);
+  return k;
+}
+
+// Linear index of a voxel inside its region: x fastest, then y, then z.
+int local_index(const Voxel& v) {
+  int l[3];
+  for (int a = 0; a < 3; ++a) l[a] = (int)(v.v[a] - floor_div(v.v[a], kRegionDim) * kRegionDim);
+  return l[0] + kRegionDim * (l[1] + kRegionDim * l[2]);
+}
+
+Region& region_for(Map& m, const Voxel& v) {
+  RegionKey k = region_of(v);
+  auto it = m.regions.find(k);
+  if (it != m.regions.end()) return it->second;
+  Region r;
+  const int L = m.p.layers;
+  if (L & kLayerOccupancy) r.occupancy.assign(kRegionVoxels, std::nanf(""));
+  if (L & kLayerCounts) {
+    r.hits.assign(kRegionVoxels, 0u);
+    r.misses.assign(kRegionVoxels, 0u);
+  }
+  if (L & kLayerNdt) r.ndt.assign((size_t)kRegionVoxels * 10, (__int128)0);
+  if (L & kLayerTsdf) {
+    r.tsdf_d.assign(kRegionVoxels, 0.0);
+    r.tsdf_w.assign(kRegionVoxels, 0.0);
+  }
+  return m.regions.emplace(k, std::move(r)).first->second;
+}
+
+// Fixed-point coordinate of one axis: rint((x - origin) * 2^F / voxel_size) in
+// double precision, one rounding per operation.
+int64_t quantise_axis(float x, double origin, double scale) {
+  double d = (double)x - origin;
+  double s = d * scale;
+  return (int64_t)std::llrint(s);
+}
+
+Voxel voxel_of(const int64_t q[3], int64_t unit) {
+  Voxel v;
+  for (int a = 0; a < 3; ++a) v.v[a] = floor_div(q[a], unit);
+  return v;
+}
+
+// Amanatides & Woo voxel walk from fixed-point point a to fixed-point point b.
+// Returns every voxel visited, first the voxel of a and last the voxel of b.
+// At each iteration, among the axes that still have boundaries to cross before
+// reaching b's voxel, the axis whose next boundary lies at the smallest ray
+// parameter t steps.  For axis k the next boundary is dist[k] fixed-point units
+// away along that axis and the ray advances |delta_k| units per unit t, so
+// t_k = dist[k] / |delta_k|; t_j < t_k is decided exactly by
+// dist[j] * |delta_k| < dist[k] * |delta_j|.  Equal t: z, then y, then x.
+std::vector<Voxel> walk(const int64_t a[3], const int64_t b[3], int64_t unit) {
+  Voxel v = voxel_of(a, unit);
+  const Voxel end = voxel_of(b, unit);
+  int64_t remaining[3], step[3], adelta[3], dist[3];
+  for (int k = 0; k < 3; ++k) {
+    int64_t delta = b[k] - a[k];
+    adelta[k] = delta < 0 ? -delta : delta;
+    step[k] = delta < 0 ? -1 : 1;
+    remaining[k] = end.v[k] - v.v[k];
+    if (remaining[k] < 0) remaining[k] = -remaining[k];
+    // Distance from a to the first boundary crossed along axis k.  Moving up,
+    // that is the upper face of the voxel; moving down, the lower face (a point
+    // lying exactly on the lower face leaves the voxel immediately, at t = 0).
+    if (step[k] > 0)
+      dist[k] = (v.v[k] + 1) * unit - a[k];
+    else
+      dist[k] = a[k] - v.v[k] * unit;
+  }
+  std::vector<Voxel> out;
+  out.push_back(v);
+  while (remaining[0] + remaining[1] + remaining[2] > 0) {
+    int best = -1;
+    for (int k = 2; k >= 0; --k) {  // z first so that ties keep the higher axis
+      if (remaining[k] == 0) continue;
+      if (best < 0) {
+        best = k;
+        continue;
+      }
+      __int128 tk = (__int128)dist[k] * adelta[best];
+      __int128 tb = (__int128)dist[best] * adelta[k];
+      if (tk < tb) best = k;
+    }
+    v.v[best] += step[best];
+    dist[best] += unit;
+    remaining[best] -= 1;
+    out.push_back(v);
+  }
+  return out;
+}
+
+struct PreparedRay {
+  int64_t qo[3];
+  int64_t qe[3];
+  bool has_sample;  // the endpoint is a return (a sample) inside the maximum range
+  double length;    // |qe - qo| in fixed-point units, before truncation
+};
+
+// Quantise one ray and truncate it to the maximum range (Sec. IV-A).
+// Returns false for a ray with a non-finite coordinate (skipped).
+bool prepare_ray(const Map& m, const float* o, const float* e, uint8_t flag, PreparedRay* r) {
+  for (int a = 0; a < 3; ++a)
+    if (!std::isfinite(o[a]) || !std::isfinite(e[a])) return false;
+  for (int a = 0; a < 3; ++a) {
+    r->qo[a] = quantise_axis(o[a], m.p.map_origin[a], m.scale);
+    r->qe[a] = quantise_axis(e[a], m.p.map_origin[a], m.scale);
+  }
+  r->has_sample = (flag & kFlagNoReturn) == 0;
+  double d[3];
+  for (int a = 0; a < 3; ++a) d[a] = (double)(r->qe[a] - r->qo[a]);
+  double len2 = d[0] * d[0];
+  len2 = len2 + d[1] * d[1];
+  len2 = len2 + d[2] * d[2];
+  double len = std::sqrt(len2);
+  r->length = len;
+  double rmax = m.p.max_range * m.scale;
+  if (len > rmax) {
+    double ratio = rmax / len;
+    for (int a = 0; a < 3; ++a) r->qe[a] = r->qo[a] + (int64_t)std::llrint(d[a] * ratio);
+    r->has_sample = false;
+  }
+  return true;
+}
+
+void apply_miss(Map& m, const Voxel& v) {
+  Region& r = region_for(m, v);
+  int i = local_index(v);
+  if (m.p.layers & kLayerOccupancy) {
+    float l = r.occupancy[i];
+    float l0 = std::isnan(l) ? 0.0f : l;
+    float u = l0 + m.p.miss;
+    r.occupancy[i] = std::fmin(std::fmax(u, m.p.l_min), m.p.l_max);
+  }
+  if (m.p.layers & kLayerCounts) r.misses[i] += 1u;
+}
+
+void apply_hit(Map& m, const Voxel& v, const int64_t qe[3]) {
+  Region& r = region_for(m, v);
+  int i = local_index(v);
+  if (m.p.layers & kLayerOccupancy) {
+    float l = r.occupancy[i];
+    float l0 = std::isnan(l) ? 0.0f : l;
+    float u = l0 + m.p.hit;
+    r.occupancy[i] = std::fmin(std::fmax(u, m.p.l_min), m.p.l_max);
+  }
+  if (m.p.layers & kLayerCounts) r.hits[i] += 1u;
+  if (m.p.layers & kLayerNdt) {
+    // Sample position relative to the voxel's lower corner, in fixed-point units.
+    __int128 p[3];
+    for (int a = 0; a < 3; ++a) p[a] = (__int128)(qe[a] - v.v[a] * m.unit);
+    __int128* s = &r.ndt[(size_t)i * 10];
+    s[0] += 1;
+    s[1] += p[0];
+    s[2] += p[1];
+    s[3] += p[2];
+    s[4] += p[0] * p[0];
+    s[5] += p[0] * p[1];
+    s[6] += p[0] * p[2];
+    s[7] += p[1] * p[1];
+    s[8] += p[1] * p[2];
+    s[9] += p[2] * p[2];
+  }
+}
+
+struct VoxelHash {
+  size_t operator()(const std::tuple<int64_t, int64_t, int64_t>& t) const {
+    uint64_t h = (uint64_t)std::get<0>(t) * 0x9E3779B97F4A7C15ull;
+    h ^= (uint64_t)std::get<1>(t) * 0xC2B2AE3D27D4EB4Full + (h << 6) + (h >> 2);
+    h ^= (uint64_t)std::get<2>(t) * 0x165667B19E3779F9ull + (h << 6) + (h >> 2);
+    return (size_t)h;
+  }
+};
+
+// TSDF contribution of one ray (Sec. II-F).  All geometry in metres, double.
+int64_t tsdf_ray(Map& m, const PreparedRay& r,
+                 std::unordered_map<std::tuple<int64_t, int64_t, int64_t>, std::pair<double, int64_t>, VoxelHash>& acc) {
+  const double tau_q = m.p.tsdf_trunc * m.scale;
+  const double len = r.length;
+  double d[3];
+  for (int a = 0; a < 3; ++a) d[a] = (double)(r.qe[a] - r.qo[a]);
+  // Band end points along the ray at ranges max(0, len - tau) and len + tau,
+  // quantised with the same rule as a truncated endpoint.
+  double t0 = len - tau_q;
+  if (t0 < 0.0) t0 = 0.0;
+  double t1 = len + tau_q;
+  double f0 = t0 / len, f1 = t1 / len;
+  int64_t a0[3], a1[3];
+  for (int a = 0; a < 3; ++a) {
+    a0[a] = r.qo[a] + (int64_t)std::llrint(d[a] * f0);
+    a1[a] = r.qo[a] + (int64_t)std::llrint(d[a] * f1);
+  }
+  // Range d and direction u in metres from the quantised sensor origin.
+  const double inv_scale = m.p.voxel_size / (double)m.unit;
+  const double dist_m = len * inv_scale;
+  double u[3];
+  for (int a = 0; a < 3; ++a) u[a] = d[a] / len;
+  std::vector<Voxel> vox = walk(a0, a1, m.unit);
+  for (const Voxel& v : vox) {
+    double proj = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      double centre = ((double)v.v[a] + 0.5) * m.p.voxel_size;  // relative to the map origin
+      double origin = (double)r.qo[a] * inv_scale;
+      proj += (centre - origin) * u[a];
+    }
+    double s = dist_m - proj;
+    if (s > m.p.tsdf_trunc) s = m.p.tsdf_trunc;
+    if (s < -m.p.tsdf_trunc) s = -m.p.tsdf_trunc;
+    auto& e = acc[std::make_tuple(v.v[0], v.v[1], v.v[2])];
+    e.first += s;
+    e.second += 1;
+  }
+  return (int64_t)vox.size();
+}
+
+}  // namespace
+
+extern "C" {
+
+void* oracle_create(const OracleParams* p) {
+  Map* m = new Map();
+  m->p = *p;
+  m->unit = (int64_t)1 << p->frac_bits;
+  m->scale = std::ldexp(1.0, p->frac_bits) / p->voxel_size;
+  return m;
+}
+
+void oracle_destroy(void* h) { delete static_cast<Map*>(h); }
+
+// Integrate one ray set (one scan).  origins holds n_origins points (1 = a
+// shared sensor origin, else one per ray); endpoints holds n points; flags may
+// be null.  Returns the number of voxel visits made by the occupancy walk plus
+// the TSDF band walks, or -1 on bad arguments.
+int64_t oracle_integrate(void* h, const float* origins, int64_t n_origins, const float* endpoints,
+                         const uint8_t* flags, int64_t n) {
+  Map& m = *static_cast<Map*>(h);
+  if (n < 0 || (n > 0 && (!origins || !endpoints)) || (n_origins != 1 && n_origins != n)) return -1;
+  std::vector<PreparedRay> rays;
+  rays.reserve((size_t)n);
+  for (int64_t i = 0; i < n; ++i) {
+    const float* o = origins + 3 * (n_origins == 1 ? 0 : i);
+    PreparedRay r;
+    if (prepare_ray(m, o, endpoints + 3 * i, flags ? flags[i] : 0, &r)) rays.push_back(r);
+  }
+  int64_t visits = 0;
+  const int occ_like = kLayerOccupancy | kLayerCounts | kLayerNdt;
+  if (m.p.layers & occ_like) {
+    // Phase 1: every pass-through (miss) of every ray.
+    for (const PreparedRay& r : rays) {
+      std::vector<Voxel> vox = walk(r.qo, r.qe, m.unit);
+      visits += (int64_t)vox.size();
+      size_t count = vox.size();
+      if (r.has_sample) count -= 1;  // the sample voxel gets the hit instead
+      for (size_t j = 0; j < count; ++j) apply_miss(m, vox[j]);
+    }
+    // Phase 2: every sample (hit).
+    for (const PreparedRay& r : rays) {
+      if (!r.has_sample) continue;
+      apply_hit(m, voxel_of(r.qe, m.unit), r.qe);
+    }
+  }
+  if (m.p.layers & kLayerTsdf) {
+    std::unordered_map<std::tuple<int64_t, int64_t, int64_t>, std::pair<double, int64_t>, VoxelHash> acc;
+    const double rmin = m.p.min_range * m.scale;
+    const double rmax = m.p.max_range * m.scale;
+    for (const PreparedRay& r : rays) {
+      if (!r.has_sample) continue;                          // no surface observed
+      if (!(r.length > rmin) || r.length > rmax) continue;  // outside the valid range
+      visits += tsdf_ray(m, r, acc);
+    }
+    for (const auto& kv : acc) {
+      Voxel v;
+      v.v[0] = std::get<0>(kv.first);
+      v.v[1] = std::get<1>(kv.first);
+      v.v[2] = std::get<2>(kv.first);
+      Region& reg = region_for(m, v);
+      int i = local_index(v);
+      double W = reg.tsdf_w[i], D = reg.tsdf_d[i];
+      double c = (double)kv.second.second;
+      reg.tsdf_d[i] = (W * D + kv.second.first) / (W + c);
+      double w2 = W + c;
+      reg.tsdf_w[i] = w2 < m.p.tsdf_wmax ? w2 : m.p.tsdf_wmax;
+    }
+  }
+  return visits;
+}
+
+int64_t oracle_region_count(void* h) { return (int64_t)static_cast<Map*>(h)->regions.size(); }
+
+// Dump every region in (rx, ry, rz) lexicographic order.  Any output pointer may
+// be null.  Per region: keys 3 x int64; occupancy 32768 float; hits, misses
+// 32768 uint32; ndt 32768 x 10 int64 (n, Sx, Sy, Sz, Sxx, Sxy, Sxz, Syy, Syz,
+// Szz); tsdf 32768 x 2 double (D, W).  Voxel order inside a region: x fastest.
+// Returns 0, or 1 if an NDT sum does not fit in int64.
+int oracle_export(void* h, int64_t* keys, float* occupancy, uint32_t* hits, uint32_t* misses, int64_t* ndt,
+                  double* tsdf) {
+  Map& m = *static_cast<Map*>(h);
+  int rc = 0;
+  size_t idx = 0;
+  for (const auto& kv : m.regions) {
+    const Region& r = kv.second;
+    if (keys)
+      for (int a = 0; a < 3; ++a) keys[idx * 3 + a] = kv.first.r[a];
+    if (occupancy && !r.occupancy.empty())
+      std::memcpy(occupancy + idx * kRegionVoxels, r.occupancy.data(), sizeof(float) * kRegionVoxels);
+    if (hits && !r.hits.empty()) std::memcpy(hits + idx * kRegionVoxels, r.hits.data(), sizeof(uint32_t) * kRegionVoxels);
+    if (misses && !r.misses.empty())
+      std::memcpy(misses + idx * kRegionVoxels, r.misses.data(), sizeof(uint32_t) * kRegionVoxels);
+    if (ndt && !r.ndt.empty()) {
+      for (size_t j = 0; j < (size_t)kRegionVoxels * 10; ++j) {
+        __int128 s = r.ndt[j];
+        if (s > (__int128)INT64_MAX || s < (__int128)INT64_MIN) rc = 1;
+        ndt[idx * (size_t)kRegionVoxels * 10 + j] = (int64_t)s;
+      }
+    }
+    if (tsdf && !r.tsdf_d.empty()) {
+      for (int j = 0; j < kRegionVoxels; ++j) {
+        tsdf[(idx * kRegionVoxels + j) * 2 + 0] = r.tsdf_d[j];
+        tsdf[(idx * kRegionVoxels + j) * 2 + 1] = r.tsdf_w[j];
+      }
+    }
+    ++idx;
+  }
+  return rc;
+}
+
+// Look up n world points.  occupancy: log-odds (NaN if unknown); known: 1 if
+// the voxel has been observed by the occupancy layer; ndt: n x 10 doubles
+// (count, mean xyz in metres, covariance xx xy xz yy yz zz in m^2; zeros if no
+// sample); tsdf: n x 2 (D, W).  Any output may be null.
+void oracle_query(void* h, const float* pts, int64_t n, float* occupancy, uint8_t* known, double* ndt,
+                  double* tsdf) {
+  Map& m = *static_cast<Map*>(h);
+  const double cell = m.p.voxel_size / (double)m.unit;  // metres per fixed-point unit
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t q[3];
+    for (int a = 0; a < 3; ++a) q[a] = quantise_axis(pts[3 * i + a], m.p.map_origin[a], m.scale);
+    Voxel v = voxel_of(q, m.unit);
+    auto it = m.regions.find(region_of(v));
+    const Region* r = it == m.regions.end() ? nullptr : &it->second;
+    int li = local_index(v);
+    if (occupancy) occupancy[i] = (r && !r->occupancy.empty()) ? r->occupancy[li] : std::nanf("");
+    if (known) known[i] = (r && !r->occupancy.empty() && !std::isnan(r->occupancy[li])) ? 1 : 0;
+    if (ndt) {
+      double* o = ndt + 10 * i;
+      for (int k = 0; k < 10; ++k) o[k] = 0.0;
+      if (r && !r->ndt.empty() && r->ndt[(size_t)li * 10] > 0) {
+        const __int128* s = &r->ndt[(size_t)li * 10];
+        double cnt = (double)s[0];
+        o[0] = cnt;
+        for (int a = 0; a < 3; ++a) {
+          double corner = (double)(v.v[a] * m.unit);
+          o[1 + a] = m.p.map_origin[a] + (corner + (double)s[1 + a] / cnt) * cell;
+        }
+        // Population covariance: (n * Sab - Sa * Sb) / n^2, numerator exact.
+        const int pairs[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+        for (int k = 0; k < 6; ++k) {
+          __int128 num = s[0] * s[4 + k] - s[1 + pairs[k][0]] * s[1 + pairs[k][1]];
+          o[4 + k] = (double)num / (cnt * cnt) * cell * cell;
+        }
+      }
+    }
+    if (tsdf) {
+      tsdf[2 * i] = (r && !r->tsdf_d.empty()) ? r->tsdf_d[li] : 0.0;
+      tsdf[2 * i + 1] = (r && !r->tsdf_w.empty()) ? r->tsdf_w[li] : 0.0;
+    }
+  }
+}
+
+// The walk alone, for tests: writes up to cap visited voxels (x, y, z) and
+// returns how many the walk visits.
+int64_t oracle_walk(const int64_t* a, const int64_t* b, int32_t frac_bits, int64_t* out, int64_t cap) {
+  std::vector<Voxel> vox = walk(a, b, (int64_t)1 << frac_bits);
+  for (int64_t i = 0; i < (int64_t)vox.size() && i < cap; ++i)
+    for (int k = 0; k < 3; ++k) out[3 * i + k] = vox[(size_t)i].v[k];
+  return (int64_t)vox.size();
+}
+
+// Quantisation and truncation alone, for tests.  Writes qo, qe (n x 3 int64)
+// and has_sample (n uint8); valid[i] = 0 for a skipped (non-finite) ray.
+void oracle_prepare(void* h, const float* origins, int64_t n_origins, const float* endpoints, const uint8_t* flags,
+                    int64_t n, int64_t* qo, int64_t* qe, uint8_t* has_sample, uint8_t* valid) {
+  Map& m = *static_cast<Map*>(h);
+  for (int64_t i = 0; i < n; ++i) {
+    PreparedRay r;
+    bool ok = prepare_ray(m, origins + 3 * (n_origins == 1 ? 0 : i), endpoints + 3 * i, flags ? flags[i] : 0, &r);
+    valid[i] = ok ? 1 : 0;
+    has_sample[i] = ok && r.has_sample ? 1 : 0;
+    for (int a = 0; a < 3; ++a) {
+      qo[3 * i + a] = ok ? r.qo[a] : 0;
+      qe[3 * i + a] = ok ? r.qe[a] : 0;
+    }
+  }
+}
+
+}  // extern "C"
