@@ -1,0 +1,202 @@
+/*
+ * ohm_gb.h - C ABI of the GB300 (sm_103a) ray-integration library.
+ *
+ * The library integrates ray sets -- (sensor origin, sample) pairs -- into a
+ * sparse voxel map, as in "OHM: GPU Based Occupancy Map Generation" (arxiv
+ * 2206.06079).  Space is cut into regions of 32^3 voxels found through a hash
+ * table (Sec. III-A); every ray is walked voxel by voxel (Sec. III-B, the
+ * Amanatides & Woo traversal) applying a clamped log-odds "miss" to each voxel
+ * it passes through and a "hit" to the voxel holding its sample (Eq. 2-3,
+ * Sec. II-B), and the optional layers of Sec. II-D/F and III-C ride on the same
+ * walk: per-voxel hit/miss counts, NDT-OM sample moments (mean/covariance), and
+ * a TSDF weighted average.
+ *
+ * Conventions shared by every entry point:
+ *  - Ownership: the caller owns every input and output buffer; the library owns
+ *    the map's memory (allocated on the map's device at ohm_map_create).
+ *  - Pointers: unless an entry point says otherwise, an array argument may be
+ *    device memory or host memory; the library detects which and copies host
+ *    data through its own device staging buffers.
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *    default stream).  Work is ordered on that stream.
+ *  - Errors: every entry point returns an ohm_status; on failure the message is
+ *    available from ohm_last_error() (thread-local, valid until the next call
+ *    on that thread).  No failure traps or hangs a kernel: device loops are
+ *    bounded and report through a status word in device memory.
+ *  - Fixed point: world coordinates become integers with `frac_bits` fraction
+ *    bits per voxel, q = rint((x - map_origin) * 2^frac_bits / voxel_size), in
+ *    IEEE double with one rounding per operation.  The voxel of q is
+ *    floor(q / 2^frac_bits); a point on a voxel face belongs to the upper voxel.
+ */
+#ifndef OHM_GB_H
+#define OHM_GB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ohm_map ohm_map;
+
+typedef enum {
+  OHM_OK = 0,
+  OHM_ERR_INVALID = 1,     /* bad argument; nothing was enqueued */
+  OHM_ERR_CAPACITY = 2,    /* region / NDT pool or scratch too small; map unchanged */
+  OHM_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+  OHM_ERR_PROBE_LIMIT = 4, /* hash probe bound exceeded; map unchanged */
+  OHM_ERR_UNSUPPORTED = 5  /* the map lacks a layer the call needs */
+} ohm_status;
+
+/* Layers (Sec. III-A "multiple contiguous layers for each voxel region"). */
+enum {
+  OHM_LAYER_OCCUPANCY = 1, /* float log-odds per voxel, NaN = unknown (Sec. II-B) */
+  OHM_LAYER_NDT = 2,       /* int64 sample moments per voxel (Sec. II-D, III-C) */
+  OHM_LAYER_TSDF = 4,      /* float signed distance + weight per voxel (Sec. II-F) */
+  OHM_LAYER_COUNTS = 8     /* uint32 hits H_i and misses M_i per voxel (Sec. II-D) */
+};
+
+/* Per-ray flag bits. */
+enum {
+  OHM_FLAG_NO_RETURN = 1   /* the endpoint is not a sample: the ray only clears space */
+};
+
+typedef struct {
+  double voxel_size;       /* voxel edge in metres (0.1 in Sec. IV-A) */
+  double map_origin[3];    /* world position of the lower corner of voxel (0,0,0) */
+  int32_t frac_bits;       /* fixed-point fraction bits per voxel, 8..20 (16 recommended) */
+  uint32_t layers;         /* OR of OHM_LAYER_* */
+  float hit;               /* log-odds increment for a sample, log(P(z|occ)/P(z|emp)) (Eq. 3) */
+  float miss;              /* log-odds increment for a pass-through (Eq. 3) */
+  float l_min, l_max;      /* clamp bounds (Sec. II-B) */
+  double max_range;        /* rays are truncated to this length and lose their sample (Sec. IV-A) */
+  double min_range;        /* TSDF only: samples at or below this range are ignored */
+  double tsdf_trunc;       /* TSDF truncation distance tau in metres */
+  double tsdf_wmax;        /* TSDF weight cap */
+  int64_t max_regions;     /* capacity of the region pool */
+  int64_t max_ndt_regions; /* capacity of the NDT layer pool (regions holding samples) */
+  int64_t max_rays;        /* largest ray count accepted by one integrate call */
+  int32_t segment_steps;   /* rays are split every this many voxel steps along their
+                              dominant axis (Sec. III-B ray segments); 0 = default */
+  int32_t device;          /* CUDA device ordinal */
+} ohm_map_params;
+
+/* Create a map.  Fills `*out` on success.  Allocates the region pool, the
+ * region hash table (capacity: the next power of two >= 2 * max_regions), the
+ * enabled layers and per-call scratch sized for max_rays, on `device`.
+ * Errors: OHM_ERR_INVALID for out-of-range parameters (including
+ * max_range * 2^frac_bits / voxel_size >= 2^30, which would overflow the exact
+ * integer walk), OHM_ERR_CUDA if allocation fails. */
+ohm_status ohm_map_create(const ohm_map_params* params, ohm_map** out);
+
+/* Free the map and everything it owns.  NULL is ignored.  The caller must not
+ * destroy a map while work on it is still pending on some stream. */
+void ohm_map_destroy(ohm_map* map);
+
+/* Integrate one ray set (Sec. III-B; one call is one "scan").
+ *   origins    n_origins x 3 float world positions, x y z interleaved;
+ *              n_origins is 1 (a shared sensor origin) or n.
+ *   endpoints  n x 3 float world positions of the samples.
+ *   flags      n bytes of OHM_FLAG_* or NULL (all returns).
+ * Semantics per voxel, per call: every ray passing through the voxel applies
+ * l <- clamp(l + miss) and afterwards every sample in the voxel applies
+ * l <- clamp(l + hit) (the two-phase order of Sec. III-C); an unknown voxel
+ * starts at l = 0.  The voxel holding a ray's sample receives the hit, not a
+ * miss, from that ray.  A ray longer than max_range is truncated to it and
+ * carries no sample; a ray with a non-finite coordinate, or a point outside
+ * +-2^24 voxels of the map origin, is skipped.  TSDF layer: each returned ray
+ * whose length lies in (min_range, max_range] updates the voxels the walk
+ * visits between ranges max(0, d - tau) and d + tau with the projective
+ * distance s = clamp(d - (c - o).u, -tau, tau); per call
+ * D <- (W D + sum s) / (W + count), W <- min(W + count, tsdf_wmax).
+ * All-or-nothing: regions are allocated before any voxel changes; if a pool
+ * or the hash probe bound runs out the map is left unchanged and the call
+ * returns OHM_ERR_CAPACITY / OHM_ERR_PROBE_LIMIT.  Blocks until the work on
+ * `stream` has finished and returns its status. */
+ohm_status ohm_integrate_rays(ohm_map* map, const float* origins, int64_t n_origins, const float* endpoints,
+                              const uint8_t* flags, int64_t n, void* stream);
+
+/* As ohm_integrate_rays, but returns once the work is enqueued.  Device-side
+ * failures are latched in the map and returned (and cleared) by the next
+ * ohm_map_sync; a failed call still leaves the map unchanged.  Input buffers
+ * must stay valid until the stream has passed the call. */
+ohm_status ohm_integrate_rays_async(ohm_map* map, const float* origins, int64_t n_origins, const float* endpoints,
+                                    const uint8_t* flags, int64_t n, void* stream);
+
+/* Wait for `stream` and return (then clear) the latched device status. */
+ohm_status ohm_map_sync(ohm_map* map, void* stream);
+
+/* Look up n world points (Sec. III-A: region key then voxel index).  Outputs
+ * (device memory only; any may be NULL):
+ *   occupancy  n floats, log-odds or NaN when unknown
+ *   known      n bytes, 1 if the voxel has been observed
+ *   ndt        n x 10 floats: sample count, mean x y z (metres, world),
+ *              population covariance xx xy xz yy yz zz (m^2); zeros if none
+ *   tsdf       n x 2 floats: D, W (zeros if unobserved)
+ *   counts     n x 2 uint32: hits H, misses M
+ * `points` may be host or device memory.  Returns once enqueued. */
+ohm_status ohm_query_voxels(ohm_map* map, const float* points, int64_t n, float* occupancy, uint8_t* known,
+                            float* ndt, float* tsdf, uint32_t* counts, void* stream);
+
+/* Number of regions allocated in the map (synchronises `stream`). */
+ohm_status ohm_map_region_count(ohm_map* map, int64_t* out, void* stream);
+
+/* Copy regions [first, first + count) in allocation order into device buffers
+ * (any may be NULL).  Voxel order inside a region: x fastest, then y, then z.
+ *   keys       count x 3 int32 region coordinates (voxel index >> 5)
+ *   occupancy  count x 32768 float
+ *   counts     count x 32768 x 2 uint32 (hits, misses)
+ *   ndt        count x 32768 x 10 int64 (n, Sx, Sy, Sz, Sxx, Sxy, Sxz, Syy,
+ *              Syz, Szz), positions in fixed-point units relative to the
+ *              voxel's lower corner
+ *   tsdf       count x 32768 x 2 float (D, W)
+ * Returns once enqueued. */
+ohm_status ohm_map_export(ohm_map* map, int64_t first, int64_t count, int32_t* keys, float* occupancy,
+                          uint32_t* counts, int64_t* ndt, float* tsdf, void* stream);
+
+typedef struct {
+  int64_t rays;          /* rays passed to the last integrate call */
+  int64_t segments;      /* ray segments walked by the last call */
+  int64_t visits;        /* voxel visits of the last call (occupancy walk + TSDF band walks) */
+  int64_t regions;       /* regions in the map after the call */
+  int64_t ndt_regions;   /* regions holding an NDT layer */
+  int64_t touched;       /* TSDF voxels updated by the last call */
+  int64_t total_visits;  /* voxel visits of every call since the map was created */
+  int64_t launches;      /* kernels this map has launched since it was created */
+} ohm_call_stats;
+
+/* Statistics of the last completed integrate call (synchronises `stream`). */
+ohm_status ohm_map_stats(ohm_map* map, ohm_call_stats* out, void* stream);
+
+/* Kernel stages of an integrate call, for per-stage GPU timing. */
+typedef enum {
+  OHM_STAGE_BEGIN = 0,        /* rollback snapshot */
+  OHM_STAGE_PREPARE = 1,      /* quantise, truncate, region allocation, segment table */
+  OHM_STAGE_NDT_ALLOC = 2,    /* NDT layer allocation for regions receiving samples */
+  OHM_STAGE_PREPARE_TSDF = 3, /* TSDF band end points and their regions */
+  OHM_STAGE_WALK = 4,         /* voxel walk, miss updates (Sec. III-C phase one) */
+  OHM_STAGE_HITS = 5,         /* sample updates and NDT moments (phase two) */
+  OHM_STAGE_TSDF_WALK = 6,    /* TSDF band walk */
+  OHM_STAGE_TSDF_APPLY = 7,   /* TSDF weighted average */
+  OHM_STAGE_END = 8,          /* rollback of a failed call */
+  OHM_STAGE_COUNT = 9
+} ohm_stage;
+
+/* Record CUDA events around the kernels of the stages whose bit (1 << stage)
+ * is set in `stage_mask` in every later integrate call (0 turns recording
+ * off).  Resets the accumulated times.  Events are recorded on the call's own
+ * stream, so the times are device durations of those launches. */
+ohm_status ohm_map_profile(ohm_map* map, uint32_t stage_mask);
+
+/* Wait for the recorded launches of `stage` and return their summed device
+ * time in milliseconds and their number. */
+ohm_status ohm_map_profile_read(ohm_map* map, int32_t stage, double* total_ms, int64_t* launches);
+
+/* Thread-local message describing the last failure on this thread. */
+const char* ohm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OHM_GB_H */

@@ -58,7 +58,11 @@ def _load():
         lib.oracle_region_count.restype = i64
         lib.oracle_region_count.argtypes = [vp]
         lib.oracle_export.restype = ctypes.c_int
-        lib.oracle_export.argtypes = [vp, p, p, p, p, p, p]
+        lib.oracle_export.argtypes = [vp, i64, i64, p, p, p, p, p, p]
+        lib.oracle_ndt_region_count.restype = i64
+        lib.oracle_ndt_region_count.argtypes = [vp]
+        lib.oracle_ndt_sparse.restype = i64
+        lib.oracle_ndt_sparse.argtypes = [vp, i64, p, p]
         lib.oracle_query.argtypes = [vp, p, i64, p, p, p, p]
         lib.oracle_walk.restype = i64
         lib.oracle_walk.argtypes = [p, p, ctypes.c_int32, p, i64]
@@ -127,20 +131,38 @@ class OracleMap:
     def region_count(self) -> int:
         return int(_load().oracle_region_count(self._h))
 
-    def export(self):
-        """All regions in (rx, ry, rz) order: a dict of numpy arrays."""
-        n = self.region_count()
+    def ndt_region_count(self) -> int:
+        return int(_load().oracle_ndt_region_count(self._h))
+
+    def export(self, first=0, count=None, occupancy=True, counts=True, ndt=True, tsdf=True):
+        """Regions [first, first + count) in (rx, ry, rz) order: a dict of numpy
+        arrays (a layer the map lacks, or one not asked for, is None)."""
+        total = self.region_count()
+        if count is None:
+            count = total - first
+        n = max(0, min(count, total - first))
         L = self.params["layers"]
         keys = np.zeros((n, 3), np.int64)
-        occ = np.full((n, REGION_VOXELS), np.nan, np.float32) if L & LAYER_OCCUPANCY else None
-        hits = np.zeros((n, REGION_VOXELS), np.uint32) if L & LAYER_COUNTS else None
-        misses = np.zeros((n, REGION_VOXELS), np.uint32) if L & LAYER_COUNTS else None
-        ndt = np.zeros((n, REGION_VOXELS, 10), np.int64) if L & LAYER_NDT else None
-        tsdf = np.zeros((n, REGION_VOXELS, 2), np.float64) if L & LAYER_TSDF else None
-        rc = _load().oracle_export(self._h, _ptr(keys), _ptr(occ), _ptr(hits), _ptr(misses), _ptr(ndt), _ptr(tsdf))
+        occ = np.full((n, REGION_VOXELS), np.nan, np.float32) if (L & LAYER_OCCUPANCY and occupancy) else None
+        hits = np.zeros((n, REGION_VOXELS), np.uint32) if (L & LAYER_COUNTS and counts) else None
+        misses = np.zeros((n, REGION_VOXELS), np.uint32) if (L & LAYER_COUNTS and counts) else None
+        nd = np.zeros((n, REGION_VOXELS, 10), np.int64) if (L & LAYER_NDT and ndt) else None
+        ts = np.zeros((n, REGION_VOXELS, 2), np.float64) if (L & LAYER_TSDF and tsdf) else None
+        rc = _load().oracle_export(self._h, first, n, _ptr(keys), _ptr(occ), _ptr(hits), _ptr(misses), _ptr(nd),
+                                   _ptr(ts))
         if rc:
             raise OverflowError("NDT moment sum exceeds int64")
-        return dict(keys=keys, occupancy=occ, hits=hits, misses=misses, ndt=ndt, tsdf=tsdf)
+        return dict(keys=keys, occupancy=occ, hits=hits, misses=misses, ndt=nd, tsdf=ts)
+
+    def ndt_sparse(self):
+        """(voxels (k, 3) int64, moments (k, 10) int64) of every voxel holding
+        a sample: n, Sx, Sy, Sz, Sxx, Sxy, Sxz, Syy, Syz, Szz."""
+        lib = _load()
+        k = int(lib.oracle_ndt_sparse(self._h, 0, None, None))
+        vox = np.zeros((k, 3), np.int64)
+        mom = np.zeros((k, 10), np.int64)
+        lib.oracle_ndt_sparse(self._h, k, _ptr(vox), _ptr(mom))
+        return vox, mom
 
     def query(self, points):
         pts = np.ascontiguousarray(points, dtype=np.float32).reshape(-1, 3)

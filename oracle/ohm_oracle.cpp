@@ -137,7 +137,6 @@ Region& region_for(Map& m, const Voxel& v) {
     r.hits.assign(kRegionVoxels, 0u);
     r.misses.assign(kRegionVoxels, 0u);
   }
-  if (L & kLayerNdt) r.ndt.assign((size_t)kRegionVoxels * 10, (__int128)0);
   if (L & kLayerTsdf) {
     r.tsdf_d.assign(kRegionVoxels, 0.0);
     r.tsdf_w.assign(kRegionVoxels, 0.0);
@@ -215,11 +214,17 @@ struct PreparedRay {
 };
 
 // Quantise one ray and truncate it to the maximum range (Sec. IV-A).
-// Returns false for a ray with a non-finite coordinate (skipped).
+// Returns false for a ray that is skipped: a non-finite coordinate, or a point
+// outside the addressable extent (|voxel index| < 2^24 per axis after
+// truncation; before it, |fixed-point value| < 2^52 so rounding is exact).
 bool prepare_ray(const Map& m, const float* o, const float* e, uint8_t flag, PreparedRay* r) {
   for (int a = 0; a < 3; ++a)
     if (!std::isfinite(o[a]) || !std::isfinite(e[a])) return false;
+  const double fp_limit = std::ldexp(1.0, 52);
   for (int a = 0; a < 3; ++a) {
+    double so = ((double)o[a] - m.p.map_origin[a]) * m.scale;
+    double se = ((double)e[a] - m.p.map_origin[a]) * m.scale;
+    if (!(std::fabs(so) < fp_limit) || !(std::fabs(se) < fp_limit)) return false;
     r->qo[a] = quantise_axis(o[a], m.p.map_origin[a], m.scale);
     r->qe[a] = quantise_axis(e[a], m.p.map_origin[a], m.scale);
   }
@@ -236,6 +241,11 @@ bool prepare_ray(const Map& m, const float* o, const float* e, uint8_t flag, Pre
     double ratio = rmax / len;
     for (int a = 0; a < 3; ++a) r->qe[a] = r->qo[a] + (int64_t)std::llrint(d[a] * ratio);
     r->has_sample = false;
+  }
+  const int64_t vlimit = (int64_t)1 << 24;
+  for (int a = 0; a < 3; ++a) {
+    int64_t vo = floor_div(r->qo[a], m.unit), ve = floor_div(r->qe[a], m.unit);
+    if (vo <= -vlimit || vo >= vlimit || ve <= -vlimit || ve >= vlimit) return false;
   }
   return true;
 }
@@ -263,6 +273,7 @@ void apply_hit(Map& m, const Voxel& v, const int64_t qe[3]) {
   }
   if (m.p.layers & kLayerCounts) r.hits[i] += 1u;
   if (m.p.layers & kLayerNdt) {
+    if (r.ndt.empty()) r.ndt.assign((size_t)kRegionVoxels * 10, (__int128)0);  // first sample in this region
     // Sample position relative to the voxel's lower corner, in fixed-point units.
     __int128 p[3];
     for (int a = 0; a < 3; ++a) p[a] = (__int128)(qe[a] - v.v[a] * m.unit);
@@ -404,17 +415,21 @@ int64_t oracle_integrate(void* h, const float* origins, int64_t n_origins, const
 
 int64_t oracle_region_count(void* h) { return (int64_t)static_cast<Map*>(h)->regions.size(); }
 
-// Dump every region in (rx, ry, rz) lexicographic order.  Any output pointer may
-// be null.  Per region: keys 3 x int64; occupancy 32768 float; hits, misses
-// 32768 uint32; ndt 32768 x 10 int64 (n, Sx, Sy, Sz, Sxx, Sxy, Sxz, Syy, Syz,
-// Szz); tsdf 32768 x 2 double (D, W).  Voxel order inside a region: x fastest.
-// Returns 0, or 1 if an NDT sum does not fit in int64.
-int oracle_export(void* h, int64_t* keys, float* occupancy, uint32_t* hits, uint32_t* misses, int64_t* ndt,
-                  double* tsdf) {
+// Dump regions [first, first + count) of the (rx, ry, rz) lexicographic order.
+// Any output pointer may be null.  Per region: keys 3 x int64; occupancy 32768
+// float; hits, misses 32768 uint32; ndt 32768 x 10 int64 (n, Sx, Sy, Sz, Sxx,
+// Sxy, Sxz, Syy, Syz, Szz; zeros for a region without samples); tsdf 32768 x 2
+// double (D, W).  Voxel order inside a region: x fastest.  Returns 0, or 1 if an
+// NDT sum does not fit in int64.
+int oracle_export(void* h, int64_t first, int64_t count, int64_t* keys, float* occupancy, uint32_t* hits,
+                  uint32_t* misses, int64_t* ndt, double* tsdf) {
   Map& m = *static_cast<Map*>(h);
   int rc = 0;
+  int64_t pos = 0;
   size_t idx = 0;
   for (const auto& kv : m.regions) {
+    if (pos++ < first) continue;
+    if ((int64_t)idx >= count) break;
     const Region& r = kv.second;
     if (keys)
       for (int a = 0; a < 3; ++a) keys[idx * 3 + a] = kv.first.r[a];
@@ -423,11 +438,16 @@ int oracle_export(void* h, int64_t* keys, float* occupancy, uint32_t* hits, uint
     if (hits && !r.hits.empty()) std::memcpy(hits + idx * kRegionVoxels, r.hits.data(), sizeof(uint32_t) * kRegionVoxels);
     if (misses && !r.misses.empty())
       std::memcpy(misses + idx * kRegionVoxels, r.misses.data(), sizeof(uint32_t) * kRegionVoxels);
-    if (ndt && !r.ndt.empty()) {
-      for (size_t j = 0; j < (size_t)kRegionVoxels * 10; ++j) {
-        __int128 s = r.ndt[j];
-        if (s > (__int128)INT64_MAX || s < (__int128)INT64_MIN) rc = 1;
-        ndt[idx * (size_t)kRegionVoxels * 10 + j] = (int64_t)s;
+    if (ndt) {
+      int64_t* dst = ndt + idx * (size_t)kRegionVoxels * 10;
+      if (r.ndt.empty()) {
+        std::memset(dst, 0, sizeof(int64_t) * (size_t)kRegionVoxels * 10);
+      } else {
+        for (size_t j = 0; j < (size_t)kRegionVoxels * 10; ++j) {
+          __int128 s = r.ndt[j];
+          if (s > (__int128)INT64_MAX || s < (__int128)INT64_MIN) rc = 1;
+          dst[j] = (int64_t)s;
+        }
       }
     }
     if (tsdf && !r.tsdf_d.empty()) {
@@ -439,6 +459,36 @@ int oracle_export(void* h, int64_t* keys, float* occupancy, uint32_t* hits, uint
     ++idx;
   }
   return rc;
+}
+
+// Every voxel holding at least one sample, in (region order, x-fastest voxel
+// order): voxel coordinates (cap x 3 int64) and its 10 moments (cap x 10
+// int64).  Writes at most cap entries; returns how many exist.
+int64_t oracle_ndt_sparse(void* h, int64_t cap, int64_t* voxels, int64_t* moments) {
+  Map& m = *static_cast<Map*>(h);
+  int64_t c = 0;
+  for (const auto& kv : m.regions) {
+    const Region& r = kv.second;
+    if (r.ndt.empty()) continue;
+    for (int li = 0; li < kRegionVoxels; ++li) {
+      const __int128* s = &r.ndt[(size_t)li * 10];
+      if (s[0] == 0) continue;
+      if (c < cap) {
+        const int l[3] = {li % kRegionDim, (li / kRegionDim) % kRegionDim, li / (kRegionDim * kRegionDim)};
+        for (int a = 0; a < 3; ++a) voxels[3 * c + a] = kv.first.r[a] * kRegionDim + l[a];
+        for (int k = 0; k < 10; ++k) moments[10 * c + k] = (int64_t)s[k];
+      }
+      ++c;
+    }
+  }
+  return c;
+}
+
+// Number of regions holding NDT samples.
+int64_t oracle_ndt_region_count(void* h) {
+  int64_t c = 0;
+  for (const auto& kv : static_cast<Map*>(h)->regions) c += kv.second.ndt.empty() ? 0 : 1;
+  return c;
 }
 
 // Look up n world points.  occupancy: log-odds (NaN if unknown); known: 1 if

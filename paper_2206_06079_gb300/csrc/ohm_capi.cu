@@ -1,0 +1,424 @@
+// C ABI of the ray-integration library: map lifetime, argument checks, host
+// staging and status reporting.  Declared in include/ohm_gb.h.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "ohm_host.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+ohm_status fail(ohm_status code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+ohm_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(OHM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// Makes the map's device current for the lifetime of the guard.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+bool is_device_pointer(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+cudaError_t alloc(T** p, size_t count, int fill) {
+  *p = nullptr;
+  if (count == 0) return cudaSuccess;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+  if (e != cudaSuccess) return e;
+  return cudaMemset(*p, fill, count * sizeof(T));
+}
+
+long long next_pow2(long long x) {
+  long long p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+void free_map(ohm_map* m) {
+  if (!m) return;
+  ohm::DeviceMap& d = m->d;
+  void* ptrs[] = {d.hkeys, d.hslots, d.region_count, d.region_coords, d.occ, d.counts, d.ndt_slot, d.ndt_count,
+                  d.ndt, d.tsdf, d.tsdf_cnt, d.tsdf_sum, d.status, d.calls, d.rays, d.trays, d.segs, d.touched,
+                  m->stage_origins, m->stage_endpoints, m->stage_flags};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (m->h_status) cudaFreeHost(m->h_status);
+  if (m->h_calls) cudaFreeHost(m->h_calls);
+  if (m->h_count) cudaFreeHost(m->h_count);
+  for (auto& pe : m->pending) {
+    cudaEventDestroy(pe.second.first);
+    cudaEventDestroy(pe.second.second);
+  }
+  for (cudaEvent_t ev : m->event_pool) cudaEventDestroy(ev);
+  delete m;
+}
+
+ohm_status status_from_bits(int bits) {
+  if (bits == 0) return OHM_OK;
+  std::string msg = "integrate failed, map unchanged:";
+  if (bits & ohm::kStatusCapacity) msg += " region or NDT pool full;";
+  if (bits & ohm::kStatusProbe) msg += " hash probe limit exceeded;";
+  if (bits & ohm::kStatusScratch) msg += " internal scratch overflow;";
+  if (bits & ohm::kStatusMissing) msg += " internal region lookup failure;";
+  if (bits & ohm::kStatusCasLimit) msg += " internal CAS retry limit;";
+  g_last_error = msg;
+  if (bits & ohm::kStatusCapacity) return OHM_ERR_CAPACITY;
+  if (bits & ohm::kStatusProbe) return OHM_ERR_PROBE_LIMIT;
+  return OHM_ERR_CUDA;
+}
+
+ohm_status enqueue_integrate(ohm_map* map, const float* origins, int64_t n_origins, const float* endpoints,
+                             const uint8_t* flags, int64_t n, cudaStream_t stream) {
+  if (!map) return fail(OHM_ERR_INVALID, "integrate: map is NULL");
+  if (n < 0 || n > map->p.max_rays) return fail(OHM_ERR_INVALID, "integrate: n outside [0, max_rays]");
+  if (n == 0) return OHM_OK;
+  if (!origins || !endpoints) return fail(OHM_ERR_INVALID, "integrate: origins/endpoints are NULL");
+  if (n_origins != 1 && n_origins != n) return fail(OHM_ERR_INVALID, "integrate: n_origins must be 1 or n");
+  ohm::CallArgs a;
+  a.n = n;
+  a.n_origins = n_origins;
+  a.origins = origins;
+  a.endpoints = endpoints;
+  a.flags = flags;
+  cudaError_t e;
+  if (!is_device_pointer(origins)) {
+    e = cudaMemcpyAsync(map->stage_origins, origins, sizeof(float) * 3 * n_origins, cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "integrate: copy origins");
+    a.origins = map->stage_origins;
+  }
+  if (!is_device_pointer(endpoints)) {
+    e = cudaMemcpyAsync(map->stage_endpoints, endpoints, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "integrate: copy endpoints");
+    a.endpoints = map->stage_endpoints;
+  }
+  if (flags && !is_device_pointer(flags)) {
+    e = cudaMemcpyAsync(map->stage_flags, flags, (size_t)n, cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "integrate: copy flags");
+    a.flags = map->stage_flags;
+  }
+  e = ohm::launch_integrate(map, a, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "integrate: launch");
+  return OHM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ohm_last_error(void) { return g_last_error.c_str(); }
+
+ohm_status ohm_map_create(const ohm_map_params* params, ohm_map** out) {
+  if (!params || !out) return fail(OHM_ERR_INVALID, "create: NULL argument");
+  *out = nullptr;
+  ohm_map_params p = *params;
+  if (p.segment_steps == 0) p.segment_steps = 64;
+  if (!(p.voxel_size > 0.0) || !std::isfinite(p.voxel_size)) return fail(OHM_ERR_INVALID, "create: voxel_size must be > 0");
+  if (p.frac_bits < 8 || p.frac_bits > 20) return fail(OHM_ERR_INVALID, "create: frac_bits must be in [8, 20]");
+  const uint32_t all = OHM_LAYER_OCCUPANCY | OHM_LAYER_NDT | OHM_LAYER_TSDF | OHM_LAYER_COUNTS;
+  if (p.layers == 0 || (p.layers & ~all)) return fail(OHM_ERR_INVALID, "create: bad layer mask");
+  if (!(p.l_min <= p.l_max)) return fail(OHM_ERR_INVALID, "create: l_min > l_max");
+  if (!(p.max_range > 0.0)) return fail(OHM_ERR_INVALID, "create: max_range must be > 0");
+  if (!(p.min_range >= 0.0)) return fail(OHM_ERR_INVALID, "create: min_range must be >= 0");
+  if (!(p.tsdf_trunc >= 0.0) || !(p.tsdf_wmax > 0.0)) return fail(OHM_ERR_INVALID, "create: bad TSDF parameters");
+  if (p.max_regions < 1 || p.max_regions > (1LL << 26)) return fail(OHM_ERR_INVALID, "create: max_regions out of range");
+  if (p.max_rays < 1 || p.max_rays > (1LL << 30)) return fail(OHM_ERR_INVALID, "create: max_rays out of range");
+  if (p.segment_steps < 1) return fail(OHM_ERR_INVALID, "create: segment_steps must be >= 1");
+  if ((p.layers & OHM_LAYER_NDT) && (p.max_ndt_regions < 1 || p.max_ndt_regions > p.max_regions))
+    return fail(OHM_ERR_INVALID, "create: max_ndt_regions must be in [1, max_regions]");
+  for (int k = 0; k < 3; ++k)
+    if (!std::isfinite(p.map_origin[k])) return fail(OHM_ERR_INVALID, "create: map_origin not finite");
+  const double scale = std::ldexp(1.0, p.frac_bits) / p.voxel_size;
+  if ((p.max_range + p.tsdf_trunc) * scale >= std::ldexp(1.0, 30))
+    return fail(OHM_ERR_INVALID, "create: (max_range + tsdf_trunc) * 2^frac_bits / voxel_size must be < 2^30");
+
+  DeviceGuard guard(p.device);
+  if (!guard.ok) return fail(OHM_ERR_CUDA, "create: cannot select device");
+  ohm_map* m = new ohm_map();
+  m->p = p;
+  m->device = p.device;
+  ohm::DeviceMap& d = m->d;
+  const long long R = p.max_regions;
+  const long long V = ohm::kRegionVoxels;
+  const long long H = next_pow2(2 * R > 1024 ? 2 * R : 1024);
+  m->hash_capacity = H;
+  d.hmask = (uint32_t)(H - 1);
+  d.max_probe = (int32_t)(H < 4096 ? H : 4096);
+  d.max_regions = (int32_t)R;
+  d.max_ndt = (p.layers & OHM_LAYER_NDT) ? (int32_t)p.max_ndt_regions : 0;
+  const long long vox_steps = (long long)std::ceil(p.max_range / p.voxel_size) + 2;
+  d.max_segs = p.max_rays * (vox_steps / p.segment_steps + 1);
+  const long long band = (long long)std::ceil(2.0 * p.tsdf_trunc / p.voxel_size) + 2;
+  d.max_touched = (p.layers & OHM_LAYER_TSDF) ? p.max_rays * (1 + 3 * band) : 0;
+  if (d.max_touched > R * V) d.max_touched = R * V;
+
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t r) {
+    if (e == cudaSuccess && r != cudaSuccess) e = r;
+  };
+  chk(alloc(&d.hkeys, H, 0xFF));
+  chk(alloc(&d.hslots, H, 0xFF));
+  chk(alloc(&d.region_count, 1, 0));
+  chk(alloc(&d.ndt_count, 1, 0));
+  chk(alloc(&d.status, 1, 0));
+  chk(alloc(&d.calls, 1, 0));
+  chk(alloc(&d.region_coords, 3 * R, 0));
+  chk(alloc(&d.ndt_slot, R, 0xFF));
+  if (p.layers & OHM_LAYER_OCCUPANCY) chk(alloc(&d.occ, R * V, 0xFF));  // all-ones float = NaN = unknown
+  if (p.layers & OHM_LAYER_COUNTS) chk(alloc(&d.counts, R * V, 0));
+  if (p.layers & OHM_LAYER_NDT) chk(alloc(&d.ndt, (long long)d.max_ndt * 10 * V, 0));
+  if (p.layers & OHM_LAYER_TSDF) {
+    chk(alloc(&d.tsdf, R * V, 0));
+    chk(alloc(&d.tsdf_cnt, R * V, 0));
+    chk(alloc(&d.tsdf_sum, R * V, 0));
+    chk(alloc(&d.trays, p.max_rays, 0));
+    chk(alloc(&d.touched, d.max_touched, 0));
+  }
+  chk(alloc(&d.rays, p.max_rays, 0));
+  chk(alloc(&d.segs, d.max_segs, 0));
+  chk(alloc(&m->stage_origins, 3 * p.max_rays, 0));
+  chk(alloc(&m->stage_endpoints, 3 * p.max_rays, 0));
+  chk(alloc(&m->stage_flags, p.max_rays, 0));
+  if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&m->h_status), sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&m->h_calls), sizeof(ohm::CallCounters));
+  if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&m->h_count), 2 * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    free_map(m);
+    return cuda_fail(e, "create: allocation");
+  }
+  for (int k = 0; k < 3; ++k) d.origin[k] = p.map_origin[k];
+  d.scale = scale;
+  d.rmax_q = p.max_range * scale;
+  d.rmin_q = p.min_range * scale;
+  d.tau_q = p.tsdf_trunc * scale;
+  d.voxel_size = p.voxel_size;
+  d.frac_bits = p.frac_bits;
+  d.layers = p.layers;
+  d.seg_steps = p.segment_steps;
+  d.hit = p.hit;
+  d.miss = p.miss;
+  d.l_min = p.l_min;
+  d.l_max = p.l_max;
+  d.tau_m = (float)p.tsdf_trunc;
+  d.wmax = (float)p.tsdf_wmax;
+  cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, p.device);
+  m->walk_blocks = m->num_sms * ohm::walk_blocks_per_sm();
+  *out = m;
+  return OHM_OK;
+}
+
+void ohm_map_destroy(ohm_map* map) {
+  if (!map) return;
+  DeviceGuard guard(map->device);
+  cudaDeviceSynchronize();
+  free_map(map);
+}
+
+ohm_status ohm_integrate_rays_async(ohm_map* map, const float* origins, int64_t n_origins, const float* endpoints,
+                                    const uint8_t* flags, int64_t n, void* stream) {
+  if (!map) return fail(OHM_ERR_INVALID, "integrate: map is NULL");
+  DeviceGuard guard(map->device);
+  return enqueue_integrate(map, origins, n_origins, endpoints, flags, n, static_cast<cudaStream_t>(stream));
+}
+
+ohm_status ohm_map_sync(ohm_map* map, void* stream) {
+  if (!map) return fail(OHM_ERR_INVALID, "sync: map is NULL");
+  DeviceGuard guard(map->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(map->h_status, map->d.status, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "sync");
+  const int bits = *map->h_status;
+  if (bits != 0) {
+    e = cudaMemsetAsync(map->d.status, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "sync: clear status");
+  }
+  return status_from_bits(bits);
+}
+
+ohm_status ohm_integrate_rays(ohm_map* map, const float* origins, int64_t n_origins, const float* endpoints,
+                              const uint8_t* flags, int64_t n, void* stream) {
+  ohm_status st = ohm_integrate_rays_async(map, origins, n_origins, endpoints, flags, n, stream);
+  if (st != OHM_OK) return st;
+  return ohm_map_sync(map, stream);
+}
+
+ohm_status ohm_query_voxels(ohm_map* map, const float* points, int64_t n, float* occupancy, uint8_t* known,
+                            float* ndt, float* tsdf, uint32_t* counts, void* stream) {
+  if (!map) return fail(OHM_ERR_INVALID, "query: map is NULL");
+  if (n < 0) return fail(OHM_ERR_INVALID, "query: n < 0");
+  if (n == 0) return OHM_OK;
+  if (!points) return fail(OHM_ERR_INVALID, "query: points is NULL");
+  void* outs[] = {occupancy, known, ndt, tsdf, counts};
+  for (void* o : outs)
+    if (o && !is_device_pointer(o)) return fail(OHM_ERR_INVALID, "query: outputs must be device memory");
+  if (ndt && !(map->p.layers & OHM_LAYER_NDT)) return fail(OHM_ERR_UNSUPPORTED, "query: map has no NDT layer");
+  if (tsdf && !(map->p.layers & OHM_LAYER_TSDF)) return fail(OHM_ERR_UNSUPPORTED, "query: map has no TSDF layer");
+  DeviceGuard guard(map->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const float* pts = points;
+  float* staged = nullptr;
+  cudaError_t e;
+  if (!is_device_pointer(points)) {
+    e = cudaMallocAsync(reinterpret_cast<void**>(&staged), sizeof(float) * 3 * n, s);
+    if (e != cudaSuccess) return cuda_fail(e, "query: staging");
+    e = cudaMemcpyAsync(staged, points, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "query: copy points");
+    pts = staged;
+  }
+  e = ohm::launch_query(map, pts, n, occupancy, known, ndt, tsdf, counts, s);
+  if (staged) cudaFreeAsync(staged, s);
+  if (e != cudaSuccess) return cuda_fail(e, "query: launch");
+  return OHM_OK;
+}
+
+ohm_status ohm_map_region_count(ohm_map* map, int64_t* out, void* stream) {
+  if (!map || !out) return fail(OHM_ERR_INVALID, "region_count: NULL argument");
+  DeviceGuard guard(map->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(map->h_count, map->d.region_count, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "region_count");
+  const long long c = *map->h_count;
+  *out = c < map->p.max_regions ? c : map->p.max_regions;
+  return OHM_OK;
+}
+
+ohm_status ohm_map_export(ohm_map* map, int64_t first, int64_t count, int32_t* keys, float* occupancy,
+                          uint32_t* counts, int64_t* ndt, float* tsdf, void* stream) {
+  if (!map) return fail(OHM_ERR_INVALID, "export: map is NULL");
+  if (first < 0 || count < 0 || first + count > map->p.max_regions)
+    return fail(OHM_ERR_INVALID, "export: region range outside the pool");
+  void* outs[] = {keys, occupancy, counts, ndt, tsdf};
+  for (void* o : outs)
+    if (o && !is_device_pointer(o)) return fail(OHM_ERR_INVALID, "export: outputs must be device memory");
+  if (occupancy && !(map->p.layers & OHM_LAYER_OCCUPANCY)) return fail(OHM_ERR_UNSUPPORTED, "export: no occupancy layer");
+  if (counts && !(map->p.layers & OHM_LAYER_COUNTS)) return fail(OHM_ERR_UNSUPPORTED, "export: no counts layer");
+  if (ndt && !(map->p.layers & OHM_LAYER_NDT)) return fail(OHM_ERR_UNSUPPORTED, "export: no NDT layer");
+  if (tsdf && !(map->p.layers & OHM_LAYER_TSDF)) return fail(OHM_ERR_UNSUPPORTED, "export: no TSDF layer");
+  DeviceGuard guard(map->device);
+  cudaError_t e = ohm::launch_export(map, first, count, keys, occupancy, counts, reinterpret_cast<long long*>(ndt),
+                                     tsdf, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "export: launch");
+  return OHM_OK;
+}
+
+ohm_status ohm_map_stats(ohm_map* map, ohm_call_stats* out, void* stream) {
+  if (!map || !out) return fail(OHM_ERR_INVALID, "stats: NULL argument");
+  DeviceGuard guard(map->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(map->h_calls, map->d.calls, sizeof(ohm::CallCounters), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(map->h_count, map->d.region_count, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(map->h_count + 1, map->d.ndt_count, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "stats");
+  out->rays = (int64_t)map->h_calls->rays;
+  out->segments = (int64_t)map->h_calls->segments;
+  out->visits = (int64_t)map->h_calls->visits;
+  out->touched = (int64_t)map->h_calls->touched;
+  out->regions = map->h_count[0] < map->p.max_regions ? map->h_count[0] : map->p.max_regions;
+  out->ndt_regions = map->h_count[1];
+  out->total_visits = (int64_t)map->h_calls->total_visits;
+  out->launches = map->launches;
+  return OHM_OK;
+}
+
+ohm_status ohm_map_profile(ohm_map* map, uint32_t stage_mask) {
+  if (!map) return fail(OHM_ERR_INVALID, "profile: map is NULL");
+  if (stage_mask >> OHM_STAGE_COUNT) return fail(OHM_ERR_INVALID, "profile: unknown stage bit");
+  DeviceGuard guard(map->device);
+  for (auto& pe : map->pending) {
+    cudaEventSynchronize(pe.second.second);
+    map->event_pool.push_back(pe.second.first);
+    map->event_pool.push_back(pe.second.second);
+  }
+  map->pending.clear();
+  map->profile_mask = stage_mask;
+  for (int k = 0; k < OHM_STAGE_COUNT; ++k) {
+    map->stage_ms[k] = 0.0;
+    map->stage_launches[k] = 0;
+  }
+  return OHM_OK;
+}
+
+ohm_status ohm_map_profile_read(ohm_map* map, int32_t stage, double* total_ms, int64_t* launches) {
+  if (!map || !total_ms || !launches) return fail(OHM_ERR_INVALID, "profile_read: NULL argument");
+  if (stage < 0 || stage >= OHM_STAGE_COUNT) return fail(OHM_ERR_INVALID, "profile_read: unknown stage");
+  DeviceGuard guard(map->device);
+  for (auto& pe : map->pending) {
+    cudaError_t e = cudaEventSynchronize(pe.second.second);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, pe.second.first, pe.second.second);
+    if (e != cudaSuccess) return cuda_fail(e, "profile_read");
+    map->stage_ms[pe.first] += ms;
+    map->stage_launches[pe.first] += 1;
+    map->event_pool.push_back(pe.second.first);
+    map->event_pool.push_back(pe.second.second);
+  }
+  map->pending.clear();
+  *total_ms = map->stage_ms[stage];
+  *launches = map->stage_launches[stage];
+  return OHM_OK;
+}
+
+}  // extern "C"
+
+namespace ohm {
+
+static cudaEvent_t pooled_event(ohm_map* map) {
+  if (!map->event_pool.empty()) {
+    cudaEvent_t ev = map->event_pool.back();
+    map->event_pool.pop_back();
+    return ev;
+  }
+  cudaEvent_t ev = nullptr;
+  cudaEventCreate(&ev);
+  return ev;
+}
+
+void stage_begin(ohm_map* map, int stage, cudaStream_t stream, cudaEvent_t* ev) {
+  *ev = nullptr;
+  if (!(map->profile_mask & (1u << stage))) return;
+  *ev = pooled_event(map);
+  cudaEventRecord(*ev, stream);
+}
+
+void stage_end(ohm_map* map, int stage, cudaStream_t stream, cudaEvent_t ev) {
+  if (!ev) return;
+  cudaEvent_t e1 = pooled_event(map);
+  cudaEventRecord(e1, stream);
+  map->pending.push_back(std::make_pair(stage, std::make_pair(ev, e1)));
+}
+
+}  // namespace ohm
+
+extern "C" {
+
+}  // extern "C"

@@ -1,0 +1,404 @@
+// Device-side data structures of the GB300 ray-integration library: the map
+// (region hash table, region pool, layers), the per-call scratch, and the
+// exact fixed-point voxel walk shared by every kernel.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ohm {
+
+constexpr int kRegionShift = 5;                  // 32 voxels per region edge (Sec. III-B: 3.2 m at 0.1 m)
+constexpr int kRegionVoxels = 1 << (3 * kRegionShift);
+constexpr long long kEmptyKey = -1;              // never a packed key (packed keys are < 2^63)
+constexpr long long kTombKey = -2;               // a key removed by a rolled-back call
+constexpr long long kBig = 1LL << 62;            // "never first" time difference, see Walker
+
+constexpr uint32_t kLayerOcc = 1, kLayerNdt = 2, kLayerTsdf = 4, kLayerCounts = 8;
+constexpr uint8_t kFlagNoReturn = 1;
+
+// Status bits latched in device memory (0 = fine).
+constexpr int kStatusCapacity = 1;   // region or NDT pool full
+constexpr int kStatusProbe = 2;      // hash probe bound exceeded
+constexpr int kStatusScratch = 4;    // per-call scratch too small (a library bug)
+constexpr int kStatusMissing = 8;    // a region expected in the table was not found (a library bug)
+constexpr int kStatusCasLimit = 16;  // a CAS loop gave up (a library bug)
+
+// Ray record written by the occupancy prepare kernel.
+struct __align__(16) RayRec {
+  long long a[3];   // walk start (sensor origin), fixed point
+  long long b[3];   // walk end (sample or truncation point), fixed point
+  int32_t flags;    // kRayValid | kRaySample
+  int32_t nseg;     // number of segments
+};
+constexpr int32_t kRayValid = 1, kRaySample = 2;
+
+// Ray record written by the TSDF prepare kernel: the walk covers the band
+// [max(0, d - tau), d + tau] of the ray from the sensor to the sample e.
+struct __align__(16) TsdfRec {
+  long long a[3];   // band start, fixed point
+  long long b[3];   // band end, fixed point
+  long long e[3];   // sample, fixed point
+  float u[3];       // unit direction sensor -> sample
+  int32_t flags;    // kRayValid when the ray updates the TSDF
+};
+
+// Per-call counters in device memory.
+struct CallCounters {
+  unsigned long long segments;
+  unsigned long long visits;
+  unsigned long long touched;
+  int32_t region_start;   // pool counters when the call began (rollback point)
+  int32_t ndt_start;
+  unsigned long long rays;
+  unsigned long long total_visits;  // every call since the map was made
+};
+
+// Everything a kernel needs, passed by value.
+struct DeviceMap {
+  // region hash table: key -> pool slot (Sec. III-A)
+  long long* hkeys;
+  int32_t* hslots;
+  uint32_t hmask;
+  int32_t max_probe;
+  // region pool
+  int32_t* region_count;
+  int32_t max_regions;
+  int32_t* region_coords;        // [max_regions][3]
+  float* occ;                    // [max_regions][32768], Morton order inside a region
+  unsigned long long* counts;    // [max_regions][32768], hits << 32 | misses
+  int32_t* ndt_slot;             // [max_regions], -1 = no NDT layer yet
+  int32_t* ndt_count;
+  int32_t max_ndt;
+  long long* ndt;                // [max_ndt][10][32768]
+  float2* tsdf;                  // [max_regions][32768] (D, W)
+  uint32_t* tsdf_cnt;            // [max_regions][32768] per-call scratch, zero between calls
+  long long* tsdf_sum;           // [max_regions][32768] per-call scratch, 2^-32 m units
+  int32_t* status;
+  CallCounters* calls;
+  // per-call scratch
+  RayRec* rays;
+  TsdfRec* trays;
+  int2* segs;                    // (ray, segment index)
+  long long max_segs;
+  int32_t* touched;              // TSDF voxels touched by this call (slot * 32768 + morton)
+  long long max_touched;
+  // parameters
+  double origin[3];
+  double scale;                  // 2^F / voxel_size
+  double rmax_q, rmin_q, tau_q;  // ranges in fixed-point units
+  double voxel_size;
+  int32_t frac_bits;
+  uint32_t layers;
+  int32_t seg_steps;
+  float hit, miss, l_min, l_max;
+  float tau_m, wmax;
+};
+
+// Arguments of one integrate call.
+struct CallArgs {
+  const float* origins;
+  const float* endpoints;
+  const uint8_t* flags;
+  long long n;
+  long long n_origins;
+};
+
+// ---------------------------------------------------------------------------
+// Region keys and the hash table.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline long long pack_region(int rx, int ry, int rz) {
+  const unsigned long long m = (1ULL << 21) - 1;
+  return (long long)((((unsigned long long)rx & m) << 42) | (((unsigned long long)ry & m) << 21) |
+                     ((unsigned long long)rz & m));
+}
+
+// 64-bit finaliser of MurmurHash3 (Appleby), a published bit mixer.
+__device__ __forceinline__ uint32_t hash_key(long long k) {
+  unsigned long long x = (unsigned long long)k;
+  x ^= x >> 33;
+  x *= 0xff51afd7ed558ccdULL;
+  x ^= x >> 33;
+  x *= 0xc4ceb9fe1a85ec53ULL;
+  x ^= x >> 33;
+  return (uint32_t)x;
+}
+
+// Pool slot of a region, or -1.  Read-only use of the table.
+__device__ __forceinline__ int32_t find_region(const DeviceMap& m, long long key) {
+  uint32_t h = hash_key(key) & m.hmask;
+  for (int i = 0; i < m.max_probe; ++i) {
+    long long k = m.hkeys[h];
+    if (k == key) return m.hslots[h];
+    if (k == kEmptyKey) return -1;
+    h = (h + 1) & m.hmask;
+  }
+  return -1;
+}
+
+// Insert a region if absent.  The inserting thread takes a pool slot; other
+// threads only learn that the key exists (slots are read after this kernel).
+__device__ inline void insert_region(const DeviceMap& m, int rx, int ry, int rz) {
+  const long long key = pack_region(rx, ry, rz);
+  uint32_t h = hash_key(key) & m.hmask;
+  for (int i = 0; i < m.max_probe; ++i) {
+    long long k = *(volatile long long*)&m.hkeys[h];
+    if (k == key) return;
+    if (k == kEmptyKey) {
+      long long prev = (long long)atomicCAS((unsigned long long*)&m.hkeys[h], (unsigned long long)kEmptyKey,
+                                            (unsigned long long)key);
+      if (prev == kEmptyKey) {
+        int32_t s = atomicAdd(m.region_count, 1);
+        if (s < m.max_regions) {
+          m.hslots[h] = s;
+          m.region_coords[3 * s + 0] = rx;
+          m.region_coords[3 * s + 1] = ry;
+          m.region_coords[3 * s + 2] = rz;
+        } else {
+          atomicOr(m.status, kStatusCapacity);
+        }
+        return;
+      }
+      if (prev == key) return;
+    }
+    h = (h + 1) & m.hmask;
+  }
+  atomicOr(m.status, kStatusProbe);
+}
+
+// ---------------------------------------------------------------------------
+// Fixed-point quantisation: q = rint((x - origin) * scale), double, one
+// rounding per operation (no contraction).  Returns false when |value| would
+// not be exactly representable (>= 2^52).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool quantise(float x, double origin, double scale, long long* q) {
+  double d = __dsub_rn((double)x, origin);
+  double s = __dmul_rn(d, scale);
+  if (!(fabs(s) < 4503599627370496.0)) return false;  // 2^52, also rejects NaN
+  *q = __double2ll_rn(s);
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Morton order inside a region: bit 3i = x_i, 3i+1 = y_i, 3i+2 = z_i.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint32_t spread5(uint32_t x) {
+  uint32_t r = 0;
+  for (int b = 0; b < 5; ++b) r |= ((x >> b) & 1u) << (3 * b);
+  return r;
+}
+__host__ __device__ __forceinline__ uint32_t morton(uint32_t x, uint32_t y, uint32_t z) {
+  return spread5(x) | (spread5(y) << 1) | (spread5(z) << 2);
+}
+
+// Step one axis of a Morton index by +-1, wrapping inside the 5 bits of that axis.
+__device__ __forceinline__ uint32_t morton_step(uint32_t m, uint32_t mask, int sign) {
+  uint32_t moved = sign > 0 ? ((m | ~mask) + 1u) : ((m & mask) - 1u);
+  return (moved & mask) | (m & ~mask);
+}
+
+// ---------------------------------------------------------------------------
+// Exact integer voxel walk (Amanatides & Woo, as adapted in Sec. III-B).
+//
+// Along axis k the ray from a to b moves A_k = |b_k - a_k| fixed-point units
+// per unit of the ray parameter t; the next boundary of the current voxel is
+// dist_k units away, reached at t_k = dist_k / A_k.  Every iteration steps the
+// axis with the smallest t_k (ties: z, then y, then x), never an axis that has
+// already reached b's voxel.  Instead of comparing quotients the walker keeps
+// the three pairwise differences
+//     C_xy = dist_x A_y - dist_y A_x   (t_x < t_y  <=>  C_xy < 0)
+//     C_xz = dist_x A_z - dist_z A_x
+//     C_yz = dist_y A_z - dist_z A_y
+// which change by constants when an axis steps (dist_k grows by U = 2^F).  An
+// axis with no steps left has its differences pinned to +-2^62, so it is never
+// chosen and never blocks the others; magnitudes stay below 2^61 because every
+// ray is shorter than 2^30 fixed-point units (checked when the map is made).
+//
+// Segments (Sec. III-B "breaking long rays into several segments"): the walk
+// of one ray is split by the number K of steps taken along its dominant axis
+// M.  walk_init(K) reconstructs the exact state right after the K-th M step
+// without walking: for every other axis it counts, by integer division, the
+// boundary crossings that come before that step in walk order.  So every
+// segment visits exactly the voxels the unsplit walk visits, in order.
+// ---------------------------------------------------------------------------
+struct Walker {
+  long long cxy, cxz, cyz;
+  long long ua, ub, uc;   // U*A_x, U*A_y, U*A_z
+  int32_t vx, vy, vz;     // current voxel
+  int32_t nx, ny, nz;     // steps left per axis
+  int32_t sx, sy, sz;     // step sign per axis (+1 / -1)
+  int32_t total;          // steps left in the whole ray
+};
+
+__device__ __forceinline__ long long sel3(int k, long long a, long long b, long long c) {
+  return k == 0 ? a : (k == 1 ? b : c);
+}
+
+// Returns the index of the dominant axis (the lowest of equal ones) and the
+// number of steps it takes.
+__device__ __forceinline__ int dominant_axis(const long long a[3], const long long b[3], int F, int32_t* nmaj) {
+  long long d0 = (b[0] >> F) - (a[0] >> F), d1 = (b[1] >> F) - (a[1] >> F), d2 = (b[2] >> F) - (a[2] >> F);
+  d0 = d0 < 0 ? -d0 : d0;
+  d1 = d1 < 0 ? -d1 : d1;
+  d2 = d2 < 0 ? -d2 : d2;
+  int M = 0;
+  long long best = d0;
+  if (d1 > best) {
+    best = d1;
+    M = 1;
+  }
+  if (d2 > best) {
+    best = d2;
+    M = 2;
+  }
+  *nmaj = (int32_t)best;
+  return M;
+}
+
+// Crossings of a non-dominant axis (distance d0k to its first boundary,
+// speed Ak) that come before the K-th step of the dominant axis M (distance
+// d0M, speed AM), in walk order: crossing i precedes it when
+// (d0k + i U) / Ak < (d0M + (K-1) U) / AM, or the two are equal and the axis
+// is above M (ties step z, then y, then x).  Capped at the axis' total ntot.
+__device__ __forceinline__ long long crossings_before(long long d0k, long long Ak, long long d0M, long long AM,
+                                                      long long U, long long K, bool above_major, int32_t ntot) {
+  long long R = (d0M + (K - 1) * U) * Ak - d0k * AM;
+  unsigned long long den = (unsigned long long)(U * AM);
+  long long c;
+  if (!above_major)
+    c = R > 0 ? (long long)(((unsigned long long)R - 1ULL) / den) + 1 : 0;
+  else
+    c = R >= 0 ? (long long)((unsigned long long)R / den) + 1 : 0;
+  return c < ntot ? c : (long long)ntot;
+}
+
+__device__ __forceinline__ void walker_exhaust_x(Walker& w) { w.cxy = kBig; w.cxz = kBig; }
+__device__ __forceinline__ void walker_exhaust_y(Walker& w) { w.cxy = -kBig; w.cyz = kBig; }
+__device__ __forceinline__ void walker_exhaust_z(Walker& w) { w.cxz = -kBig; w.cyz = -kBig; }
+
+// State of the walk from a to b right after K steps along the dominant axis M
+// (K = 0: the start).
+__device__ inline void walker_init(Walker& w, const long long a[3], const long long b[3], int F, int M, long long K) {
+  const long long U = 1LL << F;
+  long long A[3], d0[3], cnt[3];
+  int32_t ntot[3], sgn[3], v0[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    long long delta = b[k] - a[k];
+    A[k] = delta < 0 ? -delta : delta;
+    sgn[k] = delta < 0 ? -1 : 1;
+    long long va = a[k] >> F;  // arithmetic shift: floor
+    long long vb = b[k] >> F;
+    long long nt = vb - va;
+    ntot[k] = (int32_t)(nt < 0 ? -nt : nt);
+    d0[k] = delta < 0 ? (a[k] - va * U) : ((va + 1) * U - a[k]);
+    v0[k] = (int32_t)va;
+  }
+  const long long d0M = sel3(M, d0[0], d0[1], d0[2]);
+  const long long AM = sel3(M, A[0], A[1], A[2]);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    if (K == 0)
+      cnt[k] = 0;
+    else if (k == M)
+      cnt[k] = K;
+    else
+      cnt[k] = crossings_before(d0[k], A[k], d0M, AM, U, K, k > M, ntot[k]);
+  }
+  long long dist[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) dist[k] = d0[k] + cnt[k] * U;
+  w.vx = v0[0] + (int32_t)(sgn[0] * cnt[0]);
+  w.vy = v0[1] + (int32_t)(sgn[1] * cnt[1]);
+  w.vz = v0[2] + (int32_t)(sgn[2] * cnt[2]);
+  w.nx = ntot[0] - (int32_t)cnt[0];
+  w.ny = ntot[1] - (int32_t)cnt[1];
+  w.nz = ntot[2] - (int32_t)cnt[2];
+  w.sx = sgn[0];
+  w.sy = sgn[1];
+  w.sz = sgn[2];
+  w.ua = U * A[0];
+  w.ub = U * A[1];
+  w.uc = U * A[2];
+  w.cxy = dist[0] * A[1] - dist[1] * A[0];
+  w.cxz = dist[0] * A[2] - dist[2] * A[0];
+  w.cyz = dist[1] * A[2] - dist[2] * A[1];
+  w.total = w.nx + w.ny + w.nz;
+  if (w.nx == 0) walker_exhaust_x(w);
+  if (w.ny == 0) walker_exhaust_y(w);
+  if (w.nz == 0) walker_exhaust_z(w);
+}
+
+// Axis of the next step (requires w.total > 0).
+__device__ __forceinline__ int walker_choose(const Walker& w) {
+  return (w.cxy < 0 && w.cxz < 0) ? 0 : ((w.cxy >= 0 && w.cyz < 0) ? 1 : 2);
+}
+
+// Take one step along `axis`; returns the new coordinate along that axis and
+// its step sign through *coord / *sign.
+__device__ __forceinline__ void walker_step(Walker& w, int axis, int32_t* coord, int32_t* sign) {
+  if (axis == 0) {
+    w.cxy += w.ub;
+    w.cxz += w.uc;
+    w.vx += w.sx;
+    w.nx -= 1;
+    if (w.nx == 0) walker_exhaust_x(w);
+    *coord = w.vx;
+    *sign = w.sx;
+  } else if (axis == 1) {
+    w.cxy -= w.ua;
+    w.cyz += w.uc;
+    w.vy += w.sy;
+    w.ny -= 1;
+    if (w.ny == 0) walker_exhaust_y(w);
+    *coord = w.vy;
+    *sign = w.sy;
+  } else {
+    w.cxz -= w.ua;
+    w.cyz -= w.ub;
+    w.vz += w.sz;
+    w.nz -= 1;
+    if (w.nz == 0) walker_exhaust_z(w);
+    *coord = w.vz;
+    *sign = w.sz;
+  }
+  w.total -= 1;
+}
+
+__device__ __forceinline__ uint32_t morton_mask(int axis) {
+  return axis == 0 ? 0x1249u : (axis == 1 ? 0x2492u : 0x4924u);
+}
+
+// Number of segments of a walk whose dominant axis takes nmaj steps.
+__device__ __forceinline__ int32_t segment_count(int32_t nmaj, int32_t S) { return nmaj / S + 1; }
+
+// ---------------------------------------------------------------------------
+// Warp-aggregated reservation: every lane of a full warp calls this together
+// with its own count (possibly 0); returns this lane's first index.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long warp_reserve(unsigned long long* counter, unsigned int count) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  unsigned int incl = count;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned int t = __shfl_up_sync(full, incl, o);
+    if (lane >= o) incl += t;
+  }
+  const unsigned int total = __shfl_sync(full, incl, 31);
+  unsigned long long base = 0;
+  if (lane == 31 && total != 0) base = atomicAdd(counter, (unsigned long long)total);
+  base = __shfl_sync(full, base, 31);
+  return base + incl - count;
+}
+
+// Warp sum of a 32-bit value, added by one lane to two 64-bit counters; full warp.
+__device__ __forceinline__ void warp_add(unsigned long long* counter, unsigned long long* counter2, unsigned int value) {
+  unsigned int total = __reduce_add_sync(0xffffffffu, value);
+  if ((threadIdx.x & 31) == 0 && total != 0) {
+    atomicAdd(counter, (unsigned long long)total);
+    atomicAdd(counter2, (unsigned long long)total);
+  }
+}
+
+}  // namespace ohm

@@ -1,0 +1,51 @@
+// Host-side definition of the map handle and the launch functions shared by
+// the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <utility>
+#include <vector>
+
+#include "../../include/ohm_gb.h"
+#include "ohm_device.cuh"
+
+struct ohm_map {
+  ohm_map_params p;
+  ohm::DeviceMap d;
+  int device;
+  int num_sms;
+  int walk_blocks;          // persistent grid for the walk kernels
+  long long hash_capacity;
+  // device staging for host inputs
+  float* stage_origins;
+  float* stage_endpoints;
+  uint8_t* stage_flags;
+  // pinned host mirrors for status / counters
+  int32_t* h_status;
+  ohm::CallCounters* h_calls;
+  int32_t* h_count;
+  long long launches;       // kernels launched by this map
+  // per-stage event timing
+  uint32_t profile_mask;
+  std::vector<cudaEvent_t> event_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+  double stage_ms[OHM_STAGE_COUNT];
+  long long stage_launches[OHM_STAGE_COUNT];
+};
+
+namespace ohm {
+
+// Enqueue every kernel of one integrate call on `stream`.
+cudaError_t launch_integrate(ohm_map* map, const CallArgs& args, cudaStream_t stream);
+cudaError_t launch_query(ohm_map* map, const float* points, long long n, float* occupancy, uint8_t* known, float* ndt,
+                         float* tsdf, uint32_t* counts, cudaStream_t stream);
+cudaError_t launch_export(ohm_map* map, long long first, long long count, int32_t* keys, float* occupancy,
+                          uint32_t* counts, long long* ndt, float* tsdf, cudaStream_t stream);
+int walk_blocks_per_sm();
+
+// Stage timing helpers (no-ops unless the stage is being profiled).
+void stage_begin(ohm_map* map, int stage, cudaStream_t stream, cudaEvent_t* ev);
+void stage_end(ohm_map* map, int stage, cudaStream_t stream, cudaEvent_t ev);
+
+}  // namespace ohm

@@ -1,0 +1,272 @@
+"""Python binding of the GB300 ray-integration library (include/ohm_gb.h).
+
+Argument marshalling only: every step of ray integration, query and export
+runs in the CUDA library.  PyTorch supplies device memory and streams.  If the
+library has not been built, or no CUDA device is present, calls raise; there
+is no CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libohm_gb.so")
+
+OK, ERR_INVALID, ERR_CAPACITY, ERR_CUDA, ERR_PROBE_LIMIT, ERR_UNSUPPORTED = range(6)
+LAYER_OCCUPANCY, LAYER_NDT, LAYER_TSDF, LAYER_COUNTS = 1, 2, 4, 8
+FLAG_NO_RETURN = 1
+REGION_VOXELS = 32768
+
+_STATUS_NAMES = {ERR_INVALID: "invalid argument", ERR_CAPACITY: "capacity", ERR_CUDA: "CUDA error",
+                 ERR_PROBE_LIMIT: "hash probe limit", ERR_UNSUPPORTED: "unsupported"}
+
+# Every symbol include/ohm_gb.h declares.
+EXPORTED = ["ohm_map_create", "ohm_map_destroy", "ohm_integrate_rays", "ohm_integrate_rays_async", "ohm_map_sync",
+            "ohm_query_voxels", "ohm_map_region_count", "ohm_map_export", "ohm_map_stats", "ohm_map_profile",
+            "ohm_map_profile_read", "ohm_last_error"]
+
+# Kernel stages of an integrate call (ohm_stage).
+STAGES = ["begin", "prepare", "ndt_alloc", "prepare_tsdf", "walk", "hits", "tsdf_walk", "tsdf_apply", "end"]
+
+
+class OhmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (_STATUS_NAMES.get(code, str(code)), msg))
+        self.code = code
+
+
+class MapParams(ctypes.Structure):
+    _fields_ = [
+        ("voxel_size", ctypes.c_double),
+        ("map_origin", ctypes.c_double * 3),
+        ("frac_bits", ctypes.c_int32),
+        ("layers", ctypes.c_uint32),
+        ("hit", ctypes.c_float),
+        ("miss", ctypes.c_float),
+        ("l_min", ctypes.c_float),
+        ("l_max", ctypes.c_float),
+        ("max_range", ctypes.c_double),
+        ("min_range", ctypes.c_double),
+        ("tsdf_trunc", ctypes.c_double),
+        ("tsdf_wmax", ctypes.c_double),
+        ("max_regions", ctypes.c_int64),
+        ("max_ndt_regions", ctypes.c_int64),
+        ("max_rays", ctypes.c_int64),
+        ("segment_steps", ctypes.c_int32),
+        ("device", ctypes.c_int32),
+    ]
+
+
+class CallStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("rays", "segments", "visits", "regions", "ndt_regions", "touched",
+                                              "total_visits", "launches")]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load the shared library (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("CUDA library %s is not built; run __graft_entry__.build()" % path)
+    lib = ctypes.CDLL(path)
+    vp, i64, p = ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p
+    st = ctypes.c_int
+    lib.ohm_map_create.restype = st
+    lib.ohm_map_create.argtypes = [ctypes.POINTER(MapParams), ctypes.POINTER(vp)]
+    lib.ohm_map_destroy.restype = None
+    lib.ohm_map_destroy.argtypes = [vp]
+    for name in ("ohm_integrate_rays", "ohm_integrate_rays_async"):
+        f = getattr(lib, name)
+        f.restype = st
+        f.argtypes = [vp, p, i64, p, p, i64, vp]
+    lib.ohm_map_sync.restype = st
+    lib.ohm_map_sync.argtypes = [vp, vp]
+    lib.ohm_query_voxels.restype = st
+    lib.ohm_query_voxels.argtypes = [vp, p, i64, p, p, p, p, p, vp]
+    lib.ohm_map_region_count.restype = st
+    lib.ohm_map_region_count.argtypes = [vp, ctypes.POINTER(i64), vp]
+    lib.ohm_map_export.restype = st
+    lib.ohm_map_export.argtypes = [vp, i64, i64, p, p, p, p, p, vp]
+    lib.ohm_map_stats.restype = st
+    lib.ohm_map_stats.argtypes = [vp, ctypes.POINTER(CallStats), vp]
+    lib.ohm_map_profile.restype = st
+    lib.ohm_map_profile.argtypes = [vp, ctypes.c_uint32]
+    lib.ohm_map_profile_read.restype = st
+    lib.ohm_map_profile_read.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
+    lib.ohm_last_error.restype = ctypes.c_char_p
+    lib.ohm_last_error.argtypes = []
+    _lib = lib
+    return lib
+
+
+def _check(code):
+    if code != OK:
+        raise OhmError(code, load_library().ohm_last_error().decode())
+
+
+def _stream_handle(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _ptr(x):
+    """Raw pointer of a contiguous torch tensor or numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, torch.Tensor):
+        return ctypes.c_void_p(x.data_ptr())
+    return x.ctypes.data_as(ctypes.c_void_p)
+
+
+def _as_points(x, name):
+    if isinstance(x, torch.Tensor):
+        t = x.contiguous()
+        if t.dtype != torch.float32:
+            raise TypeError("%s must be float32" % name)
+        return t.reshape(-1, 3)
+    a = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, 3)
+    return a
+
+
+def _as_flags(x):
+    if x is None:
+        return None
+    if isinstance(x, torch.Tensor):
+        if x.dtype != torch.uint8:
+            raise TypeError("flags must be uint8")
+        return x.contiguous()
+    return np.ascontiguousarray(x, dtype=np.uint8)
+
+
+def default_params(**kw) -> dict:
+    """Room / tunnel occupancy workload parameters (0.1 m voxels)."""
+    import math
+    p = dict(voxel_size=0.1, map_origin=(0.0, 0.0, 0.0), frac_bits=16, layers=LAYER_OCCUPANCY,
+             hit=float(np.float32(math.log(0.7 / 0.3))), miss=float(np.float32(math.log(0.4 / 0.6))),
+             l_min=-2.0, l_max=3.5, max_range=20.0, min_range=0.0, tsdf_trunc=0.2, tsdf_wmax=float(1 << 20),
+             max_regions=4096, max_ndt_regions=1024, max_rays=1 << 18, segment_steps=0, device=0)
+    p.update(kw)
+    return p
+
+
+class Map:
+    """A voxel map living on one CUDA device."""
+
+    def __init__(self, **params):
+        lib = load_library()
+        self.params = default_params(**params)
+        cp = MapParams()
+        for k, v in self.params.items():
+            if k == "map_origin":
+                for i in range(3):
+                    cp.map_origin[i] = float(v[i])
+            else:
+                setattr(cp, k, v)
+        h = ctypes.c_void_p()
+        _check(lib.ohm_map_create(ctypes.byref(cp), ctypes.byref(h)))
+        self._h = h
+        self.device = torch.device("cuda", int(self.params["device"]))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().ohm_map_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def integrate(self, origins, endpoints, flags=None, stream=None, sync=True):
+        """Integrate one ray set.  Inputs may be CUDA tensors or host arrays."""
+        o = _as_points(origins, "origins")
+        e = _as_points(endpoints, "endpoints")
+        f = _as_flags(flags)
+        lib = load_library()
+        fn = lib.ohm_integrate_rays if sync else lib.ohm_integrate_rays_async
+        _check(fn(self._h, _ptr(o), int(o.shape[0]), _ptr(e), _ptr(f), int(e.shape[0]), _stream_handle(stream)))
+
+    def sync(self, stream=None):
+        _check(load_library().ohm_map_sync(self._h, _stream_handle(stream)))
+
+    def query(self, points, stream=None, ndt=False, tsdf=False, counts=False):
+        """Look up world points; returns a dict of CUDA tensors."""
+        p = _as_points(points, "points")
+        n = int(p.shape[0])
+        dev = self.device
+        out = dict(occupancy=torch.empty(n, dtype=torch.float32, device=dev),
+                   known=torch.empty(n, dtype=torch.uint8, device=dev))
+        if ndt:
+            out["ndt"] = torch.empty((n, 10), dtype=torch.float32, device=dev)
+        if tsdf:
+            out["tsdf"] = torch.empty((n, 2), dtype=torch.float32, device=dev)
+        if counts:
+            out["counts"] = torch.empty((n, 2), dtype=torch.int32, device=dev)
+        _check(load_library().ohm_query_voxels(self._h, _ptr(p), n, _ptr(out["occupancy"]), _ptr(out["known"]),
+                                               _ptr(out.get("ndt")), _ptr(out.get("tsdf")), _ptr(out.get("counts")),
+                                               _stream_handle(stream)))
+        return out
+
+    def region_count(self, stream=None) -> int:
+        c = ctypes.c_int64()
+        _check(load_library().ohm_map_region_count(self._h, ctypes.byref(c), _stream_handle(stream)))
+        return int(c.value)
+
+    def stats(self, stream=None) -> dict:
+        s = CallStats()
+        _check(load_library().ohm_map_stats(self._h, ctypes.byref(s), _stream_handle(stream)))
+        return {k: int(getattr(s, k)) for k, _ in CallStats._fields_}
+
+    def profile(self, stages=()):
+        """Time the kernels of the named stages (see STAGES) in later calls."""
+        mask = 0
+        for name in stages:
+            mask |= 1 << STAGES.index(name)
+        _check(load_library().ohm_map_profile(self._h, mask))
+
+    def profile_read(self, stage: str):
+        """(total device ms, launches) of a profiled stage; waits for them."""
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        _check(load_library().ohm_map_profile_read(self._h, STAGES.index(stage), ctypes.byref(ms), ctypes.byref(n)))
+        return float(ms.value), int(n.value)
+
+    def export(self, occupancy=True, counts=False, ndt=False, tsdf=False, first=0, count=None, stream=None):
+        """Regions [first, first + count) in allocation order as CUDA tensors;
+        voxels x fastest inside a region."""
+        if count is None:
+            count = self.region_count(stream) - first
+        dev = self.device
+        out = dict(keys=torch.empty((count, 3), dtype=torch.int32, device=dev))
+        if occupancy:
+            out["occupancy"] = torch.empty((count, REGION_VOXELS), dtype=torch.float32, device=dev)
+        if counts:
+            out["counts"] = torch.empty((count, REGION_VOXELS, 2), dtype=torch.int32, device=dev)
+        if ndt:
+            out["ndt"] = torch.empty((count, REGION_VOXELS, 10), dtype=torch.int64, device=dev)
+        if tsdf:
+            out["tsdf"] = torch.empty((count, REGION_VOXELS, 2), dtype=torch.float32, device=dev)
+        _check(load_library().ohm_map_export(self._h, first, count, _ptr(out["keys"]), _ptr(out.get("occupancy")),
+                                             _ptr(out.get("counts")), _ptr(out.get("ndt")), _ptr(out.get("tsdf")),
+                                             _stream_handle(stream)))
+        return out

@@ -1,0 +1,106 @@
+"""Helpers comparing a GPU map (through the C ABI) with the oracle."""
+import numpy as np
+import torch
+
+import oracle
+from paper_2206_06079_gb300 import ohm
+
+
+def gpu_region_order(gm: ohm.Map):
+    """GPU region keys and the permutation sorting them like the oracle."""
+    n = gm.region_count()
+    keys = gm.export(occupancy=False, count=n)["keys"].cpu().numpy().astype(np.int64)
+    order = np.lexsort((keys[:, 2], keys[:, 1], keys[:, 0]))
+    return keys, order
+
+
+def compare_dense(gm: ohm.Map, om: oracle.OracleMap, occupancy=True, counts=True, tsdf=False,
+                  tsdf_atol=1e-5, batch=1024):
+    """Region set equal; occupancy bit-exact; hit/miss counts exact; TSDF D
+    within tsdf_atol and W exact.  Returns the number of regions compared."""
+    keys, order = gpu_region_order(gm)
+    n = len(order)
+    assert n == om.region_count(), (n, om.region_count())
+    for i0 in range(0, n, batch):
+        i1 = min(n, i0 + batch)
+        ref = om.export(first=i0, count=i1 - i0, occupancy=occupancy, counts=counts, ndt=False, tsdf=tsdf)
+        assert np.array_equal(keys[order[i0:i1]], ref["keys"]), "region keys differ"
+        slots = torch.from_numpy(order[i0:i1]).cuda()
+        for s0 in range(0, i1 - i0, 256):
+            sl = slots[s0:s0 + 256]
+            # export contiguous GPU slots covering this batch, then gather
+            lo, hi = int(sl.min()), int(sl.max()) + 1
+            ex = gm.export(occupancy=occupancy, counts=counts, tsdf=tsdf, first=lo, count=hi - lo)
+            idx = sl - lo
+            r = slice(s0, s0 + len(sl))
+            if occupancy:
+                g = ex["occupancy"][idx].cpu().numpy()
+                assert np.array_equal(g.view(np.uint32), ref["occupancy"][r].view(np.uint32)), "occupancy differs"
+            if counts:
+                c = ex["counts"][idx].cpu().numpy().view(np.uint32)
+                assert np.array_equal(c[..., 0], ref["hits"][r]), "hit counts differ"
+                assert np.array_equal(c[..., 1], ref["misses"][r]), "miss counts differ"
+            if tsdf:
+                t = ex["tsdf"][idx].cpu().numpy().astype(np.float64)
+                assert np.array_equal(t[..., 1], ref["tsdf"][r][..., 1]), "TSDF weights differ"
+                err = np.abs(t[..., 0] - ref["tsdf"][r][..., 0]).max()
+                assert err <= tsdf_atol, "TSDF distance differs by %g" % err
+    return n
+
+
+def gpu_ndt_sparse(gm: ohm.Map, batch=64):
+    """(voxels, moments) of every GPU voxel holding a sample, in oracle order."""
+    keys, order = gpu_region_order(gm)
+    vox_all, mom_all = [], []
+    n = len(keys)
+    lin = torch.arange(ohm.REGION_VOXELS, device="cuda")
+    local = torch.stack([lin % 32, (lin // 32) % 32, lin // 1024], 1)
+    for s0 in range(0, n, batch):
+        cnt = min(batch, n - s0)
+        ex = gm.export(occupancy=False, ndt=True, first=s0, count=cnt)
+        nd = ex["ndt"]
+        hit = nd[..., 0] > 0
+        r, v = torch.nonzero(hit, as_tuple=True)
+        k = ex["keys"].long()[r] * 32 + local[v]
+        vox_all.append(k.cpu().numpy())
+        mom_all.append(nd[r, v].cpu().numpy())
+    vox = np.concatenate(vox_all) if vox_all else np.zeros((0, 3), np.int64)
+    mom = np.concatenate(mom_all) if mom_all else np.zeros((0, 10), np.int64)
+    return vox, mom
+
+
+def compare_ndt(gm: ohm.Map, om: oracle.OracleMap):
+    """Exact equality of every sample voxel's integer moments."""
+    gv, gmom = gpu_ndt_sparse(gm)
+    ov, omom = om.ndt_sparse()
+    assert len(gv) == len(ov), (len(gv), len(ov))
+    og = np.lexsort((gv[:, 0], gv[:, 1], gv[:, 2]))
+    oo = np.lexsort((ov[:, 0], ov[:, 1], ov[:, 2]))
+    assert np.array_equal(gv[og], ov[oo]), "NDT voxel sets differ"
+    assert np.array_equal(gmom[og], omom[oo]), "NDT moments differ"
+    return len(gv), ov
+
+
+def compare_query(gm: ohm.Map, om: oracle.OracleMap, pts: np.ndarray, ndt=False, tsdf=False, ndt_rtol=1e-4,
+                  tsdf_atol=1e-5):
+    g = gm.query(torch.from_numpy(np.ascontiguousarray(pts, dtype=np.float32)).cuda(), ndt=ndt, tsdf=tsdf)
+    r = om.query(pts)
+    assert np.array_equal(g["known"].cpu().numpy(), r["known"]), "known flags differ"
+    k = r["known"] == 1
+    go = g["occupancy"].cpu().numpy()
+    assert np.array_equal(go[k].view(np.uint32), r["occupancy"][k].view(np.uint32)), "occupancy differs"
+    assert np.isnan(go[~k]).all()
+    if ndt:
+        gn = g["ndt"].cpu().numpy().astype(np.float64)
+        rn = r["ndt"]
+        assert np.array_equal(gn[:, 0], rn[:, 0]), "NDT counts differ"
+        s = rn[:, 0] > 0
+        assert np.allclose(gn[s, 1:4], rn[s, 1:4], rtol=ndt_rtol, atol=0), "NDT means differ"
+        # covariance: relative to the voxel's squared size (entries can be ~0)
+        vs2 = gm.params["voxel_size"] ** 2
+        assert np.allclose(gn[s, 4:], rn[s, 4:], rtol=ndt_rtol, atol=ndt_rtol * vs2), "NDT covariances differ"
+    if tsdf:
+        gt = g["tsdf"].cpu().numpy().astype(np.float64)
+        assert np.array_equal(gt[:, 1], r["tsdf"][:, 1])
+        assert np.abs(gt[:, 0] - r["tsdf"][:, 0]).max(initial=0) <= tsdf_atol
+    return int(k.sum())

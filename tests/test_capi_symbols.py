@@ -1,0 +1,63 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, and exports every
+function include/ohm_gb.h declares (no compute calls here)."""
+import ctypes
+import os
+import re
+
+from paper_2206_06079_gb300 import build_lib, ohm
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "ohm_gb.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ohm_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("ohm_map_create", "ohm_integrate_rays", "ohm_query_voxels", "ohm_map_destroy"):
+        assert required in names
+    assert set(names) == set(ohm.EXPORTED)
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(build_lib.build())
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_rejects_a_missing_library(tmp_path):
+    import pytest
+    saved = ohm._lib
+    ohm._lib = None
+    try:
+        with pytest.raises(RuntimeError):
+            ohm.load_library(str(tmp_path / "missing.so"))
+    finally:
+        ohm._lib = saved
+
+
+def _c_layout(struct, fields, tmp_path):
+    """Field offsets and size of a header struct, as gcc lays it out."""
+    import subprocess
+    src = tmp_path / "layout.c"
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ohm_gb.h"', 'int main(void) {']
+    for f in fields:
+        lines.append('  printf("%%zu\\n", offsetof(%s, %s));' % (struct, f))
+    lines.append('  printf("%%zu\\n", sizeof(%s));' % struct)
+    lines.append('  return 0; }')
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    return [int(x) for x in out]
+
+
+def test_param_structs_match_the_header(tmp_path):
+    for cls, name in ((ohm.MapParams, "ohm_map_params"), (ohm.CallStats, "ohm_call_stats")):
+        fields = [f for f, _ in cls._fields_]
+        got = _c_layout(name, fields, tmp_path)
+        assert got[:-1] == [getattr(cls, f).offset for f in fields], name
+        assert got[-1] == ctypes.sizeof(cls), name

@@ -1,0 +1,242 @@
+"""GPU path (through the C ABI) against the oracle on seeded inputs.
+
+Bar: voxel traversal bit-exact (region sets, per-voxel hit/miss counts, NDT
+integer moments), log-odds bit-exact (both sides apply the same FP32 clamped
+updates in the same per-call order), NDT mean/covariance within 1e-4
+relative, TSDF distance within 1e-5 m absolute and weights exact.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2206_06079_gb300 import ohm, synth, workloads as W
+
+from .parity import compare_dense, compare_ndt, compare_query
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+    assert torch.cuda.is_available()
+
+
+def _pair(params):
+    gm = ohm.Map(**params)
+    om = oracle.OracleMap(**W.oracle_params(params))
+    return gm, om
+
+
+def _integrate_both(gm, om, rays, device_inputs=True):
+    o, e, f = rays.numpy()
+    if device_inputs:
+        gm.integrate(rays.origins.cuda(), rays.endpoints.cuda(), rays.flags.cuda())
+    else:
+        gm.integrate(o, e, f)
+    return om.integrate(o, e, f)
+
+
+def _sample_points(rays, k=20000, seed=0):
+    o, e, f = rays.numpy()
+    rng = np.random.default_rng(seed)
+    idx = rng.integers(0, len(e), size=min(k, len(e)))
+    t = rng.uniform(0, 1.05, size=(len(idx), 1))
+    oo = o[0] if len(o) == 1 else o[idx]
+    return np.concatenate([e[idx], oo + t * (e[idx] - oo)]).astype(np.float32)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_fuzz_rays_all_layers(seed):
+    p = W.room_params(layers=W.OCC | W.COUNTS | W.NDT, max_regions=4096, max_rays=4096, max_range=2.5)
+    gm, om = _pair(p)
+    for scan in range(3):
+        rays = synth.fuzz_rays(seed * 100 + scan, 3000)
+        _integrate_both(gm, om, rays)
+    compare_dense(gm, om)
+    compare_ndt(gm, om)
+    compare_query(gm, om, _sample_points(rays), ndt=True)
+
+
+@pytest.mark.parametrize("steps", [1, 3, 17, 64, 100000])
+def test_segment_split_never_changes_the_walk(steps):
+    """Segments (Sec. III-B) are a scheduling device: every split reproduces
+    the unsplit walk exactly."""
+    p = W.tunnel_params(layers=W.OCC | W.COUNTS, segment_steps=steps, max_rays=16384, max_regions=16384)
+    gm, om = _pair(p)
+    for i in range(2):
+        rays = synth.tunnel_scan(i, beams=16, azimuths=1024)
+        _integrate_both(gm, om, rays)
+    compare_dense(gm, om)
+
+
+def test_room_scan_full_size():
+    p = W.room_params(layers=W.OCC | W.COUNTS)
+    gm, om = _pair(p)
+    rays = W.room_rays(0)
+    visits = _integrate_both(gm, om, rays)
+    assert gm.stats()["visits"] == visits
+    compare_dense(gm, om)
+    compare_query(gm, om, _sample_points(rays))
+
+
+def test_tunnel_scans_full_size_occupancy_ndt():
+    """The tunnel workload's map parameters and launch configuration, three
+    full 131,072-ray scans, every layer compared."""
+    p = W.tunnel_params(layers=W.OCC | W.NDT | W.COUNTS)
+    gm, om = _pair(p)
+    for i in range(3):
+        rays = W.tunnel_rays(i)
+        visits = _integrate_both(gm, om, rays)
+        st = gm.stats()
+        assert st["visits"] == visits and st["rays"] == rays.n
+    compare_dense(gm, om, batch=512)
+    nsamp, _ = compare_ndt(gm, om)
+    assert nsamp > 10000
+    compare_query(gm, om, _sample_points(rays), ndt=True)
+
+
+def test_tunnel_bench_layers_query_parity():
+    """Bench layers (occupancy + NDT, no counts): sampled outputs via query."""
+    p = W.tunnel_params()
+    gm, om = _pair(p)
+    for i in range(2):
+        rays = W.tunnel_rays(10 + i)
+        _integrate_both(gm, om, rays)
+    assert gm.region_count() == om.region_count()
+    compare_query(gm, om, _sample_points(rays, k=50000), ndt=True)
+    compare_ndt(gm, om)
+
+
+@pytest.mark.parametrize("size", [(160, 120), (640, 480)])
+def test_tsdf_frames(size):
+    w, h = size
+    p = W.tsdf_params(max_rays=w * h)
+    gm, om = _pair(p)
+    scene = synth.depth_scene()
+    frames = 3 if w < 640 else 1
+    for i in range(frames):
+        rays = W.tsdf_rays(i * 7, width=w, height=h, scene=scene)
+        visits = _integrate_both(gm, om, rays)
+        assert gm.stats()["visits"] == visits
+    n = compare_dense(gm, om, occupancy=False, counts=False, tsdf=True, tsdf_atol=1e-5)
+    assert n > 0
+
+
+def test_occupancy_and_tsdf_in_one_map():
+    p = W.tsdf_params(layers=W.OCC | W.TSDF | W.COUNTS, max_rays=160 * 120)
+    gm, om = _pair(p)
+    rays = W.tsdf_rays(3, width=160, height=120)
+    _integrate_both(gm, om, rays)
+    compare_dense(gm, om, occupancy=True, counts=True, tsdf=True)
+
+
+def test_host_inputs_match_device_inputs():
+    p = W.room_params(layers=W.OCC | W.COUNTS)
+    a = ohm.Map(**p)
+    b = ohm.Map(**p)
+    rays = W.room_rays(1)
+    o, e, f = rays.numpy()
+    a.integrate(o, e, f)
+    b.integrate(rays.origins.cuda(), rays.endpoints.cuda(), rays.flags.cuda())
+    ea, eb = a.export(counts=True), b.export(counts=True)
+    ka, kb = ea["keys"].cpu().numpy(), eb["keys"].cpu().numpy()
+    oa, ob = np.lexsort(ka.T[::-1]), np.lexsort(kb.T[::-1])
+    assert np.array_equal(ka[oa], kb[ob])
+    assert torch.equal(ea["occupancy"][torch.from_numpy(oa).cuda()].view(torch.int32),
+                       eb["occupancy"][torch.from_numpy(ob).cuda()].view(torch.int32))
+
+
+def test_repeat_runs_are_bit_identical():
+    p = W.tunnel_params(layers=W.OCC | W.COUNTS | W.NDT, max_rays=32768)
+    outs = []
+    for _ in range(2):
+        gm = ohm.Map(**p)
+        for i in range(2):
+            r = synth.tunnel_scan(i, beams=32, azimuths=1024)
+            gm.integrate(r.origins.cuda(), r.endpoints.cuda(), r.flags.cuda())
+        ex = gm.export(counts=True, ndt=False)
+        k = ex["keys"].cpu().numpy()
+        o = torch.from_numpy(np.lexsort(k.T[::-1])).cuda()
+        outs.append((k[o.cpu().numpy()], ex["occupancy"][o].view(torch.int32).cpu(), ex["counts"][o].cpu()))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert torch.equal(outs[0][1], outs[1][1]) and torch.equal(outs[0][2], outs[1][2])
+
+
+def test_per_ray_origins_and_async_sync():
+    p = W.room_params(layers=W.OCC | W.COUNTS | W.NDT, max_rays=8192)
+    gm, om = _pair(p)
+    rng = np.random.default_rng(5)
+    o = rng.uniform(-1, 1, size=(8000, 3)).astype(np.float32)
+    e = (o + rng.normal(size=(8000, 3)) * 3).astype(np.float32)
+    f = (rng.uniform(size=8000) < 0.1).astype(np.uint8)
+    gm.integrate(torch.from_numpy(o).cuda(), torch.from_numpy(e).cuda(), torch.from_numpy(f).cuda(), sync=False)
+    gm.integrate(torch.from_numpy(e).cuda(), torch.from_numpy(o).cuda(), None, sync=False)
+    gm.sync()
+    om.integrate(o, e, f)
+    om.integrate(e, o, None)
+    compare_dense(gm, om)
+    compare_ndt(gm, om)
+
+
+def test_edge_cases():
+    p = W.room_params(layers=W.OCC | W.COUNTS | W.NDT, max_rays=64)
+    gm, om = _pair(p)
+    gm.integrate(np.zeros((1, 3), np.float32), np.zeros((0, 3), np.float32))  # empty ray set
+    assert gm.region_count() == 0
+    o = np.array([[0.05, 0.05, 0.05]], np.float32)
+    e = np.array([[0.05, 0.05, 0.05],            # zero length
+                  [np.nan, 0, 0],                 # skipped
+                  [1e30, 0, 0],                   # beyond fixed-point range: skipped
+                  [0.1, 0.1, 0.1],                # corner of the origin voxel
+                  [-0.1, 0.0, 0.0],               # on faces, negative direction
+                  [30.0, 0.0, 0.0],               # truncated to 20 m
+                  [0.3, -0.3, 0.3]], np.float32)  # exact diagonal
+    f = np.array([0, 0, 0, 0, 0, 0, 1], np.uint8)
+    _integrate_both(gm, om, synth.RaySet(torch.from_numpy(o), torch.from_numpy(e), torch.from_numpy(f)))
+    compare_dense(gm, om)
+    compare_ndt(gm, om)
+    # all rays skipped
+    bad = np.full((5, 3), np.inf, np.float32)
+    gm.integrate(o, bad)
+    om.integrate(o, bad)
+    compare_dense(gm, om)
+    with pytest.raises(ohm.OhmError):
+        gm.integrate(o, np.zeros((65, 3), np.float32))  # more than max_rays
+
+
+def test_region_pool_exhaustion_leaves_map_unchanged():
+    p = W.room_params(layers=W.OCC | W.COUNTS | W.NDT, max_regions=40, max_ndt_regions=40)
+    gm, om = _pair(p)
+    small = synth.room_scan(n=2000, room_min=(-1, -1, 0), room_max=(1, 1, 2))
+    _integrate_both(gm, om, small)
+    before = gm.export(counts=True)
+    n_before = gm.region_count()
+    with pytest.raises(ohm.OhmError) as ei:
+        gm.integrate(*W.room_rays(0).numpy())  # needs 48 regions
+    assert ei.value.code == ohm.ERR_CAPACITY
+    assert gm.region_count() == n_before
+    after = gm.export(counts=True)
+    assert torch.equal(before["occupancy"].view(torch.int32), after["occupancy"].view(torch.int32))
+    assert torch.equal(before["counts"], after["counts"])
+    # the map keeps working and still matches the oracle that never saw the failed call
+    _integrate_both(gm, om, synth.room_scan(seed=9, n=2000, room_min=(-1, -1, 0), room_max=(1, 1, 2)))
+    compare_dense(gm, om)
+    compare_ndt(gm, om)
+
+
+def test_ndt_pool_exhaustion_leaves_map_unchanged():
+    p = W.room_params(layers=W.OCC | W.NDT, max_regions=1024, max_ndt_regions=4)
+    gm, om = _pair(p)
+    with pytest.raises(ohm.OhmError) as ei:
+        gm.integrate(*W.room_rays(0).numpy())
+    assert ei.value.code == ohm.ERR_CAPACITY
+    assert gm.region_count() == 0
+    st = gm.stats()
+    assert st["ndt_regions"] == 0
+    tiny = synth.room_scan(n=500, room_min=(-0.5, -0.5, 0.5), room_max=(0.5, 0.5, 1.5))
+    _integrate_both(gm, om, tiny)
+    compare_dense(gm, om, counts=False)
+    compare_ndt(gm, om)
