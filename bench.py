@@ -191,7 +191,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     rays_per_scan = scans[0].n
 
-    gm = ohm.Map(**W.tunnel_params(device=local))
+    pools = dict(max_regions=12288, max_ndt_regions=512) if args.profile_case else {}
+    gm = ohm.Map(**W.tunnel_params(device=local, **pools))
     stream = torch.cuda.current_stream()
 
     def scan(i):
@@ -233,11 +234,31 @@ def run_ours(args):
     visits = st1["total_visits"] - st0["total_visits"]
     launches = st1["launches"] - st0["launches"]
 
+    # per-stage device time (separate, untimed pass with events around every kernel)
+    stage_ms = {}
+    if not args.profile_case:
+        gm.profile(ohm.STAGES)
+        for k in range(min(args.steps, 50)):
+            s = scan(args.warmup + k)
+            gm.integrate(s.origins, s.endpoints, s.flags, stream=stream, sync=False)
+        gm.sync()
+        for name in ohm.STAGES:
+            ms, nl = gm.profile_read(name)
+            if nl:
+                stage_ms[name] = ms / nl
+        gm.profile([])
+
     max_ms = _max_over_ranks(elapsed_ms, ws)
     total_rays = _sum_over_ranks(float(rays_per_scan * args.steps), ws)
     total_visits = _sum_over_ranks(float(visits), ws)
     value = total_rays / (max_ms / 1e3)
 
+    if args.profile_case:
+        if rank == 0:
+            print(json.dumps({"profile_case": True, "rays_per_scan": rays_per_scan, "steps": args.steps,
+                              "visits_per_scan": visits / args.steps, "walk_avg_ms": walk_ms / max(walk_launches, 1),
+                              "segments_last_scan": st1["segments"], "regions": st1["regions"]}), flush=True)
+        return
     # ---- end to end: host (pinned) inputs copied inside each call, status read back
     host = []
     for i in range(n_unique):
@@ -302,6 +323,7 @@ def run_ours(args):
                            "max": lat[-1]},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4},
             "gpu_launches": int(launches),
+            "stages_ms": stage_ms,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic, "kernel": "k_walk_miss",
                          "algorithmic_bytes_per_launch": algo_bytes, "avg_launch_ms": walk_avg_s * 1e3,
@@ -370,6 +392,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--profile-case", action="store_true",
+                    help="small pools (a few GB on the device), no e2e or CPU leg: the case ncu captures")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

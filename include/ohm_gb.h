@@ -73,7 +73,7 @@ typedef struct {
   double min_range;        /* TSDF only: samples at or below this range are ignored */
   double tsdf_trunc;       /* TSDF truncation distance tau in metres */
   double tsdf_wmax;        /* TSDF weight cap */
-  int64_t max_regions;     /* capacity of the region pool */
+  int64_t max_regions;     /* capacity of the region pool, 1..65536 (8 GB of occupancy) */
   int64_t max_ndt_regions; /* capacity of the NDT layer pool (regions holding samples) */
   int64_t max_rays;        /* largest ray count accepted by one integrate call */
   int32_t segment_steps;   /* rays are split every this many voxel steps along their

@@ -145,7 +145,7 @@ ohm_status ohm_map_create(const ohm_map_params* params, ohm_map** out) {
   if (!(p.max_range > 0.0)) return fail(OHM_ERR_INVALID, "create: max_range must be > 0");
   if (!(p.min_range >= 0.0)) return fail(OHM_ERR_INVALID, "create: min_range must be >= 0");
   if (!(p.tsdf_trunc >= 0.0) || !(p.tsdf_wmax > 0.0)) return fail(OHM_ERR_INVALID, "create: bad TSDF parameters");
-  if (p.max_regions < 1 || p.max_regions > (1LL << 26)) return fail(OHM_ERR_INVALID, "create: max_regions out of range");
+  if (p.max_regions < 1 || p.max_regions > (1LL << 16)) return fail(OHM_ERR_INVALID, "create: max_regions must be in [1, 65536]");
   if (p.max_rays < 1 || p.max_rays > (1LL << 30)) return fail(OHM_ERR_INVALID, "create: max_rays out of range");
   if (p.segment_steps < 1) return fail(OHM_ERR_INVALID, "create: segment_steps must be >= 1");
   if ((p.layers & OHM_LAYER_NDT) && (p.max_ndt_regions < 1 || p.max_ndt_regions > p.max_regions))

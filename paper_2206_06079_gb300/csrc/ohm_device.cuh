@@ -192,7 +192,7 @@ __host__ __device__ __forceinline__ uint32_t morton(uint32_t x, uint32_t y, uint
 }
 
 // Step one axis of a Morton index by +-1, wrapping inside the 5 bits of that axis.
-__device__ __forceinline__ uint32_t morton_step(uint32_t m, uint32_t mask, int sign) {
+__host__ __device__ __forceinline__ uint32_t morton_step(uint32_t m, uint32_t mask, int sign) {
   uint32_t moved = sign > 0 ? ((m | ~mask) + 1u) : ((m & mask) - 1u);
   return (moved & mask) | (m & ~mask);
 }
@@ -230,13 +230,13 @@ struct Walker {
   int32_t total;          // steps left in the whole ray
 };
 
-__device__ __forceinline__ long long sel3(int k, long long a, long long b, long long c) {
+__host__ __device__ __forceinline__ long long sel3(int k, long long a, long long b, long long c) {
   return k == 0 ? a : (k == 1 ? b : c);
 }
 
 // Returns the index of the dominant axis (the lowest of equal ones) and the
 // number of steps it takes.
-__device__ __forceinline__ int dominant_axis(const long long a[3], const long long b[3], int F, int32_t* nmaj) {
+__host__ __device__ __forceinline__ int dominant_axis(const long long a[3], const long long b[3], int F, int32_t* nmaj) {
   long long d0 = (b[0] >> F) - (a[0] >> F), d1 = (b[1] >> F) - (a[1] >> F), d2 = (b[2] >> F) - (a[2] >> F);
   d0 = d0 < 0 ? -d0 : d0;
   d1 = d1 < 0 ? -d1 : d1;
@@ -260,7 +260,7 @@ __device__ __forceinline__ int dominant_axis(const long long a[3], const long lo
 // d0M, speed AM), in walk order: crossing i precedes it when
 // (d0k + i U) / Ak < (d0M + (K-1) U) / AM, or the two are equal and the axis
 // is above M (ties step z, then y, then x).  Capped at the axis' total ntot.
-__device__ __forceinline__ long long crossings_before(long long d0k, long long Ak, long long d0M, long long AM,
+__host__ __device__ __forceinline__ long long crossings_before(long long d0k, long long Ak, long long d0M, long long AM,
                                                       long long U, long long K, bool above_major, int32_t ntot) {
   long long R = (d0M + (K - 1) * U) * Ak - d0k * AM;
   unsigned long long den = (unsigned long long)(U * AM);
@@ -272,13 +272,13 @@ __device__ __forceinline__ long long crossings_before(long long d0k, long long A
   return c < ntot ? c : (long long)ntot;
 }
 
-__device__ __forceinline__ void walker_exhaust_x(Walker& w) { w.cxy = kBig; w.cxz = kBig; }
-__device__ __forceinline__ void walker_exhaust_y(Walker& w) { w.cxy = -kBig; w.cyz = kBig; }
-__device__ __forceinline__ void walker_exhaust_z(Walker& w) { w.cxz = -kBig; w.cyz = -kBig; }
+__host__ __device__ __forceinline__ void walker_exhaust_x(Walker& w) { w.cxy = kBig; w.cxz = kBig; }
+__host__ __device__ __forceinline__ void walker_exhaust_y(Walker& w) { w.cxy = -kBig; w.cyz = kBig; }
+__host__ __device__ __forceinline__ void walker_exhaust_z(Walker& w) { w.cxz = -kBig; w.cyz = -kBig; }
 
 // State of the walk from a to b right after K steps along the dominant axis M
 // (K = 0: the start).
-__device__ inline void walker_init(Walker& w, const long long a[3], const long long b[3], int F, int M, long long K) {
+__host__ __device__ inline void walker_init(Walker& w, const long long a[3], const long long b[3], int F, int M, long long K) {
   const long long U = 1LL << F;
   long long A[3], d0[3], cnt[3];
   int32_t ntot[3], sgn[3], v0[3];
@@ -330,13 +330,13 @@ __device__ inline void walker_init(Walker& w, const long long a[3], const long l
 }
 
 // Axis of the next step (requires w.total > 0).
-__device__ __forceinline__ int walker_choose(const Walker& w) {
+__host__ __device__ __forceinline__ int walker_choose(const Walker& w) {
   return (w.cxy < 0 && w.cxz < 0) ? 0 : ((w.cxy >= 0 && w.cyz < 0) ? 1 : 2);
 }
 
 // Take one step along `axis`; returns the new coordinate along that axis and
 // its step sign through *coord / *sign.
-__device__ __forceinline__ void walker_step(Walker& w, int axis, int32_t* coord, int32_t* sign) {
+__host__ __device__ __forceinline__ void walker_step(Walker& w, int axis, int32_t* coord, int32_t* sign) {
   if (axis == 0) {
     w.cxy += w.ub;
     w.cxz += w.uc;
@@ -365,12 +365,12 @@ __device__ __forceinline__ void walker_step(Walker& w, int axis, int32_t* coord,
   w.total -= 1;
 }
 
-__device__ __forceinline__ uint32_t morton_mask(int axis) {
+__host__ __device__ __forceinline__ uint32_t morton_mask(int axis) {
   return axis == 0 ? 0x1249u : (axis == 1 ? 0x2492u : 0x4924u);
 }
 
 // Number of segments of a walk whose dominant axis takes nmaj steps.
-__device__ __forceinline__ int32_t segment_count(int32_t nmaj, int32_t S) { return nmaj / S + 1; }
+__host__ __device__ __forceinline__ int32_t segment_count(int32_t nmaj, int32_t S) { return nmaj / S + 1; }
 
 // ---------------------------------------------------------------------------
 // Warp-aggregated reservation: every lane of a full warp calls this together

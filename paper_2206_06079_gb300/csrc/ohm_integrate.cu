@@ -216,12 +216,34 @@ __global__ void __launch_bounds__(kBlock) k_ndt_alloc(DeviceMap m, long long n) 
   }
 }
 
+// Retry a clamped log-odds CAS whose first attempt found `cur` instead of
+// the value it expected (see logodds_update).
+__device__ __forceinline__ void logodds_retry(const DeviceMap& m, unsigned int* u, unsigned int cur, float delta) {
+  for (int it = 0; it < 256; ++it) {
+    const float l = __uint_as_float(cur);
+    const float l0 = (l != l) ? 0.0f : l;
+    const unsigned int nb = __float_as_uint(fminf(fmaxf(__fadd_rn(l0, delta), m.l_min), m.l_max));
+    if (nb == cur) return;
+    const unsigned int prev = atomicCAS(u, cur, nb);
+    if (prev == cur) return;
+    cur = prev;
+  }
+  atomicOr(m.status, kStatusCasLimit);
+}
+
 // Miss phase (Sec. III-C phase one): every voxel a ray passes through, except
 // the voxel holding its sample, takes one miss.  One thread per segment;
 // segment j of a ray covers the voxels entered after j*S and before
 // (j+1)*S steps of the ray's dominant axis (the last segment runs to the end).
+//
+// The walk itself is cheap integer arithmetic; the cost is the read-modify-
+// write of each voxel in global memory.  So a thread walks kWalkBatch voxels
+// ahead, then issues all their loads at once, then all their CASes at once,
+// keeping that many memory operations in flight instead of one.
+constexpr int kWalkBatch = 8;
+
 template <bool kOcc, bool kCounts>
-__global__ void __launch_bounds__(kBlock) k_walk_miss(DeviceMap m) {
+__global__ void __launch_bounds__(kBlock, 2) k_walk_miss(DeviceMap m) {
   if (latched(m)) return;
   const long long nseg = (long long)m.calls->segments;
   const int F = m.frac_bits;
@@ -244,28 +266,61 @@ __global__ void __launch_bounds__(kBlock) k_walk_miss(DeviceMap m) {
       continue;
     }
     uint32_t mo = local_morton(w.vx, w.vy, w.vz);
-    for (;;) {
-      // visit the current voxel: a miss unless it is the sample's voxel
-      if (!(sample && w.total == 0)) {
-        const long long off = voxel_offset(slot, mo);
-        if (kOcc) logodds_update(m, m.occ + off, miss);
-        if (kCounts) atomicAdd(m.counts + off, 1ULL);
-      }
-      if (w.total == 0) break;
-      const int axis = walker_choose(w);
-      if (axis == M) {
-        if (mrem == 0) break;
-        --mrem;
-      }
-      int32_t c, s;
-      walker_step(w, axis, &c, &s);
-      mo = morton_step(mo, morton_mask(axis), s);
-      if ((c & ((1 << kRegionShift) - 1)) == (s > 0 ? 0 : (1 << kRegionShift) - 1)) {
-        slot = region_slot_of(m, w.vx, w.vy, w.vz);
-        if (slot < 0) {
-          atomicOr(m.status, kStatusMissing);
-          break;
+    bool done = false;
+    while (!done) {
+      uint32_t off[kWalkBatch];  // voxel offsets (< 2^31: at most 2^16 regions of 2^15 voxels)
+      uint32_t todo = 0;         // bit j: off[j] takes a miss
+#pragma unroll
+      for (int j = 0; j < kWalkBatch; ++j) {
+        off[j] = 0;
+        if (done) continue;
+        // the current voxel takes a miss unless it holds this ray's sample
+        off[j] = (uint32_t)voxel_offset(slot, mo);
+        if (!(sample && w.total == 0)) {
+          todo |= 1u << j;
+          if (kCounts) atomicAdd(m.counts + off[j], 1ULL);
         }
+        if (w.total == 0) {
+          done = true;
+          continue;
+        }
+        const int axis = walker_choose(w);
+        if (axis == M) {
+          if (mrem == 0) {
+            done = true;
+            continue;
+          }
+          --mrem;
+        }
+        int32_t c, s;
+        walker_step(w, axis, &c, &s);
+        mo = morton_step(mo, morton_mask(axis), s);
+        if ((c & ((1 << kRegionShift) - 1)) == (s > 0 ? 0 : (1 << kRegionShift) - 1)) {
+          slot = region_slot_of(m, w.vx, w.vy, w.vz);
+          if (slot < 0) {
+            atomicOr(m.status, kStatusMissing);
+            done = true;
+          }
+        }
+      }
+      if (kOcc) {
+        unsigned int* base = reinterpret_cast<unsigned int*>(m.occ);
+        unsigned int old[kWalkBatch], prev[kWalkBatch];
+#pragma unroll
+        for (int j = 0; j < kWalkBatch; ++j) old[j] = (todo >> j) & 1u ? base[off[j]] : 0u;
+#pragma unroll
+        for (int j = 0; j < kWalkBatch; ++j) {
+          prev[j] = old[j];
+          if (!((todo >> j) & 1u)) continue;
+          const float l = __uint_as_float(old[j]);
+          const float l0 = (l != l) ? 0.0f : l;
+          const unsigned int nb = __float_as_uint(fminf(fmaxf(__fadd_rn(l0, miss), m.l_min), m.l_max));
+          if (nb == old[j]) continue;
+          prev[j] = atomicCAS(base + off[j], old[j], nb);
+        }
+#pragma unroll
+        for (int j = 0; j < kWalkBatch; ++j)
+          if (prev[j] != old[j]) logodds_retry(m, base + off[j], prev[j], miss);
       }
     }
   }

@@ -1,0 +1,55 @@
+// Host-side check of the device walker: compiles the library's walker
+// (ohm_device.cuh, host+device functions) for the CPU and prints, for every
+// ray, the voxels visited by all of its segments in segment order.  The
+// Python test compares this with the oracle's walk.  No GPU is needed.
+//
+// stdin:  F S n, then n lines "ax ay az bx by bz" (fixed point)
+// stdout: per ray "count" then count lines "x y z"
+#include <climits>
+#include <cstdio>
+
+#include "../../paper_2206_06079_gb300/csrc/ohm_device.cuh"
+
+int main() {
+  int F, S;
+  long long n;
+  if (scanf("%d %d %lld", &F, &S, &n) != 3) return 1;
+  static int vox[1 << 20][3];
+  for (long long r = 0; r < n; ++r) {
+    long long a[3], b[3];
+    if (scanf("%lld %lld %lld %lld %lld %lld", &a[0], &a[1], &a[2], &b[0], &b[1], &b[2]) != 6) return 1;
+    int32_t nmaj;
+    const int M = ohm::dominant_axis(a, b, F, &nmaj);
+    const int nseg = ohm::segment_count(nmaj, S);
+    long long c = 0;
+    for (int j = 0; j < nseg; ++j) {
+      ohm::Walker w;
+      ohm::walker_init(w, a, b, F, M, (long long)j * S);
+      const bool last = j == nseg - 1;
+      int mrem = last ? INT_MAX : S - 1;
+      uint32_t mo = ohm::morton((uint32_t)(w.vx & 31), (uint32_t)(w.vy & 31), (uint32_t)(w.vz & 31));
+      for (;;) {
+        // the incrementally stepped Morton index must equal the recomputed one
+        if (mo != ohm::morton((uint32_t)(w.vx & 31), (uint32_t)(w.vy & 31), (uint32_t)(w.vz & 31))) return 2;
+        if (c < (1 << 20)) {
+          vox[c][0] = w.vx;
+          vox[c][1] = w.vy;
+          vox[c][2] = w.vz;
+        }
+        ++c;
+        if (w.total == 0) break;
+        const int axis = ohm::walker_choose(w);
+        if (axis == M) {
+          if (mrem == 0) break;
+          --mrem;
+        }
+        int32_t cc, sg;
+        ohm::walker_step(w, axis, &cc, &sg);
+        mo = ohm::morton_step(mo, ohm::morton_mask(axis), sg);
+      }
+    }
+    printf("%lld\n", c);
+    for (long long i = 0; i < c && i < (1 << 20); ++i) printf("%d %d %d\n", vox[i][0], vox[i][1], vox[i][2]);
+  }
+  return 0;
+}
