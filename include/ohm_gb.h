@@ -192,6 +192,49 @@ ohm_status ohm_map_profile(ohm_map* map, uint32_t stage_mask);
  * time in milliseconds and their number. */
 ohm_status ohm_map_profile_read(ohm_map* map, int32_t stage, double* total_ms, int64_t* launches);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free ray counting (the paper has no counterpart to this entry
+ * point).
+ *
+ * For callers that cannot call cudaMalloc when they need to integrate rays:
+ * code running while a stream is captured into a CUDA graph (allocation is not
+ * allowed there), real-time loops that must not wait on the allocator or on
+ * the synchronisation cudaFree implies, and plug-ins whose host application
+ * owns all device memory.  ohm_count_rays_noalloc walks a ray set exactly like
+ * ohm_integrate_rays (same quantisation, truncation and voxel walk) and adds
+ * each ray's per-voxel counts to two uint32 arrays the caller owns: every voxel
+ * a ray passes through gets misses += 1, the voxel holding its sample (if it
+ * has one) gets hits += 1.  Voxels outside the grid are not counted.
+ *
+ * It allocates nothing: its working memory is one statically sized device
+ * array inside the library (about 3 MB), which every GPU that loads the library
+ * holds until the process exits.  The first call on a device looks up that
+ * array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  Every call uses the calling thread's current device and
+ * shares the array: calls whose work may overlap on the GPU (unordered streams)
+ * race on it and must not be issued.  Each call clears the part that must start
+ * at zero.  All pointers must be device memory.
+ * Errors: OHM_ERR_INVALID when n > OHM_NOALLOC_MAX_RAYS, when n times the
+ * segments a ray can have (max_range / voxel_size + 2) / segment_steps + 1
+ * exceeds 4 * OHM_NOALLOC_MAX_RAYS, for bad grid parameters or host pointers;
+ * OHM_ERR_CUDA for a failed CUDA call.  Returns once the work is enqueued.
+ * ------------------------------------------------------------------------- */
+#define OHM_NOALLOC_MAX_RAYS 32768
+
+typedef struct {
+  double voxel_size;       /* voxel edge in metres */
+  double map_origin[3];    /* world position of the lower corner of voxel (0,0,0) */
+  int32_t frac_bits;       /* fixed-point fraction bits per voxel, 8..20 */
+  int32_t segment_steps;   /* ray segment length in dominant-axis steps; 0 = 64 */
+  double max_range;        /* truncation length in metres */
+  int64_t corner[3];       /* voxel index of grid cell (0,0,0) */
+  int64_t dims[3];         /* grid size in voxels; cell (x,y,z) is element x + dims[0] * (y + dims[1] * z) */
+} ohm_count_grid;
+
+ohm_status ohm_count_rays_noalloc(const ohm_count_grid* grid, const float* origins, int64_t n_origins,
+                                  const float* endpoints, const uint8_t* flags, int64_t n, uint32_t* hits,
+                                  uint32_t* misses, void* stream);
+
 /* Thread-local message describing the last failure on this thread. */
 const char* ohm_last_error(void);
 

@@ -392,6 +392,8 @@ ohm_status ohm_map_profile_read(ohm_map* map, int32_t stage, double* total_ms, i
 
 namespace ohm {
 
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
 static cudaEvent_t pooled_event(ohm_map* map) {
   if (!map->event_pool.empty()) {
     cudaEvent_t ev = map->event_pool.back();

@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include <string>
 #include <utility>
 #include <vector>
 
@@ -43,6 +44,9 @@ cudaError_t launch_query(ohm_map* map, const float* points, long long n, float* 
 cudaError_t launch_export(ohm_map* map, long long first, long long count, int32_t* keys, float* occupancy,
                           uint32_t* counts, long long* ndt, float* tsdf, cudaStream_t stream);
 int walk_blocks_per_sm();
+
+// Set the message ohm_last_error() returns on this thread.
+void set_last_error(const std::string& msg);
 
 // Stage timing helpers (no-ops unless the stage is being profiled).
 void stage_begin(ohm_map* map, int stage, cudaStream_t stream, cudaEvent_t* ev);

@@ -25,7 +25,9 @@ _STATUS_NAMES = {ERR_INVALID: "invalid argument", ERR_CAPACITY: "capacity", ERR_
 # Every symbol include/ohm_gb.h declares.
 EXPORTED = ["ohm_map_create", "ohm_map_destroy", "ohm_integrate_rays", "ohm_integrate_rays_async", "ohm_map_sync",
             "ohm_query_voxels", "ohm_map_region_count", "ohm_map_export", "ohm_map_stats", "ohm_map_profile",
-            "ohm_map_profile_read", "ohm_last_error"]
+            "ohm_map_profile_read", "ohm_last_error", "ohm_count_rays_noalloc"]
+
+NOALLOC_MAX_RAYS = 32768
 
 # Kernel stages of an integrate call (ohm_stage).
 STAGES = ["begin", "prepare", "ndt_alloc", "prepare_tsdf", "walk", "hits", "tsdf_walk", "tsdf_apply", "end"]
@@ -64,6 +66,19 @@ class CallStats(ctypes.Structure):
                                               "total_visits", "launches")]
 
 
+class CountGrid(ctypes.Structure):
+    """ohm_count_grid: a dense voxel box for ohm_count_rays_noalloc."""
+    _fields_ = [
+        ("voxel_size", ctypes.c_double),
+        ("map_origin", ctypes.c_double * 3),
+        ("frac_bits", ctypes.c_int32),
+        ("segment_steps", ctypes.c_int32),
+        ("max_range", ctypes.c_double),
+        ("corner", ctypes.c_int64 * 3),
+        ("dims", ctypes.c_int64 * 3),
+    ]
+
+
 _lib = None
 
 
@@ -99,6 +114,8 @@ def load_library(path: str = LIB_PATH):
     lib.ohm_map_profile.argtypes = [vp, ctypes.c_uint32]
     lib.ohm_map_profile_read.restype = st
     lib.ohm_map_profile_read.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
+    lib.ohm_count_rays_noalloc.restype = st
+    lib.ohm_count_rays_noalloc.argtypes = [ctypes.POINTER(CountGrid), p, i64, p, p, i64, p, p, vp]
     lib.ohm_last_error.restype = ctypes.c_char_p
     lib.ohm_last_error.argtypes = []
     _lib = lib
@@ -270,3 +287,25 @@ class Map:
                                              _ptr(out.get("counts")), _ptr(out.get("ndt")), _ptr(out.get("tsdf")),
                                              _stream_handle(stream)))
         return out
+
+
+def count_rays_noalloc(grid: dict, origins, endpoints, flags, hits, misses, stream=None):
+    """Add each ray's per-voxel hit and miss counts into the caller's dense
+    uint32 grids `hits` and `misses` (CUDA tensors of dims[0]*dims[1]*dims[2]
+    elements, x fastest) without any device allocation by the library.  All
+    inputs must be CUDA tensors.  `grid` holds voxel_size, map_origin,
+    frac_bits, segment_steps, max_range, corner and dims (see ohm_count_grid)."""
+    g = CountGrid()
+    g.voxel_size = float(grid["voxel_size"])
+    for i in range(3):
+        g.map_origin[i] = float(grid.get("map_origin", (0.0, 0.0, 0.0))[i])
+        g.corner[i] = int(grid["corner"][i])
+        g.dims[i] = int(grid["dims"][i])
+    g.frac_bits = int(grid.get("frac_bits", 16))
+    g.segment_steps = int(grid.get("segment_steps", 0))
+    g.max_range = float(grid["max_range"])
+    o = _as_points(origins, "origins")
+    e = _as_points(endpoints, "endpoints")
+    f = _as_flags(flags)
+    _check(load_library().ohm_count_rays_noalloc(ctypes.byref(g), _ptr(o), int(o.shape[0]), _ptr(e), _ptr(f),
+                                                 int(e.shape[0]), _ptr(hits), _ptr(misses), _stream_handle(stream)))

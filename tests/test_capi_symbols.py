@@ -56,7 +56,8 @@ def _c_layout(struct, fields, tmp_path):
 
 
 def test_param_structs_match_the_header(tmp_path):
-    for cls, name in ((ohm.MapParams, "ohm_map_params"), (ohm.CallStats, "ohm_call_stats")):
+    for cls, name in ((ohm.MapParams, "ohm_map_params"), (ohm.CallStats, "ohm_call_stats"),
+                      (ohm.CountGrid, "ohm_count_grid")):
         fields = [f for f, _ in cls._fields_]
         got = _c_layout(name, fields, tmp_path)
         assert got[:-1] == [getattr(cls, f).offset for f in fields], name
