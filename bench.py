@@ -192,6 +192,8 @@ def run_ours(args):
     rays_per_scan = scans[0].n
 
     pools = dict(max_regions=12288, max_ndt_regions=512) if args.profile_case else {}
+    if args.segment_steps:
+        pools["segment_steps"] = args.segment_steps
     gm = ohm.Map(**W.tunnel_params(device=local, **pools))
     stream = torch.cuda.current_stream()
 
@@ -315,7 +317,7 @@ def run_ours(args):
             "data": "synthetic (seeded tunnel lidar scans generated on the device)",
             "config": {"workload": WORKLOAD, "rays_per_scan": rays_per_scan, "scans": SCANS,
                        "layers": "occupancy+ndt", "voxel_size_m": 0.1, "max_range_m": 50.0,
-                       "segment_steps": 64, "parallelism": "replicas" if ws > 1 else "single GPU",
+                       "segment_steps": args.segment_steps or 8, "parallelism": "replicas" if ws > 1 else "single GPU",
                        "l2": "map working set per scan (~7.7k 128 KB regions) exceeds the 129 MB L2; "
                              "each step integrates a different scan"},
             "voxel_updates_per_s": total_visits / (max_ms / 1e3),
@@ -392,6 +394,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--segment-steps", type=int, default=0, help="ray segment length (0 = library default)")
     ap.add_argument("--profile-case", action="store_true",
                     help="small pools (a few GB on the device), no e2e or CPU leg: the case ncu captures")
     args = ap.parse_args()

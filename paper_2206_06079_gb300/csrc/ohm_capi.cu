@@ -62,7 +62,7 @@ long long next_pow2(long long x) {
 void free_map(ohm_map* m) {
   if (!m) return;
   ohm::DeviceMap& d = m->d;
-  void* ptrs[] = {d.hkeys, d.hslots, d.region_count, d.region_coords, d.occ, d.counts, d.ndt_slot, d.ndt_count,
+  void* ptrs[] = {d.htab, d.region_count, d.region_coords, d.occ, d.counts, d.ndt_slot, d.ndt_count,
                   d.ndt, d.tsdf, d.tsdf_cnt, d.tsdf_sum, d.status, d.calls, d.rays, d.trays, d.segs, d.touched,
                   m->stage_origins, m->stage_endpoints, m->stage_flags};
   for (void* p : ptrs)
@@ -136,7 +136,7 @@ ohm_status ohm_map_create(const ohm_map_params* params, ohm_map** out) {
   if (!params || !out) return fail(OHM_ERR_INVALID, "create: NULL argument");
   *out = nullptr;
   ohm_map_params p = *params;
-  if (p.segment_steps == 0) p.segment_steps = 64;
+  if (p.segment_steps == 0) p.segment_steps = 8;
   if (!(p.voxel_size > 0.0) || !std::isfinite(p.voxel_size)) return fail(OHM_ERR_INVALID, "create: voxel_size must be > 0");
   if (p.frac_bits < 8 || p.frac_bits > 20) return fail(OHM_ERR_INVALID, "create: frac_bits must be in [8, 20]");
   const uint32_t all = OHM_LAYER_OCCUPANCY | OHM_LAYER_NDT | OHM_LAYER_TSDF | OHM_LAYER_COUNTS;
@@ -180,8 +180,7 @@ ohm_status ohm_map_create(const ohm_map_params* params, ohm_map** out) {
   auto chk = [&](cudaError_t r) {
     if (e == cudaSuccess && r != cudaSuccess) e = r;
   };
-  chk(alloc(&d.hkeys, H, 0xFF));
-  chk(alloc(&d.hslots, H, 0xFF));
+  chk(alloc(&d.htab, H, 0xFF));  // key -1 (empty), slot -1
   chk(alloc(&d.region_count, 1, 0));
   chk(alloc(&d.ndt_count, 1, 0));
   chk(alloc(&d.status, 1, 0));

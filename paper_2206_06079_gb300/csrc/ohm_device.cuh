@@ -26,12 +26,13 @@ constexpr int kStatusCasLimit = 16;  // a CAS loop gave up (a library bug)
 
 // Ray record written by the occupancy prepare kernel.
 struct __align__(16) RayRec {
-  long long a[3];   // walk start (sensor origin), fixed point
-  long long b[3];   // walk end (sample or truncation point), fixed point
-  int32_t flags;    // kRayValid | kRaySample
-  int32_t nseg;     // number of segments
+  long long a[3];          // walk start (sensor origin), fixed point
+  long long b[3];          // walk end (sample or truncation point), fixed point
+  unsigned long long inv;  // reciprocal64 of the dominant axis' |b - a| (0 if unset)
+  int32_t flags;           // kRayValid | kRaySample | dominant axis << kRayAxisShift
+  int32_t nseg;            // number of segments
 };
-constexpr int32_t kRayValid = 1, kRaySample = 2;
+constexpr int32_t kRayValid = 1, kRaySample = 2, kRayAxisShift = 4;
 
 // Ray record written by the TSDF prepare kernel: the walk covers the band
 // [max(0, d - tau), d + tau] of the ray from the sensor to the sample e.
@@ -56,9 +57,8 @@ struct CallCounters {
 
 // Everything a kernel needs, passed by value.
 struct DeviceMap {
-  // region hash table: key -> pool slot (Sec. III-A)
-  long long* hkeys;
-  int32_t* hslots;
+  // region hash table: key -> pool slot (Sec. III-A); entry = (key, slot)
+  longlong2* htab;
   uint32_t hmask;
   int32_t max_probe;
   // region pool
@@ -124,13 +124,14 @@ __device__ __forceinline__ uint32_t hash_key(long long k) {
   return (uint32_t)x;
 }
 
-// Pool slot of a region, or -1.  Read-only use of the table.
+// Pool slot of a region, or -1.  Read-only use of the table: one 16-byte
+// load per probe brings the key and its slot together.
 __device__ __forceinline__ int32_t find_region(const DeviceMap& m, long long key) {
   uint32_t h = hash_key(key) & m.hmask;
   for (int i = 0; i < m.max_probe; ++i) {
-    long long k = m.hkeys[h];
-    if (k == key) return m.hslots[h];
-    if (k == kEmptyKey) return -1;
+    const longlong2 e = m.htab[h];
+    if (e.x == key) return (int32_t)e.y;
+    if (e.x == kEmptyKey) return -1;
     h = (h + 1) & m.hmask;
   }
   return -1;
@@ -138,19 +139,21 @@ __device__ __forceinline__ int32_t find_region(const DeviceMap& m, long long key
 
 // Insert a region if absent.  The inserting thread takes a pool slot; other
 // threads only learn that the key exists (slots are read after this kernel).
+// The first probe may read a stale cached entry: a key once written never
+// changes within a call, and a stale "empty" only sends us to the CAS below.
 __device__ inline void insert_region(const DeviceMap& m, int rx, int ry, int rz) {
   const long long key = pack_region(rx, ry, rz);
   uint32_t h = hash_key(key) & m.hmask;
   for (int i = 0; i < m.max_probe; ++i) {
-    long long k = *(volatile long long*)&m.hkeys[h];
+    long long k = m.htab[h].x;
     if (k == key) return;
     if (k == kEmptyKey) {
-      long long prev = (long long)atomicCAS((unsigned long long*)&m.hkeys[h], (unsigned long long)kEmptyKey,
+      long long prev = (long long)atomicCAS((unsigned long long*)&m.htab[h].x, (unsigned long long)kEmptyKey,
                                             (unsigned long long)key);
       if (prev == kEmptyKey) {
         int32_t s = atomicAdd(m.region_count, 1);
         if (s < m.max_regions) {
-          m.hslots[h] = s;
+          m.htab[h].y = s;
           m.region_coords[3 * s + 0] = rx;
           m.region_coords[3 * s + 1] = ry;
           m.region_coords[3 * s + 2] = rz;
@@ -255,20 +258,51 @@ __host__ __device__ __forceinline__ int dominant_axis(const long long a[3], cons
   return M;
 }
 
+// High 64 bits of the 128-bit product x * y.
+__host__ __device__ __forceinline__ unsigned long long umulhi64(unsigned long long x, unsigned long long y) {
+#ifdef __CUDA_ARCH__
+  return __umul64hi(x, y);
+#else
+  return (unsigned long long)(((unsigned __int128)x * y) >> 64);
+#endif
+}
+
+// Reciprocal of a divisor d >= 1 for div_by_inv: floor((2^64 - 1) / d).
+__host__ __device__ __forceinline__ unsigned long long reciprocal64(unsigned long long d) {
+  return d ? ~0ULL / d : 0ULL;
+}
+
+// floor(x / d) for 0 <= x < 2^63 and d >= 1, given inv = reciprocal64(d).
+// inv <= 2^64 / d gives q = floor(x inv / 2^64) <= x / d, and
+// inv >= 2^64 / d - 1 gives x inv / 2^64 >= x / d - x / 2^64 > x / d - 1, so
+// q is floor(x / d) or one less; one remainder test makes it exact.
+__host__ __device__ __forceinline__ unsigned long long div_by_inv(unsigned long long x, unsigned long long d,
+                                                                unsigned long long inv) {
+  unsigned long long q = umulhi64(x, inv);
+  if (x - q * d >= d) q += 1;
+  return q;
+}
+
 // Crossings of a non-dominant axis (distance d0k to its first boundary,
 // speed Ak) that come before the K-th step of the dominant axis M (distance
 // d0M, speed AM), in walk order: crossing i precedes it when
 // (d0k + i U) / Ak < (d0M + (K-1) U) / AM, or the two are equal and the axis
 // is above M (ties step z, then y, then x).  Capped at the axis' total ntot.
+// Division by U AM is done as floor(floor(x / U) / AM); inv_am is
+// reciprocal64(AM), or 0 to divide directly.
 __host__ __device__ __forceinline__ long long crossings_before(long long d0k, long long Ak, long long d0M, long long AM,
-                                                      long long U, long long K, bool above_major, int32_t ntot) {
-  long long R = (d0M + (K - 1) * U) * Ak - d0k * AM;
-  unsigned long long den = (unsigned long long)(U * AM);
+                                                              int F, long long K, bool above_major, int32_t ntot,
+                                                              unsigned long long inv_am) {
+  const long long U = 1LL << F;
+  const long long R = (d0M + (K - 1) * U) * Ak - d0k * AM;
   long long c;
-  if (!above_major)
-    c = R > 0 ? (long long)(((unsigned long long)R - 1ULL) / den) + 1 : 0;
-  else
-    c = R >= 0 ? (long long)((unsigned long long)R / den) + 1 : 0;
+  if (!above_major ? R <= 0 : R < 0) {
+    c = 0;
+  } else {
+    const unsigned long long x = ((unsigned long long)(above_major ? R : R - 1)) >> F;
+    const unsigned long long q = inv_am ? div_by_inv(x, (unsigned long long)AM, inv_am) : x / (unsigned long long)AM;
+    c = (long long)q + 1;
+  }
   return c < ntot ? c : (long long)ntot;
 }
 
@@ -277,8 +311,9 @@ __host__ __device__ __forceinline__ void walker_exhaust_y(Walker& w) { w.cxy = -
 __host__ __device__ __forceinline__ void walker_exhaust_z(Walker& w) { w.cxz = -kBig; w.cyz = -kBig; }
 
 // State of the walk from a to b right after K steps along the dominant axis M
-// (K = 0: the start).
-__host__ __device__ inline void walker_init(Walker& w, const long long a[3], const long long b[3], int F, int M, long long K) {
+// (K = 0: the start).  inv_am: reciprocal64(|b_M - a_M|), or 0.
+__host__ __device__ inline void walker_init(Walker& w, const long long a[3], const long long b[3], int F, int M, long long K,
+                                            unsigned long long inv_am = 0) {
   const long long U = 1LL << F;
   long long A[3], d0[3], cnt[3];
   int32_t ntot[3], sgn[3], v0[3];
@@ -303,7 +338,7 @@ __host__ __device__ inline void walker_init(Walker& w, const long long a[3], con
     else if (k == M)
       cnt[k] = K;
     else
-      cnt[k] = crossings_before(d0[k], A[k], d0M, AM, U, K, k > M, ntot[k]);
+      cnt[k] = crossings_before(d0[k], A[k], d0M, AM, F, K, k > M, ntot[k], inv_am);
   }
   long long dist[3];
 #pragma unroll
@@ -335,34 +370,26 @@ __host__ __device__ __forceinline__ int walker_choose(const Walker& w) {
 }
 
 // Take one step along `axis`; returns the new coordinate along that axis and
-// its step sign through *coord / *sign.
+// its step sign through *coord / *sign.  Written with selects so that lanes
+// stepping different axes do not diverge.  Re-pinning the differences of an
+// exhausted axis on every step is harmless: they only ever mean "never first".
 __host__ __device__ __forceinline__ void walker_step(Walker& w, int axis, int32_t* coord, int32_t* sign) {
-  if (axis == 0) {
-    w.cxy += w.ub;
-    w.cxz += w.uc;
-    w.vx += w.sx;
-    w.nx -= 1;
-    if (w.nx == 0) walker_exhaust_x(w);
-    *coord = w.vx;
-    *sign = w.sx;
-  } else if (axis == 1) {
-    w.cxy -= w.ua;
-    w.cyz += w.uc;
-    w.vy += w.sy;
-    w.ny -= 1;
-    if (w.ny == 0) walker_exhaust_y(w);
-    *coord = w.vy;
-    *sign = w.sy;
-  } else {
-    w.cxz -= w.ua;
-    w.cyz -= w.ub;
-    w.vz += w.sz;
-    w.nz -= 1;
-    if (w.nz == 0) walker_exhaust_z(w);
-    *coord = w.vz;
-    *sign = w.sz;
-  }
+  const bool bx = axis == 0, by = axis == 1, bz = axis == 2;
+  w.cxy += bx ? w.ub : (by ? -w.ua : 0LL);
+  w.cxz += bx ? w.uc : (bz ? -w.ua : 0LL);
+  w.cyz += by ? w.uc : (bz ? -w.ub : 0LL);
+  w.vx += bx ? w.sx : 0;
+  w.vy += by ? w.sy : 0;
+  w.vz += bz ? w.sz : 0;
+  w.nx -= bx ? 1 : 0;
+  w.ny -= by ? 1 : 0;
+  w.nz -= bz ? 1 : 0;
   w.total -= 1;
+  if (w.nx == 0) walker_exhaust_x(w);
+  if (w.ny == 0) walker_exhaust_y(w);
+  if (w.nz == 0) walker_exhaust_z(w);
+  *coord = bx ? w.vx : (by ? w.vy : w.vz);
+  *sign = bx ? w.sx : (by ? w.sy : w.sz);
 }
 
 __host__ __device__ __forceinline__ uint32_t morton_mask(int axis) {

@@ -143,6 +143,7 @@ __global__ void __launch_bounds__(kBlock) k_prepare_occ(DeviceMap m, CallArgs ar
   RayRec r;
   r.flags = 0;
   r.nseg = 0;
+  r.inv = 0;
   if (active) {
     float o[3], e[3];
     uint8_t flag;
@@ -168,9 +169,11 @@ __global__ void __launch_bounds__(kBlock) k_prepare_occ(DeviceMap m, CallArgs ar
         r.b[k] = qe[k];
       }
       int32_t nmaj;
-      dominant_axis(qo, qe, F, &nmaj);
+      const int M = dominant_axis(qo, qe, F, &nmaj);
       nseg = (unsigned int)segment_count(nmaj, m.seg_steps);
-      r.flags = kRayValid | (sample ? kRaySample : 0);
+      const long long am = sel3(M, qe[0] - qo[0], qe[1] - qo[1], qe[2] - qo[2]);
+      r.inv = reciprocal64((unsigned long long)(am < 0 ? -am : am));
+      r.flags = kRayValid | (sample ? kRaySample : 0) | (M << kRayAxisShift);
       r.nseg = (int32_t)nseg;
       long long l1 = 0;
 #pragma unroll
@@ -253,12 +256,11 @@ __global__ void __launch_bounds__(kBlock, 2) k_walk_miss(DeviceMap m) {
        si += (long long)gridDim.x * blockDim.x) {
     const int2 sg = m.segs[si];
     const RayRec r = m.rays[sg.x];
-    int32_t nmaj;
-    const int M = dominant_axis(r.a, r.b, F, &nmaj);
+    const int M = (r.flags >> kRayAxisShift) & 3;
     const bool last = sg.y == r.nseg - 1;
     const bool sample = (r.flags & kRaySample) != 0;
     Walker w;
-    walker_init(w, r.a, r.b, F, M, (long long)sg.y * S);
+    walker_init(w, r.a, r.b, F, M, (long long)sg.y * S, r.inv);
     int32_t mrem = last ? INT_MAX : S - 1;
     int32_t slot = region_slot_of(m, w.vx, w.vy, w.vz);
     if (slot < 0) {
@@ -495,13 +497,9 @@ __global__ void k_end(DeviceMap m) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   for (long long h = t0; h <= (long long)m.hmask; h += stride) {
-    const long long k = m.hkeys[h];
-    if (k == kEmptyKey || k == kTombKey) continue;
-    const int32_t s = m.hslots[h];
-    if (s < 0 || s >= rs) {
-      m.hkeys[h] = kTombKey;
-      m.hslots[h] = -1;
-    }
+    const longlong2 e = m.htab[h];
+    if (e.x == kEmptyKey || e.x == kTombKey) continue;
+    if (e.y < 0 || e.y >= rs) m.htab[h] = make_longlong2(kTombKey, -1);
   }
   for (long long s = t0; s < m.max_regions; s += stride) {
     const int32_t v = m.ndt_slot[s];

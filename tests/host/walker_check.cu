@@ -10,9 +10,10 @@
 
 #include "../../paper_2206_06079_gb300/csrc/ohm_device.cuh"
 
-int main() {
+int main(int argc, char** argv) {
   int F, S;
   long long n;
+  const bool use_inv = argc > 1;  // jump into segments with the reciprocal division
   if (scanf("%d %d %lld", &F, &S, &n) != 3) return 1;
   static int vox[1 << 20][3];
   for (long long r = 0; r < n; ++r) {
@@ -24,7 +25,9 @@ int main() {
     long long c = 0;
     for (int j = 0; j < nseg; ++j) {
       ohm::Walker w;
-      ohm::walker_init(w, a, b, F, M, (long long)j * S);
+      const long long am = b[M] - a[M];
+      const unsigned long long inv = use_inv ? ohm::reciprocal64((unsigned long long)(am < 0 ? -am : am)) : 0ULL;
+      ohm::walker_init(w, a, b, F, M, (long long)j * S, inv);
       const bool last = j == nseg - 1;
       int mrem = last ? INT_MAX : S - 1;
       uint32_t mo = ohm::morton((uint32_t)(w.vx & 31), (uint32_t)(w.vy & 31), (uint32_t)(w.vz & 31));

@@ -21,9 +21,10 @@ def checker(tmp_path_factory):
     return exe
 
 
-def _run(exe, rays, F=16, S=64):
+def _run(exe, rays, F=16, S=64, inv=False):
     lines = ["%d %d %d" % (F, S, len(rays))] + ["%d %d %d %d %d %d" % tuple(int(v) for v in (*a, *b)) for a, b in rays]
-    out = subprocess.run([exe], input="\n".join(lines) + "\n", capture_output=True, text=True)
+    args = [exe, "inv"] if inv else [exe]
+    out = subprocess.run(args, input="\n".join(lines) + "\n", capture_output=True, text=True)
     assert out.returncode == 0, "walker check exited %d (Morton mismatch = 2)" % out.returncode
     tok = out.stdout.split()
     res, i = [], 0
@@ -52,11 +53,12 @@ def _rays(seed, n, lattice):
     return out
 
 
-@pytest.mark.parametrize("S", [1, 2, 5, 64, 1 << 20])
+@pytest.mark.parametrize("S", [1, 2, 5, 8, 64, 1 << 20])
 @pytest.mark.parametrize("lattice", [False, True])
-def test_device_walker_matches_oracle(checker, S, lattice):
+@pytest.mark.parametrize("inv", [False, True])
+def test_device_walker_matches_oracle(checker, S, lattice, inv):
     rays = _rays(100 + S + lattice, 150, lattice)
-    got = _run(checker, rays, S=S)
+    got = _run(checker, rays, S=S, inv=inv)
     for (a, b), g in zip(rays, got):
         assert np.array_equal(g, oracle.walk(a, b)), (a, b)
 
@@ -65,8 +67,8 @@ def test_golden_ties_through_device_walker(checker):
     import json
     spec = json.load(open(os.path.join(HERE, "golden", "walk_ties.json")))
     rays = [(np.array(c["a"]), np.array(c["b"])) for c in spec["cases"]]
-    for S in (1, 64):
-        for c, g in zip(spec["cases"], _run(checker, rays, S=S)):
+    for S, inv in ((1, False), (1, True), (64, True)):
+        for c, g in zip(spec["cases"], _run(checker, rays, S=S, inv=inv)):
             assert g.tolist() == c["visits"], c["name"]
 
 
