@@ -243,10 +243,16 @@ __device__ __forceinline__ void logodds_retry(const DeviceMap& m, unsigned int* 
 // write of each voxel in global memory.  So a thread walks kWalkBatch voxels
 // ahead, then issues all their loads at once, then all their CASes at once,
 // keeping that many memory operations in flight instead of one.
-constexpr int kWalkBatch = 8;
+#ifndef OHM_WALK_BATCH
+#define OHM_WALK_BATCH 8
+#endif
+#ifndef OHM_WALK_MIN_BLOCKS
+#define OHM_WALK_MIN_BLOCKS 2
+#endif
+constexpr int kWalkBatch = OHM_WALK_BATCH;
 
 template <bool kOcc, bool kCounts>
-__global__ void __launch_bounds__(kBlock, 2) k_walk_miss(DeviceMap m) {
+__global__ void __launch_bounds__(kBlock, OHM_WALK_MIN_BLOCKS) k_walk_miss(DeviceMap m) {
   if (latched(m)) return;
   const long long nseg = (long long)m.calls->segments;
   const int F = m.frac_bits;

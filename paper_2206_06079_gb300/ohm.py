@@ -12,7 +12,9 @@ import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_lib", "libohm_gb.so")
+# OHM_GB_LIB may point at a build of the same sources with other compile-time
+# tile parameters (used when tuning); by default the in-tree build is loaded.
+LIB_PATH = os.environ.get("OHM_GB_LIB") or os.path.join(_HERE, "_lib", "libohm_gb.so")
 
 OK, ERR_INVALID, ERR_CAPACITY, ERR_CUDA, ERR_PROBE_LIMIT, ERR_UNSUPPORTED = range(6)
 LAYER_OCCUPANCY, LAYER_NDT, LAYER_TSDF, LAYER_COUNTS = 1, 2, 4, 8
