@@ -77,7 +77,7 @@ typedef struct {
   int64_t max_ndt_regions; /* capacity of the NDT layer pool (regions holding samples) */
   int64_t max_rays;        /* largest ray count accepted by one integrate call */
   int32_t segment_steps;   /* rays are split every this many voxel steps along their
-                              dominant axis (Sec. III-B ray segments); 0 = default */
+                              dominant axis (Sec. III-B ray segments); 0 = 4 */
   int32_t device;          /* CUDA device ordinal */
 } ohm_map_params;
 

@@ -12,7 +12,6 @@ constexpr int kRegionShift = 5;                  // 32 voxels per region edge (S
 constexpr int kRegionVoxels = 1 << (3 * kRegionShift);
 constexpr long long kEmptyKey = -1;              // never a packed key (packed keys are < 2^63)
 constexpr long long kTombKey = -2;               // a key removed by a rolled-back call
-constexpr long long kBig = 1LL << 62;            // "never first" time difference, see Walker
 
 constexpr uint32_t kLayerOcc = 1, kLayerNdt = 2, kLayerTsdf = 4, kLayerCounts = 8;
 constexpr uint8_t kFlagNoReturn = 1;
@@ -212,10 +211,15 @@ __host__ __device__ __forceinline__ uint32_t morton_step(uint32_t m, uint32_t ma
 //     C_xy = dist_x A_y - dist_y A_x   (t_x < t_y  <=>  C_xy < 0)
 //     C_xz = dist_x A_z - dist_z A_x
 //     C_yz = dist_y A_z - dist_z A_y
-// which change by constants when an axis steps (dist_k grows by U = 2^F).  An
-// axis with no steps left has its differences pinned to +-2^62, so it is never
-// chosen and never blocks the others; magnitudes stay below 2^61 because every
-// ray is shorter than 2^30 fixed-point units (checked when the map is made).
+// which change by constants when an axis steps (dist_k grows by U = 2^F).
+// Magnitudes stay below 2^61 because every ray is shorter than 2^30
+// fixed-point units (checked when the map is made).
+//
+// An axis with no steps left ("exhausted") keeps exact differences: its next
+// boundary lies at or beyond b, so t >= 1 while every remaining crossing has
+// t <= 1.  It can therefore only be picked on a tie at t = 1, when every axis
+// with steps left also sits at t = 1; the highest such axis steps then, which
+// is what the tie order prescribes among them.
 //
 // Segments (Sec. III-B "breaking long rays into several segments"): the walk
 // of one ray is split by the number K of steps taken along its dominant axis
@@ -306,10 +310,6 @@ __host__ __device__ __forceinline__ long long crossings_before(long long d0k, lo
   return c < ntot ? c : (long long)ntot;
 }
 
-__host__ __device__ __forceinline__ void walker_exhaust_x(Walker& w) { w.cxy = kBig; w.cxz = kBig; }
-__host__ __device__ __forceinline__ void walker_exhaust_y(Walker& w) { w.cxy = -kBig; w.cyz = kBig; }
-__host__ __device__ __forceinline__ void walker_exhaust_z(Walker& w) { w.cxz = -kBig; w.cyz = -kBig; }
-
 // State of the walk from a to b right after K steps along the dominant axis M
 // (K = 0: the start).  inv_am: reciprocal64(|b_M - a_M|), or 0.
 __host__ __device__ inline void walker_init(Walker& w, const long long a[3], const long long b[3], int F, int M, long long K,
@@ -359,20 +359,19 @@ __host__ __device__ inline void walker_init(Walker& w, const long long a[3], con
   w.cxz = dist[0] * A[2] - dist[2] * A[0];
   w.cyz = dist[1] * A[2] - dist[2] * A[1];
   w.total = w.nx + w.ny + w.nz;
-  if (w.nx == 0) walker_exhaust_x(w);
-  if (w.ny == 0) walker_exhaust_y(w);
-  if (w.nz == 0) walker_exhaust_z(w);
 }
 
 // Axis of the next step (requires w.total > 0).
 __host__ __device__ __forceinline__ int walker_choose(const Walker& w) {
-  return (w.cxy < 0 && w.cxz < 0) ? 0 : ((w.cxy >= 0 && w.cyz < 0) ? 1 : 2);
+  int axis = (w.cxy < 0 && w.cxz < 0) ? 0 : ((w.cxy >= 0 && w.cyz < 0) ? 1 : 2);
+  const int32_t left = axis == 0 ? w.nx : (axis == 1 ? w.ny : w.nz);
+  if (left == 0) axis = w.nz > 0 ? 2 : (w.ny > 0 ? 1 : 0);  // a tie at t = 1 (see above)
+  return axis;
 }
 
 // Take one step along `axis`; returns the new coordinate along that axis and
 // its step sign through *coord / *sign.  Written with selects so that lanes
-// stepping different axes do not diverge.  Re-pinning the differences of an
-// exhausted axis on every step is harmless: they only ever mean "never first".
+// stepping different axes do not diverge.
 __host__ __device__ __forceinline__ void walker_step(Walker& w, int axis, int32_t* coord, int32_t* sign) {
   const bool bx = axis == 0, by = axis == 1, bz = axis == 2;
   w.cxy += bx ? w.ub : (by ? -w.ua : 0LL);
@@ -385,9 +384,6 @@ __host__ __device__ __forceinline__ void walker_step(Walker& w, int axis, int32_
   w.ny -= by ? 1 : 0;
   w.nz -= bz ? 1 : 0;
   w.total -= 1;
-  if (w.nx == 0) walker_exhaust_x(w);
-  if (w.ny == 0) walker_exhaust_y(w);
-  if (w.nz == 0) walker_exhaust_z(w);
   *coord = bx ? w.vx : (by ? w.vy : w.vz);
   *sign = bx ? w.sx : (by ? w.sy : w.sz);
 }

@@ -119,6 +119,12 @@ __device__ __forceinline__ int32_t region_slot_of(const DeviceMap& m, int32_t vx
   return find_region(m, pack_region(vx >> kRegionShift, vy >> kRegionShift, vz >> kRegionShift));
 }
 
+// The same lookup kept out of line: the walk kernels call it from every slot
+// of an unrolled batch, and one shared copy keeps the instruction cache warm.
+__device__ __noinline__ int32_t region_slot_call(const DeviceMap& m, int32_t vx, int32_t vy, int32_t vz) {
+  return region_slot_of(m, vx, vy, vz);
+}
+
 __device__ __forceinline__ uint32_t local_morton(int32_t vx, int32_t vy, int32_t vz) {
   const int32_t mask = (1 << kRegionShift) - 1;
   return morton((uint32_t)(vx & mask), (uint32_t)(vy & mask), (uint32_t)(vz & mask));
@@ -221,7 +227,7 @@ __global__ void __launch_bounds__(kBlock) k_ndt_alloc(DeviceMap m, long long n) 
 
 // Retry a clamped log-odds CAS whose first attempt found `cur` instead of
 // the value it expected (see logodds_update).
-__device__ __forceinline__ void logodds_retry(const DeviceMap& m, unsigned int* u, unsigned int cur, float delta) {
+__device__ __noinline__ void logodds_retry(const DeviceMap& m, unsigned int* u, unsigned int cur, float delta) {
   for (int it = 0; it < 256; ++it) {
     const float l = __uint_as_float(cur);
     const float l0 = (l != l) ? 0.0f : l;
@@ -244,10 +250,10 @@ __device__ __forceinline__ void logodds_retry(const DeviceMap& m, unsigned int* 
 // ahead, then issues all their loads at once, then all their CASes at once,
 // keeping that many memory operations in flight instead of one.
 #ifndef OHM_WALK_BATCH
-#define OHM_WALK_BATCH 8
+#define OHM_WALK_BATCH 4
 #endif
 #ifndef OHM_WALK_MIN_BLOCKS
-#define OHM_WALK_MIN_BLOCKS 2
+#define OHM_WALK_MIN_BLOCKS 4
 #endif
 constexpr int kWalkBatch = OHM_WALK_BATCH;
 
@@ -304,7 +310,7 @@ __global__ void __launch_bounds__(kBlock, OHM_WALK_MIN_BLOCKS) k_walk_miss(Devic
         walker_step(w, axis, &c, &s);
         mo = morton_step(mo, morton_mask(axis), s);
         if ((c & ((1 << kRegionShift) - 1)) == (s > 0 ? 0 : (1 << kRegionShift) - 1)) {
-          slot = region_slot_of(m, w.vx, w.vy, w.vz);
+          slot = region_slot_call(m, w.vx, w.vy, w.vz);
           if (slot < 0) {
             atomicOr(m.status, kStatusMissing);
             done = true;
