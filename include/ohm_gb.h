@@ -193,6 +193,52 @@ ohm_status ohm_map_profile(ohm_map* map, uint32_t stage_mask);
 ohm_status ohm_map_profile_read(ohm_map* map, int32_t stage, double* total_ms, int64_t* launches);
 
 /* ---------------------------------------------------------------------------
+ * Batched integration of many maps (no counterpart in the paper, which
+ * integrates one ray set into one map at a time).
+ *
+ * A batch groups up to OHM_BATCH_MAX_MAPS independent maps on one device.
+ * ohm_batch_integrate integrates one ray set into each map with one kernel
+ * launch per stage for all maps together, so small and uneven ray sets share
+ * the GPU instead of running one after another.  Per map the result is exactly
+ * that of ohm_integrate_rays_async on the same rays (same order semantics,
+ * same all-or-nothing rule per map).  With use_graph != 0 the first call
+ * captures the step into a CUDA graph and later calls replay it; the stream
+ * must then be a created stream, not the legacy default stream.
+ * ------------------------------------------------------------------------- */
+#define OHM_BATCH_MAX_MAPS 32
+
+typedef struct ohm_batch ohm_batch;
+
+/* Group n_maps distinct maps (same device) into a batch.  The maps stay owned
+ * by the caller and must outlive the batch. */
+ohm_status ohm_batch_create(ohm_map* const* maps, int32_t n_maps, ohm_batch** out);
+
+/* Free the batch (not its maps).  NULL is ignored. */
+void ohm_batch_destroy(ohm_batch* batch);
+
+/* Tile parameters of later steps: segment_steps (ray segment length in
+ * dominant-axis steps, applied to every map; 0 = unchanged) and the walk
+ * kernel's blocks per SM (0 = unchanged).  Results do not depend on them.
+ * Drops the captured graph.  Synchronises the device. */
+ohm_status ohm_batch_tune(ohm_batch* batch, int32_t segment_steps, int32_t walk_blocks_per_sm);
+
+/* One step: for map i, n[i] rays (0 = no rays this step) with n_origins[i]
+ * origins (1 or n[i]) at origins[i], endpoints at endpoints[i] and flags at
+ * flags[i] (flags or flags[i] may be NULL).  All ray arrays are device memory
+ * and must stay valid until the stream has passed the step.  The small host
+ * arrays are copied before the call returns.  Device-side failures are latched
+ * per map and reported by ohm_batch_sync. */
+ohm_status ohm_batch_integrate(ohm_batch* batch, const float* const* origins, const int64_t* n_origins,
+                               const float* const* endpoints, const uint8_t* const* flags, const int64_t* n,
+                               int32_t use_graph, void* stream);
+
+/* Wait for `stream`; return (and clear) the first failure latched by any map. */
+ohm_status ohm_batch_sync(ohm_batch* batch, void* stream);
+
+/* Kernels launched through this batch, and graph launches among the steps. */
+ohm_status ohm_batch_stats(ohm_batch* batch, int64_t* kernel_launches, int64_t* graph_launches);
+
+/* ---------------------------------------------------------------------------
  * Allocation-free ray counting (the paper has no counterpart to this entry
  * point).
  *

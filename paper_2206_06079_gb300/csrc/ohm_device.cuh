@@ -6,6 +6,13 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+// Loop unrolling hint for code compiled for both host and device.
+#ifdef __CUDA_ARCH__
+#define OHM_UNROLL _Pragma("unroll")
+#else
+#define OHM_UNROLL
+#endif
+
 namespace ohm {
 
 constexpr int kRegionShift = 5;                  // 32 voxels per region edge (Sec. III-B: 3.2 m at 0.1 m)
@@ -317,7 +324,7 @@ __host__ __device__ inline void walker_init(Walker& w, const long long a[3], con
   const long long U = 1LL << F;
   long long A[3], d0[3], cnt[3];
   int32_t ntot[3], sgn[3], v0[3];
-#pragma unroll
+OHM_UNROLL
   for (int k = 0; k < 3; ++k) {
     long long delta = b[k] - a[k];
     A[k] = delta < 0 ? -delta : delta;
@@ -331,7 +338,7 @@ __host__ __device__ inline void walker_init(Walker& w, const long long a[3], con
   }
   const long long d0M = sel3(M, d0[0], d0[1], d0[2]);
   const long long AM = sel3(M, A[0], A[1], A[2]);
-#pragma unroll
+OHM_UNROLL
   for (int k = 0; k < 3; ++k) {
     if (K == 0)
       cnt[k] = 0;
@@ -341,7 +348,7 @@ __host__ __device__ inline void walker_init(Walker& w, const long long a[3], con
       cnt[k] = crossings_before(d0[k], A[k], d0M, AM, F, K, k > M, ntot[k], inv_am);
   }
   long long dist[3];
-#pragma unroll
+OHM_UNROLL
   for (int k = 0; k < 3; ++k) dist[k] = d0[k] + cnt[k] * U;
   w.vx = v0[0] + (int32_t)(sgn[0] * cnt[0]);
   w.vy = v0[1] + (int32_t)(sgn[1] * cnt[1]);

@@ -1,0 +1,492 @@
+// Per-item device functions of the ray-integration kernels (Sec. III-B,
+// III-C of arxiv 2206.06079, re-designed for sm_103a).  The single-map
+// kernels (ohm_integrate.cu) and the multi-map batch kernels (ohm_batch.cu)
+// are thin loops around these.
+#pragma once
+
+#include <climits>
+
+#include "ohm_host.h"
+
+namespace ohm {
+
+constexpr int kBlock = 256;
+
+__device__ __forceinline__ bool latched(const DeviceMap& m) { return *(volatile int32_t*)m.status != 0; }
+
+// Clamped log-odds update of one voxel (Eq. 2 with the clamp of Sec. II-B):
+// l <- min(max(l0 + delta, l_min), l_max), l0 = 0 for an unknown (NaN) voxel.
+// Concurrent updates of one voxel are serialised by compare-and-swap; within
+// a kernel all updates of a voxel use the same delta, so the result does not
+// depend on their order.  The loop is bounded: every failed CAS means another
+// thread advanced the value one step toward its clamp.
+__device__ __forceinline__ void logodds_update(const DeviceMap& m, float* p, float delta) {
+  unsigned int* u = reinterpret_cast<unsigned int*>(p);
+  unsigned int old = *u;
+  for (int it = 0; it < 256; ++it) {
+    const float l = __uint_as_float(old);
+    const float l0 = (l != l) ? 0.0f : l;
+    const float nv = fminf(fmaxf(__fadd_rn(l0, delta), m.l_min), m.l_max);
+    const unsigned int nb = __float_as_uint(nv);
+    if (nb == old) return;
+    const unsigned int prev = atomicCAS(u, old, nb);
+    if (prev == old) return;
+    old = prev;
+  }
+  atomicOr(m.status, kStatusCasLimit);
+}
+
+// Quantise a ray, returns false when it is skipped (non-finite coordinate or
+// a point beyond the fixed-point range).
+__device__ __forceinline__ bool quantise_ray(const DeviceMap& m, const float o[3], const float e[3], long long qo[3],
+                                             long long qe[3]) {
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    ok = ok && isfinite(o[k]) && isfinite(e[k]);
+    ok = ok && quantise(o[k], m.origin[k], m.scale, &qo[k]);
+    ok = ok && quantise(e[k], m.origin[k], m.scale, &qe[k]);
+  }
+  return ok;
+}
+
+// |qe - qo| in fixed-point units, double, fixed evaluation order.
+__device__ __forceinline__ double ray_length(const long long qo[3], const long long qe[3], double d[3]) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) d[k] = (double)(qe[k] - qo[k]);
+  double l2 = __dmul_rn(d[0], d[0]);
+  l2 = __dadd_rn(l2, __dmul_rn(d[1], d[1]));
+  l2 = __dadd_rn(l2, __dmul_rn(d[2], d[2]));
+  return __dsqrt_rn(l2);
+}
+
+__device__ __forceinline__ bool in_extent(const long long q[3], int F) {
+  const long long lim = 1LL << 24;
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    long long v = q[k] >> F;
+    ok = ok && v > -lim && v < lim;
+  }
+  return ok;
+}
+
+__device__ __forceinline__ void load_ray(const CallArgs& a, long long i, float o[3], float e[3], uint8_t* flag) {
+  const long long oi = a.n_origins == 1 ? 0 : i;
+  o[0] = a.origins[3 * oi + 0];
+  o[1] = a.origins[3 * oi + 1];
+  o[2] = a.origins[3 * oi + 2];
+  e[0] = a.endpoints[3 * i + 0];
+  e[1] = a.endpoints[3 * i + 1];
+  e[2] = a.endpoints[3 * i + 2];
+  *flag = a.flags ? a.flags[i] : 0;
+}
+
+// Walk the regions (32^3 voxel blocks) a ray passes through, inserting each
+// into the hash table.  The same exact walk at region resolution visits
+// exactly the regions of the voxels the voxel walk visits: region boundaries
+// are voxel boundaries, crossed at the same t in the same tie order.
+__device__ __forceinline__ void insert_ray_regions(const DeviceMap& m, const long long a[3], const long long b[3]) {
+  Walker w;
+  walker_init(w, a, b, m.frac_bits + kRegionShift, 0, 0);
+  insert_region(m, w.vx, w.vy, w.vz);
+  while (w.total > 0) {
+    int32_t c, s;
+    walker_step(w, walker_choose(w), &c, &s);
+    insert_region(m, w.vx, w.vy, w.vz);
+  }
+}
+
+__device__ __forceinline__ long long voxel_offset(int32_t slot, uint32_t mo) {
+  return (long long)slot * kRegionVoxels + mo;
+}
+
+__device__ __forceinline__ int32_t region_slot_of(const DeviceMap& m, int32_t vx, int32_t vy, int32_t vz) {
+  return find_region(m, pack_region(vx >> kRegionShift, vy >> kRegionShift, vz >> kRegionShift));
+}
+
+__device__ __forceinline__ uint32_t local_morton(int32_t vx, int32_t vy, int32_t vz) {
+  const int32_t mask = (1 << kRegionShift) - 1;
+  return morton((uint32_t)(vx & mask), (uint32_t)(vy & mask), (uint32_t)(vz & mask));
+}
+
+// Retry a clamped log-odds CAS whose first attempt found `cur` instead of
+// the value it expected (see logodds_update).
+static __device__ __noinline__ void logodds_retry(const DeviceMap& m, unsigned int* u, unsigned int cur, float delta) {
+  for (int it = 0; it < 256; ++it) {
+    const float l = __uint_as_float(cur);
+    const float l0 = (l != l) ? 0.0f : l;
+    const unsigned int nb = __float_as_uint(fminf(fmaxf(__fadd_rn(l0, delta), m.l_min), m.l_max));
+    if (nb == cur) return;
+    const unsigned int prev = atomicCAS(u, cur, nb);
+    if (prev == cur) return;
+    cur = prev;
+  }
+  atomicOr(m.status, kStatusCasLimit);
+}
+
+#ifndef OHM_WALK_BATCH
+#define OHM_WALK_BATCH 4
+#endif
+#ifndef OHM_WALK_MIN_BLOCKS
+#define OHM_WALK_MIN_BLOCKS 4
+#endif
+constexpr int kWalkBatch = OHM_WALK_BATCH;
+
+// Snapshot of the pool counters at the start of a call (the rollback point).
+__device__ __forceinline__ void begin_call(const DeviceMap& m, long long n) {
+  m.calls->region_start = *m.region_count;
+  m.calls->ndt_start = *m.ndt_count;
+  m.calls->segments = 0;
+  m.calls->visits = 0;
+  m.calls->touched = 0;
+  m.calls->rays = (unsigned long long)n;
+}
+
+// Per ray: fixed-point quantisation, max-range truncation, region walk with
+// hash insertion, segment table.  Every lane of the warp must call this
+// together with the same map (the segment reservation is warp-aggregated);
+// lanes without a ray pass active = false.
+__device__ __forceinline__ void prepare_occ_ray(const DeviceMap& m, const CallArgs& args, long long i, bool active) {
+  active = active && !latched(m);
+  const int F = m.frac_bits;
+  unsigned int nseg = 0, nvisit = 0;
+  RayRec r;
+  r.flags = 0;
+  r.nseg = 0;
+  r.inv = 0;
+  if (active) {
+    float o[3], e[3];
+    uint8_t flag;
+    load_ray(args, i, o, e, &flag);
+    long long qo[3], qe[3];
+    bool ok = quantise_ray(m, o, e, qo, qe);
+    bool sample = (flag & kFlagNoReturn) == 0;
+    if (ok) {
+      double d[3];
+      const double len = ray_length(qo, qe, d);
+      if (len > m.rmax_q) {
+        const double ratio = __ddiv_rn(m.rmax_q, len);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) qe[k] = qo[k] + __double2ll_rn(__dmul_rn(d[k], ratio));
+        sample = false;
+      }
+      ok = in_extent(qo, F) && in_extent(qe, F);
+    }
+    if (ok) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        r.a[k] = qo[k];
+        r.b[k] = qe[k];
+      }
+      int32_t nmaj;
+      const int M = dominant_axis(qo, qe, F, &nmaj);
+      nseg = (unsigned int)segment_count(nmaj, m.seg_steps);
+      const long long am = sel3(M, qe[0] - qo[0], qe[1] - qo[1], qe[2] - qo[2]);
+      r.inv = reciprocal64((unsigned long long)(am < 0 ? -am : am));
+      r.flags = kRayValid | (sample ? kRaySample : 0) | (M << kRayAxisShift);
+      r.nseg = (int32_t)nseg;
+      long long l1 = 0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        long long dv = (qe[k] >> F) - (qo[k] >> F);
+        l1 += dv < 0 ? -dv : dv;
+      }
+      nvisit = (unsigned int)(1 + l1);
+      insert_ray_regions(m, qo, qe);
+    }
+    m.rays[i] = r;
+  }
+  const unsigned long long base = warp_reserve(&m.calls->segments, nseg);
+  if (nseg > 0) {
+    if (base + nseg > (unsigned long long)m.max_segs) {
+      atomicOr(m.status, kStatusScratch);
+    } else {
+      for (unsigned int j = 0; j < nseg; ++j) m.segs[base + j] = make_int2((int)i, (int)j);
+    }
+  }
+  warp_add(&m.calls->visits, &m.calls->total_visits, nvisit);
+}
+
+// Per sample: give the sample's region an NDT layer.
+__device__ __forceinline__ void ndt_alloc_ray(const DeviceMap& m, long long i) {
+  const int F = m.frac_bits;
+  const RayRec r = m.rays[i];
+  if (!(r.flags & kRaySample)) return;
+  const int32_t slot = region_slot_of(m, (int32_t)(r.b[0] >> F), (int32_t)(r.b[1] >> F), (int32_t)(r.b[2] >> F));
+  if (slot < 0) {
+    atomicOr(m.status, kStatusMissing);
+    return;
+  }
+  if (*(volatile int32_t*)&m.ndt_slot[slot] != -1) return;
+  if (atomicCAS(&m.ndt_slot[slot], -1, -2) == -1) {
+    const int32_t id = atomicAdd(m.ndt_count, 1);
+    if (id < m.max_ndt)
+      m.ndt_slot[slot] = id;
+    else
+      atomicOr(m.status, kStatusCapacity);
+  }
+}
+
+// Miss phase (Sec. III-C phase one) for one segment: every voxel a ray passes
+// through, except the voxel holding its sample, takes one miss.  Segment j of
+// a ray covers the voxels entered after j*S and before (j+1)*S steps of the
+// ray's dominant axis (the last segment runs to the end).
+//
+// The walk itself is cheap integer arithmetic; the cost is the read-modify-
+// write of each voxel in global memory.  So the thread walks kWalkBatch voxels
+// ahead, then issues all their loads at once, then all their CASes at once,
+// keeping that many memory operations in flight instead of one.
+template <bool kOcc, bool kCounts>
+__device__ __forceinline__ void walk_segment(const DeviceMap& m, long long si) {
+  const int F = m.frac_bits;
+  const int32_t S = m.seg_steps;
+  const float miss = m.miss;
+  const int2 sg = m.segs[si];
+  const RayRec r = m.rays[sg.x];
+  const int M = (r.flags >> kRayAxisShift) & 3;
+  const bool last = sg.y == r.nseg - 1;
+  const bool sample = (r.flags & kRaySample) != 0;
+  Walker w;
+  walker_init(w, r.a, r.b, F, M, (long long)sg.y * S, r.inv);
+  int32_t mrem = last ? INT_MAX : S - 1;
+  int32_t slot = region_slot_of(m, w.vx, w.vy, w.vz);
+  if (slot < 0) {
+    atomicOr(m.status, kStatusMissing);
+    return;
+  }
+  uint32_t mo = local_morton(w.vx, w.vy, w.vz);
+  bool done = false;
+  while (!done) {
+    uint32_t off[kWalkBatch];  // voxel offsets (< 2^31: at most 2^16 regions of 2^15 voxels)
+    uint32_t todo = 0;         // bit j: off[j] takes a miss
+#pragma unroll
+    for (int j = 0; j < kWalkBatch; ++j) {
+      off[j] = 0;
+      if (done) continue;
+      // the current voxel takes a miss unless it holds this ray's sample
+      off[j] = (uint32_t)voxel_offset(slot, mo);
+      if (!(sample && w.total == 0)) {
+        todo |= 1u << j;
+        if (kCounts) atomicAdd(m.counts + off[j], 1ULL);
+      }
+      if (w.total == 0) {
+        done = true;
+        continue;
+      }
+      const int axis = walker_choose(w);
+      if (axis == M) {
+        if (mrem == 0) {
+          done = true;
+          continue;
+        }
+        --mrem;
+      }
+      int32_t c, s;
+      walker_step(w, axis, &c, &s);
+      mo = morton_step(mo, morton_mask(axis), s);
+      if ((c & ((1 << kRegionShift) - 1)) == (s > 0 ? 0 : (1 << kRegionShift) - 1)) {
+        slot = region_slot_of(m, w.vx, w.vy, w.vz);
+        if (slot < 0) {
+          atomicOr(m.status, kStatusMissing);
+          done = true;
+        }
+      }
+    }
+    if (kOcc) {
+      unsigned int* base = reinterpret_cast<unsigned int*>(m.occ);
+      unsigned int old[kWalkBatch], prev[kWalkBatch];
+#pragma unroll
+      for (int j = 0; j < kWalkBatch; ++j) old[j] = (todo >> j) & 1u ? base[off[j]] : 0u;
+#pragma unroll
+      for (int j = 0; j < kWalkBatch; ++j) {
+        prev[j] = old[j];
+        if (!((todo >> j) & 1u)) continue;
+        const float l = __uint_as_float(old[j]);
+        const float l0 = (l != l) ? 0.0f : l;
+        const unsigned int nb = __float_as_uint(fminf(fmaxf(__fadd_rn(l0, miss), m.l_min), m.l_max));
+        if (nb == old[j]) continue;
+        prev[j] = atomicCAS(base + off[j], old[j], nb);
+      }
+#pragma unroll
+      for (int j = 0; j < kWalkBatch; ++j)
+        if (prev[j] != old[j]) logodds_retry(m, base + off[j], prev[j], miss);
+    }
+  }
+}
+
+// Sample phase (Sec. III-C phase two) for one ray: the voxel holding its
+// sample takes a hit; with the NDT layer it also accumulates the sample's
+// exact integer moments (count, sum, outer-product sum of the position inside
+// the voxel), from which mean and covariance are formed when queried.
+template <bool kOcc, bool kCounts, bool kNdt>
+__device__ __forceinline__ void hit_ray(const DeviceMap& m, long long i) {
+  const int F = m.frac_bits;
+  const long long U = 1LL << F;
+  const RayRec r = m.rays[i];
+  if (!(r.flags & kRaySample)) return;
+  const int32_t vx = (int32_t)(r.b[0] >> F), vy = (int32_t)(r.b[1] >> F), vz = (int32_t)(r.b[2] >> F);
+  const int32_t slot = region_slot_of(m, vx, vy, vz);
+  if (slot < 0) {
+    atomicOr(m.status, kStatusMissing);
+    return;
+  }
+  const uint32_t mo = local_morton(vx, vy, vz);
+  const long long off = voxel_offset(slot, mo);
+  if (kOcc) logodds_update(m, m.occ + off, m.hit);
+  if (kCounts) atomicAdd(m.counts + off, 1ULL << 32);
+  if (kNdt) {
+    const int32_t ns = m.ndt_slot[slot];
+    if (ns < 0) {
+      atomicOr(m.status, kStatusMissing);
+      return;
+    }
+    const long long px = r.b[0] - (long long)vx * U;
+    const long long py = r.b[1] - (long long)vy * U;
+    const long long pz = r.b[2] - (long long)vz * U;
+    unsigned long long* base = reinterpret_cast<unsigned long long*>(m.ndt) + (long long)ns * 10 * kRegionVoxels + mo;
+    const long long vals[10] = {1, px, py, pz, px * px, px * py, px * pz, py * py, py * pz, pz * pz};
+#pragma unroll
+    for (int k = 0; k < 10; ++k) atomicAdd(base + (long long)k * kRegionVoxels, (unsigned long long)vals[k]);
+  }
+}
+
+// TSDF band of one ray (Sec. II-F): from range max(0, d - tau) to d + tau,
+// quantised like a truncated endpoint.  Full warp, like prepare_occ_ray.
+__device__ __forceinline__ void prepare_tsdf_ray(const DeviceMap& m, const CallArgs& args, long long i, bool active) {
+  active = active && !latched(m);
+  const int F = m.frac_bits;
+  unsigned int nvisit = 0;
+  TsdfRec r;
+  r.flags = 0;
+  if (active) {
+    float o[3], e[3];
+    uint8_t flag;
+    load_ray(args, i, o, e, &flag);
+    long long qo[3], qe[3];
+    bool ok = quantise_ray(m, o, e, qo, qe) && (flag & kFlagNoReturn) == 0;
+    double d[3], len = 0.0;
+    if (ok) {
+      len = ray_length(qo, qe, d);
+      ok = len > m.rmin_q && len <= m.rmax_q && in_extent(qo, F) && in_extent(qe, F);
+    }
+    if (ok) {
+      double t0 = __dsub_rn(len, m.tau_q);
+      if (t0 < 0.0) t0 = 0.0;
+      const double t1 = __dadd_rn(len, m.tau_q);
+      const double f0 = __ddiv_rn(t0, len), f1 = __ddiv_rn(t1, len);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        r.a[k] = qo[k] + __double2ll_rn(__dmul_rn(d[k], f0));
+        r.b[k] = qo[k] + __double2ll_rn(__dmul_rn(d[k], f1));
+        r.e[k] = qe[k];
+        r.u[k] = (float)__ddiv_rn(d[k], len);
+      }
+      r.flags = kRayValid;
+      long long l1 = 0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        long long dv = (r.b[k] >> F) - (r.a[k] >> F);
+        l1 += dv < 0 ? -dv : dv;
+      }
+      nvisit = (unsigned int)(1 + l1);
+      insert_ray_regions(m, r.a, r.b);
+    }
+    m.trays[i] = r;
+  }
+  warp_add(&m.calls->visits, &m.calls->total_visits, nvisit);
+}
+
+// TSDF band walk of one ray: per visited voxel c, s = (e - c).u (equal to
+// d - (c - o).u), truncated to [-tau, tau], summed in 2^-32 m fixed point
+// with a count.  The first visitor of a voxel in this call records it for the
+// apply pass.
+__device__ __forceinline__ void tsdf_walk_ray(const DeviceMap& m, long long i) {
+  const int F = m.frac_bits;
+  const long long U = 1LL << F;
+  const long long half = U >> 1;
+  const float to_m = (float)(m.voxel_size / (double)(1LL << F));
+  const TsdfRec r = m.trays[i];
+  if (!(r.flags & kRayValid)) return;
+  Walker w;
+  walker_init(w, r.a, r.b, F, 0, 0);
+  int32_t slot = region_slot_of(m, w.vx, w.vy, w.vz);
+  if (slot < 0) {
+    atomicOr(m.status, kStatusMissing);
+    return;
+  }
+  uint32_t mo = local_morton(w.vx, w.vy, w.vz);
+  for (;;) {
+    const float ex = (float)(r.e[0] - ((long long)w.vx * U + half));
+    const float ey = (float)(r.e[1] - ((long long)w.vy * U + half));
+    const float ez = (float)(r.e[2] - ((long long)w.vz * U + half));
+    float s = (ex * r.u[0] + ey * r.u[1] + ez * r.u[2]) * to_m;
+    s = fminf(fmaxf(s, -m.tau_m), m.tau_m);
+    const long long sq = __float2ll_rn(s * 4294967296.0f);
+    const long long off = voxel_offset(slot, mo);
+    const unsigned int prev = atomicAdd(m.tsdf_cnt + off, 1u);
+    atomicAdd(reinterpret_cast<unsigned long long*>(m.tsdf_sum) + off, (unsigned long long)sq);
+    if (prev == 0) {
+      const unsigned long long t = atomicAdd(&m.calls->touched, 1ULL);
+      if (t < (unsigned long long)m.max_touched)
+        m.touched[t] = (int32_t)off;
+      else
+        atomicOr(m.status, kStatusScratch);
+    }
+    if (w.total == 0) break;
+    const int axis = walker_choose(w);
+    int32_t c, sg;
+    walker_step(w, axis, &c, &sg);
+    mo = morton_step(mo, morton_mask(axis), sg);
+    if ((c & ((1 << kRegionShift) - 1)) == (sg > 0 ? 0 : (1 << kRegionShift) - 1)) {
+      slot = region_slot_of(m, w.vx, w.vy, w.vz);
+      if (slot < 0) {
+        atomicOr(m.status, kStatusMissing);
+        break;
+      }
+    }
+  }
+}
+
+// Weighted average of one touched voxel: D <- (W D + sum s) / (W + c),
+// W <- min(W + c, W_max); the per-call sums are cleared for the next call.
+__device__ __forceinline__ void tsdf_apply_one(const DeviceMap& m, long long t) {
+  const int32_t off = m.touched[t];
+  const unsigned int c = m.tsdf_cnt[off];
+  const long long sum = m.tsdf_sum[off];
+  m.tsdf_cnt[off] = 0;
+  m.tsdf_sum[off] = 0;
+  const float2 dw = m.tsdf[off];
+  const double W = (double)dw.y, D = (double)dw.x;
+  const double S = (double)sum * (1.0 / 4294967296.0);
+  const double Wn = W + (double)c;
+  const double Dn = (W * D + S) / Wn;
+  m.tsdf[off] = make_float2((float)Dn, (float)(Wn < (double)m.wmax ? Wn : (double)m.wmax));
+}
+
+__device__ __forceinline__ long long touched_count(const DeviceMap& m) {
+  unsigned long long nt = m.calls->touched;
+  return (long long)(nt > (unsigned long long)m.max_touched ? (unsigned long long)m.max_touched : nt);
+}
+
+// Undo the allocations of a failed call (threads t0, t0 + stride, ...): keys
+// inserted by it become tombstones, its NDT slots are released, the pool
+// counters are restored.
+__device__ __forceinline__ void rollback_call(const DeviceMap& m, long long t0, long long stride) {
+  const int32_t rs = m.calls->region_start, ns = m.calls->ndt_start;
+  for (long long h = t0; h <= (long long)m.hmask; h += stride) {
+    const longlong2 e = m.htab[h];
+    if (e.x == kEmptyKey || e.x == kTombKey) continue;
+    if (e.y < 0 || e.y >= rs) m.htab[h] = make_longlong2(kTombKey, -1);
+  }
+  for (long long s = t0; s < m.max_regions; s += stride) {
+    const int32_t v = m.ndt_slot[s];
+    if (s >= rs || v == -2 || v >= ns) m.ndt_slot[s] = -1;
+  }
+  if (t0 == 0) {
+    *m.region_count = rs;
+    *m.ndt_count = ns;
+  }
+}
+
+}  // namespace ohm

@@ -27,7 +27,10 @@ _STATUS_NAMES = {ERR_INVALID: "invalid argument", ERR_CAPACITY: "capacity", ERR_
 # Every symbol include/ohm_gb.h declares.
 EXPORTED = ["ohm_map_create", "ohm_map_destroy", "ohm_integrate_rays", "ohm_integrate_rays_async", "ohm_map_sync",
             "ohm_query_voxels", "ohm_map_region_count", "ohm_map_export", "ohm_map_stats", "ohm_map_profile",
-            "ohm_map_profile_read", "ohm_last_error", "ohm_count_rays_noalloc"]
+            "ohm_map_profile_read", "ohm_last_error", "ohm_count_rays_noalloc", "ohm_batch_create",
+            "ohm_batch_destroy", "ohm_batch_tune", "ohm_batch_integrate", "ohm_batch_sync", "ohm_batch_stats"]
+
+BATCH_MAX_MAPS = 32
 
 NOALLOC_MAX_RAYS = 32768
 
@@ -118,6 +121,19 @@ def load_library(path: str = LIB_PATH):
     lib.ohm_map_profile_read.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
     lib.ohm_count_rays_noalloc.restype = st
     lib.ohm_count_rays_noalloc.argtypes = [ctypes.POINTER(CountGrid), p, i64, p, p, i64, p, p, vp]
+    lib.ohm_batch_create.restype = st
+    lib.ohm_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int32, ctypes.POINTER(vp)]
+    lib.ohm_batch_destroy.restype = None
+    lib.ohm_batch_destroy.argtypes = [vp]
+    lib.ohm_batch_tune.restype = st
+    lib.ohm_batch_tune.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
+    lib.ohm_batch_integrate.restype = st
+    lib.ohm_batch_integrate.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(i64), ctypes.POINTER(vp),
+                                        ctypes.POINTER(vp), ctypes.POINTER(i64), ctypes.c_int32, vp]
+    lib.ohm_batch_sync.restype = st
+    lib.ohm_batch_sync.argtypes = [vp, vp]
+    lib.ohm_batch_stats.restype = st
+    lib.ohm_batch_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
     lib.ohm_last_error.restype = ctypes.c_char_p
     lib.ohm_last_error.argtypes = []
     _lib = lib
@@ -311,3 +327,61 @@ def count_rays_noalloc(grid: dict, origins, endpoints, flags, hits, misses, stre
     f = _as_flags(flags)
     _check(load_library().ohm_count_rays_noalloc(ctypes.byref(g), _ptr(o), int(o.shape[0]), _ptr(e), _ptr(f),
                                                  int(e.shape[0]), _ptr(hits), _ptr(misses), _stream_handle(stream)))
+
+
+class Batch:
+    """Up to 32 maps integrated together, one launch per kernel stage for all
+    of them, optionally replayed from a captured CUDA graph."""
+
+    def __init__(self, maps):
+        lib = load_library()
+        self.maps = list(maps)
+        n = len(self.maps)
+        arr = (ctypes.c_void_p * n)(*[m.handle.value for m in self.maps])
+        h = ctypes.c_void_p()
+        _check(lib.ohm_batch_create(arr, n, ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().ohm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def tune(self, segment_steps=0, walk_blocks_per_sm=0):
+        _check(load_library().ohm_batch_tune(self._h, int(segment_steps), int(walk_blocks_per_sm)))
+
+    def integrate(self, raysets, stream=None, graph=True):
+        """raysets[i] = (origins, endpoints, flags) CUDA tensors for map i, or
+        None for no rays this step."""
+        n = len(self.maps)
+        P = ctypes.c_void_p * n
+        I = ctypes.c_int64 * n
+        o, e, f = P(), P(), P()
+        no, nn = I(), I()
+        self._keep = []
+        for i, rs in enumerate(raysets):
+            if rs is None:
+                no[i], nn[i] = 1, 0
+                continue
+            oo = _as_points(rs[0], "origins")
+            ee = _as_points(rs[1], "endpoints")
+            ff = _as_flags(rs[2]) if len(rs) > 2 else None
+            self._keep += [oo, ee, ff]
+            o[i], e[i] = oo.data_ptr(), ee.data_ptr()
+            f[i] = ff.data_ptr() if ff is not None else None
+            no[i], nn[i] = int(oo.shape[0]), int(ee.shape[0])
+        _check(load_library().ohm_batch_integrate(self._h, o, no, e, f, nn, 1 if graph else 0, _stream_handle(stream)))
+
+    def sync(self, stream=None):
+        _check(load_library().ohm_batch_sync(self._h, _stream_handle(stream)))
+
+    def stats(self):
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        _check(load_library().ohm_batch_stats(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return {"kernel_launches": int(a.value), "graph_launches": int(b.value)}

@@ -107,3 +107,26 @@ def compare_query(gm: ohm.Map, om: oracle.OracleMap, pts: np.ndarray, ndt=False,
         assert np.array_equal(gt[:, 1], r["tsdf"][:, 1])
         assert np.abs(gt[:, 0] - r["tsdf"][:, 0]).max(initial=0) <= tsdf_atol
     return int(k.sum())
+
+
+def export_sorted(gm: ohm.Map):
+    """Every layer of every region, regions sorted by key (CPU tensors)."""
+    L = gm.params["layers"]
+    ex = gm.export(occupancy=bool(L & ohm.LAYER_OCCUPANCY), counts=bool(L & ohm.LAYER_COUNTS),
+                   ndt=bool(L & ohm.LAYER_NDT), tsdf=bool(L & ohm.LAYER_TSDF))
+    keys = ex["keys"].cpu().numpy()
+    order = torch.from_numpy(np.lexsort((keys[:, 2], keys[:, 1], keys[:, 0]))).to(ex["keys"].device)
+    out = {}
+    for k, v in ex.items():
+        v = v[order]
+        if v.dtype == torch.float32:
+            v = v.view(torch.int32)  # bitwise comparison (NaN = unknown)
+        out[k] = v.cpu()
+    return out
+
+
+def assert_maps_identical(a: ohm.Map, b: ohm.Map):
+    ea, eb = export_sorted(a), export_sorted(b)
+    assert ea.keys() == eb.keys()
+    for k in ea:
+        assert torch.equal(ea[k], eb[k]), "layer %s differs" % k
