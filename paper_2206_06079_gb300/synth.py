@@ -124,6 +124,32 @@ def lidar_directions(beams: int, azimuths: int, fov_deg: float = 22.5, device="c
     return d.reshape(-1, 3)
 
 
+def march_tunnel(o, u, max_range: float):
+    """Distance along unit rays u from o (inside the tunnel) to the wall, or
+    >= max_range when none is met: sphere tracing on a conservative bound
+    (|grad radial| <= sqrt(1 + (A k)^2)), a 1 cm step floor, then bisection."""
+    k = 2.0 * math.pi / TUNNEL_WAVELENGTH
+    lip = math.sqrt(1.0 + (TUNNEL_AMPLITUDE * k) ** 2)
+    limit = max_range + 1.0
+    n = u.shape[0]
+    t = torch.zeros(n, dtype=torch.float64, device=u.device)
+    prev = torch.zeros_like(t)
+    for _ in range(1000):
+        gap = TUNNEL_RADIUS - _tunnel_radial(o + t[:, None] * u)
+        active = (gap > 0) & (t < limit)
+        if not bool(active.any()):
+            break
+        prev = torch.where(active, t, prev)
+        t = torch.where(active, torch.clamp(t + torch.clamp(gap / lip, min=0.01), max=limit), t)
+    lo, hi = prev, t
+    for _ in range(30):
+        mid = 0.5 * (lo + hi)
+        inside = _tunnel_radial(o + mid[:, None] * u) < TUNNEL_RADIUS
+        lo = torch.where(inside, mid, lo)
+        hi = torch.where(inside, hi, mid)
+    return 0.5 * (lo + hi)
+
+
 def tunnel_scan(i: int, seed: int = 0x0A13, beams: int = 128, azimuths: int = 1024, max_range: float = 50.0,
                 missing: float = 0.1, range_noise: float = 0.03, device="cpu", fov_deg: float = 22.5,
                 step: float = 0.5) -> RaySet:
@@ -319,3 +345,76 @@ def fuzz_rays(seed: int, n: int, voxel: float = 0.1, extent: float = 2.0, device
     pts_e = torch.where((special == 2)[:, None], diag, pts_e)                           # exact diagonal
     flags = (torch.rand(n, generator=g) < 0.15).to(torch.uint8) * FLAG_NO_RETURN
     return RaySet(pts_o.float().to(device), pts_e.float().to(device), flags.to(device))
+
+
+# ---------------------------------------------------------------------------
+# Mixed sensors in either scene (the batched multi-map workload).
+# ---------------------------------------------------------------------------
+def pinhole_directions(width: int, height: int, R, fov_x_deg: float = None, fx: float = None, device="cpu"):
+    """World-frame unit directions and z-scale of a pinhole camera (x right,
+    y down, z forward; R maps camera to world axes), principal point at the
+    image centre.  Returns (u (h*w, 3), cos_to_axis (h*w,))."""
+    if fx is None:
+        fx = 0.5 * width / math.tan(math.radians(fov_x_deg) / 2)
+    vv, uu = torch.meshgrid(torch.arange(height, dtype=torch.float64), torch.arange(width, dtype=torch.float64),
+                            indexing="ij")
+    dc = torch.stack([(uu - (width - 1) / 2) / fx, (vv - (height - 1) / 2) / fx, torch.ones_like(uu)], -1).reshape(-1, 3)
+    norm = dc.norm(dim=1)
+    u = (dc / norm[:, None]) @ R.to(torch.float64).T
+    return u.to(device), (1.0 / norm).to(device)
+
+
+def mixed_scan(scene: str, kind: str, seed: int, device="cpu", max_range: float = 20.0) -> RaySet:
+    """One scan of `kind` in `scene`.  kind: 'lidar16x1800', 'lidar64x1024',
+    'lidar128x2048' (spinning lidar, +-22.5 deg, 2 % missing returns) or
+    'depth424x240' (pinhole, fx = fy = 525 * 424 / 640, z in (0.3, 6] m).
+    scene: 'tunnel' (sensor on the centreline at a seeded x) or 'room' (sensor
+    at a seeded point of the 6 x 6 x 3 m room with boxes and spheres)."""
+    g = _gen(seed)
+    jit = torch.rand(4, generator=g, dtype=torch.float64)
+    if scene == "tunnel":
+        x = float(jit[0]) * 40.0
+        o = torch.tensor([x, TUNNEL_AMPLITUDE * math.sin(2 * math.pi * x / TUNNEL_WAVELENGTH), 0.0],
+                         dtype=torch.float64, device=device)
+        yaw = math.atan(TUNNEL_AMPLITUDE * (2 * math.pi / TUNNEL_WAVELENGTH) * math.cos(2 * math.pi * x / TUNNEL_WAVELENGTH))
+    else:
+        o = torch.tensor([-1.0 + 2.0 * float(jit[0]), -2.5 + 0.4 * float(jit[1]), 1.0 + float(jit[2])],
+                         dtype=torch.float64, device=device)
+        yaw = 2 * math.pi * float(jit[3])
+    cy, sy = math.cos(yaw), math.sin(yaw)
+    if kind.startswith("lidar"):
+        beams, az = (int(v) for v in kind[5:].split("x"))
+        d = lidar_directions(beams, az, 22.5, device=device)
+        u = torch.stack([cy * d[:, 0] - sy * d[:, 1], sy * d[:, 0] + cy * d[:, 1], d[:, 2]], dim=1)
+        zscale = None
+    else:
+        w, h = (int(v) for v in kind[5:].split("x"))
+        # camera looking along the heading, level
+        f = torch.tensor([cy, sy, 0.0], dtype=torch.float64)
+        r = torch.tensor([sy, -cy, 0.0], dtype=torch.float64)
+        dn = torch.linalg.cross(f, r)
+        R = torch.stack([r, dn, f], dim=1)
+        u, zscale = pinhole_directions(w, h, R, fx=525.0 * w / 640.0, device=device)
+    n = u.shape[0]
+    miss_draw = torch.rand(n, generator=g, dtype=torch.float64).to(device)
+    noise = (torch.randn(n, generator=g, dtype=torch.float64) * 0.02).to(device)
+    if scene == "tunnel":
+        t = march_tunnel(o, u, max_range)
+    else:
+        sc = depth_scene()
+        lo = torch.tensor(sc.room_lo, dtype=torch.float64, device=device)
+        hi = torch.tensor(sc.room_hi, dtype=torch.float64, device=device)
+        bound = torch.where(u > 0, hi, lo)
+        safe = torch.where(u == 0, torch.ones_like(u), u)
+        t = torch.where(u == 0, torch.full_like(u, float("inf")), (bound - o) / safe).min(dim=1).values
+        t = torch.minimum(t, _ray_box_entry(o, u, sc.boxes_lo.to(device), sc.boxes_hi.to(device)).min(1).values)
+        t = torch.minimum(t, _ray_sphere(o, u, sc.spheres_c.to(device), sc.spheres_r.to(device)).min(1).values)
+    if zscale is None:
+        no_ret = (miss_draw < 0.02) | (t >= max_range)
+        rng = torch.where(no_ret, torch.full_like(t, max_range), t + noise)
+    else:
+        z = t * zscale
+        no_ret = (z <= 0.3) | (z > 6.0)
+        rng = torch.where(no_ret, 6.0 / zscale, t)
+    e = o[None] + rng[:, None] * u
+    return RaySet(o[None].float(), e.float(), no_ret.to(torch.uint8) * FLAG_NO_RETURN)
