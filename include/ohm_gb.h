@@ -235,7 +235,8 @@ ohm_status ohm_batch_integrate(ohm_batch* batch, const float* const* origins, co
 /* Wait for `stream`; return (and clear) the first failure latched by any map. */
 ohm_status ohm_batch_sync(ohm_batch* batch, void* stream);
 
-/* Kernels launched through this batch, and graph launches among the steps. */
+/* Kernels launched through this batch (a graph replay counts its kernel
+ * nodes), and the number of steps replayed from the captured graph. */
 ohm_status ohm_batch_stats(ohm_batch* batch, int64_t* kernel_launches, int64_t* graph_launches);
 
 /* ---------------------------------------------------------------------------

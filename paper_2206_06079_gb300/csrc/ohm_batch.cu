@@ -221,6 +221,7 @@ struct ohm_batch {
   bool any_ndt, any_tsdf, any_occ;
   long long launches;
   long long graph_launches;
+  int graph_kernels;           // kernel nodes in the captured step
 };
 
 namespace {
@@ -247,8 +248,8 @@ void drop_graph(ohm_batch* b) {
   }
 }
 
-// The kernels of one step, in stream order.
-cudaError_t enqueue_step(ohm_batch* b, cudaStream_t s) {
+// The kernels of one step, in stream order; returns their number in *count.
+cudaError_t enqueue_step(ohm_batch* b, cudaStream_t s, int* count) {
   using namespace ohm;
   const int grid = b->num_sms * b->walk_blocks_per_sm;
   const int ray_grid = b->num_sms * 4;
@@ -281,7 +282,7 @@ cudaError_t enqueue_step(ohm_batch* b, cudaStream_t s) {
   }
   k_batch_end<<<kMaxBatchMaps * 8, kBlock, 0, s>>>(b->d_desc);
   ++n;
-  b->launches += n;
+  *count = n;
   return cudaGetLastError();
 }
 
@@ -402,13 +403,15 @@ ohm_status ohm_batch_integrate(ohm_batch* b, const float* const* origins, const 
   cudaError_t e = cudaMemcpyAsync(b->d_step, &b->h_step, sizeof(ohm::BatchStep), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return bfail(OHM_ERR_CUDA, std::string("batch_integrate: ") + cudaGetErrorString(e));
   if (!use_graph) {
-    e = enqueue_step(b, s);
+    int count = 0;
+    e = enqueue_step(b, s, &count);
+    b->launches += count;
   } else {
     if (!b->have_exec) {
       // Capture the step once; later steps replay it.
       e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
-        cudaError_t el = enqueue_step(b, s);
+        cudaError_t el = enqueue_step(b, s, &b->graph_kernels);
         e = cudaStreamEndCapture(s, &b->graph);
         if (e == cudaSuccess) e = el;
       }
@@ -416,7 +419,10 @@ ohm_status ohm_batch_integrate(ohm_batch* b, const float* const* origins, const 
       if (e == cudaSuccess) b->have_exec = true;
     }
     if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, s);
-    if (e == cudaSuccess) b->graph_launches += 1;
+    if (e == cudaSuccess) {
+      b->graph_launches += 1;
+      b->launches += b->graph_kernels;
+    }
   }
   if (e != cudaSuccess) return bfail(OHM_ERR_CUDA, std::string("batch_integrate: ") + cudaGetErrorString(e));
   return OHM_OK;
