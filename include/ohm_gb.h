@@ -193,6 +193,42 @@ ohm_status ohm_map_profile(ohm_map* map, uint32_t stage_mask);
 ohm_status ohm_map_profile_read(ohm_map* map, int32_t stage, double* total_ms, int64_t* launches);
 
 /* ---------------------------------------------------------------------------
+ * Depth images and the TSDF adjoint.
+ * ------------------------------------------------------------------------- */
+
+/* Integrate one z-depth image (width x height floats, device memory, row
+ * major) seen from pose (3 x 4 row-major camera-to-world [R | t], host) with
+ * intrinsics (fx, fy, cx, cy; host): pixel (u, v) with depth z becomes the ray
+ * from t to e = R (z ((u - cx) / fx), z ((v - cy) / fy), z) + t, evaluated in
+ * double with one rounding per operation in the order
+ * e_k = ((R_k0 x + R_k1 y) + R_k2 z) + t_k and rounded to float.  A depth
+ * outside (z_min, z_max] gives a NO_RETURN ray at depth z_max (it clears space
+ * in occupancy layers and is skipped by the TSDF, Sec. II-F).  width * height
+ * must not exceed max_rays.  Like ohm_integrate_rays_async: returns once
+ * enqueued; failures are reported by ohm_map_sync. */
+ohm_status ohm_integrate_depth(ohm_map* map, const float* depth, int32_t width, int32_t height,
+                               const double* intrinsics, const double* pose, double z_min, double z_max,
+                               void* stream);
+
+/* Adjoint of the TSDF update of the depth frame just integrated (no counterpart
+ * in the paper).  With D the TSDF distance after that frame, it computes the
+ * gradient of L = sum_q grad_query[q] D(voxel of query_points[q]) with respect
+ * to every pixel's depth (grad_depth, width x height floats) and to the pose as
+ * a left twist xi = (rho, phi) that moves each world point p to
+ * p + rho + phi x p (grad_twist, 6 doubles), holding fixed the voxels each
+ * ray's band walk visits and the per-voxel counts (the update is piecewise
+ * smooth in the geometry; this is its derivative inside a piece).  Each pixel's
+ * walk is recomputed, nothing is stored by the forward pass.  Call it before
+ * any other integration into the map, with the same frame arguments as the
+ * forward call, and with TSDF weights below tsdf_wmax.  All arrays are device
+ * memory except intrinsics and pose.  The first call allocates a per-voxel
+ * weight layer (4 bytes per pool voxel).  Returns once enqueued. */
+ohm_status ohm_tsdf_backward(ohm_map* map, const float* depth, int32_t width, int32_t height,
+                             const double* intrinsics, const double* pose, double z_min, double z_max,
+                             const float* query_points, const float* grad_query, int64_t n_query, float* grad_depth,
+                             double* grad_twist, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Batched integration of many maps (no counterpart in the paper, which
  * integrates one ray set into one map at a time).
  *

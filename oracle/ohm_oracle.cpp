@@ -534,6 +534,120 @@ void oracle_query(void* h, const float* pts, int64_t n, float* occupancy, uint8_
   }
 }
 
+// ---------------------------------------------------------------------------
+// TSDF adjoint (the voxel sets held fixed).
+//
+// For one frame of rays with nominal float endpoints (which fix, through the
+// same quantised band walk as oracle_integrate, the voxels each ray updates),
+// evaluate in double precision at continuous geometry (o_eval, e_eval)
+//   L = sum_q g_q D_new(v_q),
+//   D_new(v) = (W D + sum_{j: v in band_j} s_j(v)) / (W + c(v))   (c(v) > 0)
+//            = D                                                  (c(v) = 0)
+//   s_j(v) = clamp(d_j - (centre(v) - o).u_j, -tau, tau),  d_j = |e_j - o|,
+// with W, D the map's current state (the state before this frame; the map is
+// not modified).  Also the analytic gradient: for an unclamped s,
+//   ds/de = u + r_perp / d,  ds/do = -r_perp / d,  r = e - centre,
+//   r_perp = r - (r.u) u,  dD_new/ds = 1 / (W + c).
+// qvox: m voxel indices (x, y, z) with weights g.  grad_e: n x 3, grad_o: 3
+// (either may be null).  Returns 0, or -1 on bad arguments.
+int oracle_tsdf_frame_eval(void* h, const float* o_nom, const float* e_nom, const uint8_t* flags, int64_t n,
+                           const double* o_eval, const double* e_eval, const int64_t* qvox, const double* g,
+                           int64_t m_q, double* loss, double* grad_e, double* grad_o) {
+  Map& m = *static_cast<Map*>(h);
+  if (!(m.p.layers & kLayerTsdf)) return -1;
+  typedef std::tuple<int64_t, int64_t, int64_t> Key;
+  // gradient weight per voxel
+  std::map<Key, double> G;
+  for (int64_t q = 0; q < m_q; ++q) G[std::make_tuple(qvox[3 * q], qvox[3 * q + 1], qvox[3 * q + 2])] += g[q];
+  // frozen band voxel lists from the nominal rays, and counts c(v)
+  std::vector<std::vector<Voxel>> bands((size_t)n);
+  std::map<Key, int64_t> count;
+  const double rmin = m.p.min_range * m.scale, rmax = m.p.max_range * m.scale;
+  for (int64_t j = 0; j < n; ++j) {
+    PreparedRay r;
+    if (!prepare_ray(m, o_nom, e_nom + 3 * j, flags ? flags[j] : 0, &r)) continue;
+    if (!r.has_sample || !(r.length > rmin) || r.length > rmax) continue;
+    const double tau_q = m.p.tsdf_trunc * m.scale;
+    double d[3];
+    for (int a = 0; a < 3; ++a) d[a] = (double)(r.qe[a] - r.qo[a]);
+    double t0 = r.length - tau_q;
+    if (t0 < 0.0) t0 = 0.0;
+    const double f0 = t0 / r.length, f1 = (r.length + tau_q) / r.length;
+    int64_t a0[3], a1[3];
+    for (int a = 0; a < 3; ++a) {
+      a0[a] = r.qo[a] + (int64_t)std::llrint(d[a] * f0);
+      a1[a] = r.qo[a] + (int64_t)std::llrint(d[a] * f1);
+    }
+    bands[(size_t)j] = walk(a0, a1, m.unit);
+    for (const Voxel& v : bands[(size_t)j]) count[std::make_tuple(v.v[0], v.v[1], v.v[2])] += 1;
+  }
+  // loss: unchanged voxels contribute g D, changed ones g D_new
+  double L = 0.0;
+  std::map<Key, double> sum_s;
+  const double tau = m.p.tsdf_trunc;
+  if (grad_o)
+    for (int a = 0; a < 3; ++a) grad_o[a] = 0.0;
+  for (int64_t j = 0; j < n; ++j) {
+    double ge[3] = {0.0, 0.0, 0.0};
+    if (!bands[(size_t)j].empty()) {
+      const double* e = e_eval + 3 * j;
+      double u[3], dist = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        u[a] = e[a] - o_eval[a];
+        dist += u[a] * u[a];
+      }
+      dist = std::sqrt(dist);
+      for (int a = 0; a < 3; ++a) u[a] /= dist;
+      for (const Voxel& v : bands[(size_t)j]) {
+        double r[3], ru = 0.0;
+        for (int a = 0; a < 3; ++a) {
+          const double centre = m.p.map_origin[a] + ((double)v.v[a] + 0.5) * m.p.voxel_size;
+          r[a] = e[a] - centre;
+          ru += r[a] * u[a];
+        }
+        // s = d - (centre - o).u = (e - centre).u
+        double s = ru;
+        const bool clamped = s >= tau || s <= -tau;
+        if (s > tau) s = tau;
+        if (s < -tau) s = -tau;
+        const Key k = std::make_tuple(v.v[0], v.v[1], v.v[2]);
+        sum_s[k] += s;
+        auto gi = G.find(k);
+        if (gi == G.end() || clamped) continue;
+        auto rit = m.regions.find(region_of(v));  // lookup only: the map is not modified
+        const double W = (rit != m.regions.end() && !rit->second.tsdf_w.empty()) ? rit->second.tsdf_w[local_index(v)] : 0.0;
+        const double w = gi->second / (W + (double)count[k]);
+        for (int a = 0; a < 3; ++a) {
+          const double rp = r[a] - ru * u[a];
+          ge[a] += w * (u[a] + rp / dist);
+          if (grad_o) grad_o[a] += -w * rp / dist;
+        }
+      }
+    }
+    if (grad_e)
+      for (int a = 0; a < 3; ++a) grad_e[3 * j + a] = ge[a];
+  }
+  for (const auto& kv : G) {
+    Voxel v;
+    v.v[0] = std::get<0>(kv.first);
+    v.v[1] = std::get<1>(kv.first);
+    v.v[2] = std::get<2>(kv.first);
+    auto it = m.regions.find(region_of(v));
+    double W = 0.0, D = 0.0;
+    if (it != m.regions.end() && !it->second.tsdf_w.empty()) {
+      W = it->second.tsdf_w[local_index(v)];
+      D = it->second.tsdf_d[local_index(v)];
+    }
+    auto c = count.find(kv.first);
+    if (c == count.end())
+      L += kv.second * D;
+    else
+      L += kv.second * (W * D + sum_s[kv.first]) / (W + (double)c->second);
+  }
+  *loss = L;
+  return 0;
+}
+
 // The walk alone, for tests: writes up to cap visited voxels (x, y, z) and
 // returns how many the walk visits.
 int64_t oracle_walk(const int64_t* a, const int64_t* b, int32_t frac_bits, int64_t* out, int64_t cap) {

@@ -1,0 +1,328 @@
+// Depth-image integration and the TSDF adjoint.
+//
+// ohm_integrate_depth back-projects a z-depth image into rays on the device
+// and integrates them (every layer of the map, Sec. II-F for TSDF).
+//
+// ohm_tsdf_backward gives the gradient of L = sum_q g_q D(v_q), D the TSDF
+// distance right after the frame was integrated, with respect to the frame's
+// per-pixel depths and its pose (a left twist xi = (rho, phi) moving every
+// world point p to p + rho + phi x p), with the voxel sets of the band walks
+// and the per-voxel counts held fixed.  It recomputes each pixel's band walk
+// instead of storing traces.  For an unclamped s = (e - c).u:
+//   ds/de = u + r_perp / d,  ds/do = -r_perp / d,  r = e - c,
+//   r_perp = r - (r.u) u,  dD/ds = 1 / W   (W = the weight after the frame),
+// so per ray, with w_v = G(v) / W(v) summed over its unclamped band voxels,
+//   dL/de = (sum w) u + (sum w r_perp) / d,  dL/do = -(sum w r_perp) / d,
+//   dL/dz = dL/de . R p~,  p~ = ((u - cx) / fx, (v - cy) / fy, 1),
+//   dL/drho += dL/de + dL/do,  dL/dphi += e x dL/de + o x dL/do.
+#include <string>
+
+#include "ohm_kernels.cuh"
+
+namespace ohm {
+namespace {
+
+struct DepthFrame {
+  const float* depth;
+  int32_t width, height;
+  double fx, fy, cx, cy;
+  double R[9];
+  double t[3];
+  double z_min, z_max;
+};
+
+// Back-projection of one pixel, one rounding per double operation:
+// x = ((u - cx) / fx) z, y = ((v - cy) / fy) z, e_k = ((R_k0 x + R_k1 y) + R_k2 z) + t_k,
+// rounded to float.  A depth outside (z_min, z_max] gives a NO_RETURN ray at z_max.
+__device__ __forceinline__ bool depth_ray(const DepthFrame& f, long long pix, float e[3], double pt[3]) {
+  const int u = (int)(pix % f.width), v = (int)(pix / f.width);
+  const double z = (double)f.depth[pix];
+  const bool valid = z > f.z_min && z <= f.z_max;
+  const double zz = valid ? z : f.z_max;
+  const double px = __ddiv_rn(__dsub_rn((double)u, f.cx), f.fx);
+  const double py = __ddiv_rn(__dsub_rn((double)v, f.cy), f.fy);
+  const double x = __dmul_rn(px, zz), y = __dmul_rn(py, zz);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    double a = __dmul_rn(f.R[3 * k], x);
+    a = __dadd_rn(a, __dmul_rn(f.R[3 * k + 1], y));
+    a = __dadd_rn(a, __dmul_rn(f.R[3 * k + 2], zz));
+    a = __dadd_rn(a, f.t[k]);
+    e[k] = __double2float_rn(a);
+  }
+  pt[0] = px;
+  pt[1] = py;
+  pt[2] = 1.0;
+  return valid;
+}
+
+__global__ void __launch_bounds__(kBlock) k_depth_rays(DepthFrame f, float* origins, float* endpoints, uint8_t* flags) {
+  const long long n = (long long)f.width * f.height;
+  if (blockIdx.x == 0 && threadIdx.x < 3) origins[threadIdx.x] = __double2float_rn(f.t[threadIdx.x]);
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+    float e[3];
+    double pt[3];
+    const bool valid = depth_ray(f, p, e, pt);
+    endpoints[3 * p + 0] = e[0];
+    endpoints[3 * p + 1] = e[1];
+    endpoints[3 * p + 2] = e[2];
+    flags[p] = valid ? 0 : kFlagNoReturn;
+  }
+}
+
+__device__ __forceinline__ long long point_offset(const DeviceMap& m, const float* p) {
+  long long q[3];
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) ok = ok && isfinite(p[k]) && quantise(p[k], m.origin[k], m.scale, &q[k]);
+  ok = ok && in_extent(q, m.frac_bits);
+  if (!ok) return -1;
+  const int F = m.frac_bits;
+  const int32_t vx = (int32_t)(q[0] >> F), vy = (int32_t)(q[1] >> F), vz = (int32_t)(q[2] >> F);
+  const int32_t slot = region_slot_of(m, vx, vy, vz);
+  return slot < 0 ? -1 : voxel_offset(slot, local_morton(vx, vy, vz));
+}
+
+// G(v) += g_q for each query point (clear = 0), or G(v) = 0 (clear = 1).
+__global__ void __launch_bounds__(kBlock) k_grad_scatter(DeviceMap m, const float* pts, const float* g, long long n,
+                                                         int clear) {
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    const long long off = point_offset(m, pts + 3 * q);
+    if (off < 0) continue;
+    if (clear)
+      m.grad[off] = 0.f;
+    else
+      atomicAdd(m.grad + off, g[q]);
+  }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(kBlock) k_tsdf_backward(DeviceMap m, DepthFrame f, float* grad_depth,
+                                                          double* grad_twist) {
+  __shared__ double red[kBlock / 32][6];
+  const long long n = (long long)f.width * f.height;
+  const int F = m.frac_bits;
+  const long long U = 1LL << F;
+  const long long half = U >> 1;
+  const float to_m = (float)(m.voxel_size / (double)U);
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long n_round = (n + stride - 1) / stride * stride;  // whole blocks iterate together
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n_round; p += stride) {
+    float gz = 0.f;
+    if (p < n) {
+      float e[3], o[3];
+      double pt[3];
+      bool ok = depth_ray(f, p, e, pt);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) o[k] = __double2float_rn(f.t[k]);
+      long long qo[3], qe[3];
+      ok = ok && quantise_ray(m, o, e, qo, qe);
+      double d[3], len = 0.0;
+      if (ok) {
+        len = ray_length(qo, qe, d);
+        ok = len > m.rmin_q && len <= m.rmax_q && in_extent(qo, F) && in_extent(qe, F);
+      }
+      if (ok) {
+        // the band walk of the forward pass, recomputed
+        double t0 = __dsub_rn(len, m.tau_q);
+        if (t0 < 0.0) t0 = 0.0;
+        const double t1 = __dadd_rn(len, m.tau_q);
+        const double f0 = __ddiv_rn(t0, len), f1 = __ddiv_rn(t1, len);
+        long long a[3], b[3];
+        float u[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          a[k] = qo[k] + __double2ll_rn(__dmul_rn(d[k], f0));
+          b[k] = qo[k] + __double2ll_rn(__dmul_rn(d[k], f1));
+          u[k] = (float)__ddiv_rn(d[k], len);
+        }
+        const float dm = (float)(len * m.voxel_size / (double)U);
+        Walker w;
+        walker_init(w, a, b, F, 0, 0);
+        int32_t slot = region_slot_of(m, w.vx, w.vy, w.vz);
+        uint32_t mo = local_morton(w.vx, w.vy, w.vz);
+        float A = 0.f, B[3] = {0.f, 0.f, 0.f};
+        while (slot >= 0) {
+          const long long off = voxel_offset(slot, mo);
+          const float G = m.grad[off];
+          if (G != 0.f) {
+            const float ex = (float)(qe[0] - ((long long)w.vx * U + half));
+            const float ey = (float)(qe[1] - ((long long)w.vy * U + half));
+            const float ez = (float)(qe[2] - ((long long)w.vz * U + half));
+            const float s = (ex * u[0] + ey * u[1] + ez * u[2]) * to_m;  // as in the forward pass
+            if (s > -m.tau_m && s < m.tau_m) {
+              const float wv = G / m.tsdf[off].y;
+              const float r[3] = {ex * to_m, ey * to_m, ez * to_m};
+              A += wv;
+#pragma unroll
+              for (int k = 0; k < 3; ++k) B[k] += wv * (r[k] - s * u[k]);
+            }
+          }
+          if (w.total == 0) break;
+          const int axis = walker_choose(w);
+          int32_t c, sg;
+          walker_step(w, axis, &c, &sg);
+          mo = morton_step(mo, morton_mask(axis), sg);
+          if ((c & ((1 << kRegionShift) - 1)) == (sg > 0 ? 0 : (1 << kRegionShift) - 1))
+            slot = region_slot_of(m, w.vx, w.vy, w.vz);
+        }
+        double ge[3], go[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          ge[k] = (double)A * u[k] + (double)B[k] / dm;
+          go[k] = -(double)B[k] / dm;
+        }
+        double dz = 0.0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) dz += ge[k] * (f.R[3 * k] * pt[0] + f.R[3 * k + 1] * pt[1] + f.R[3 * k + 2] * pt[2]);
+        gz = (float)dz;
+        const double E[3] = {e[0], e[1], e[2]}, O[3] = {f.t[0], f.t[1], f.t[2]};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) acc[k] += ge[k] + go[k];
+        acc[3] += E[1] * ge[2] - E[2] * ge[1] + O[1] * go[2] - O[2] * go[1];
+        acc[4] += E[2] * ge[0] - E[0] * ge[2] + O[2] * go[0] - O[0] * go[2];
+        acc[5] += E[0] * ge[1] - E[1] * ge[0] + O[0] * go[1] - O[1] * go[0];
+      }
+      grad_depth[p] = gz;
+    }
+  }
+  // block reduction of the twist gradient, one double atomic per component
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const double v = warp_sum(acc[k]);
+    if (lane == 0) red[wid][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    double v = 0.0;
+    for (int i = 0; i < kBlock / 32; ++i) v += red[i][threadIdx.x];
+    atomicAdd(grad_twist + threadIdx.x, v);
+  }
+}
+
+bool frame_from(const float* depth, int32_t width, int32_t height, const double* K, const double* pose, double z_min,
+                double z_max, DepthFrame* f) {
+  if (!depth || width < 1 || height < 1 || !K || !pose || !(z_max > z_min)) return false;
+  f->depth = depth;
+  f->width = width;
+  f->height = height;
+  f->fx = K[0];
+  f->fy = K[1];
+  f->cx = K[2];
+  f->cy = K[3];
+  for (int r = 0; r < 3; ++r) {
+    for (int c = 0; c < 3; ++c) f->R[3 * r + c] = pose[4 * r + c];
+    f->t[r] = pose[4 * r + 3];
+  }
+  f->z_min = z_min;
+  f->z_max = z_max;
+  return f->fx != 0.0 && f->fy != 0.0;
+}
+
+ohm_status afail(ohm_status code, const std::string& msg) {
+  set_last_error(msg);
+  return code;
+}
+
+bool is_device(const void* p) {
+  cudaPointerAttributes a;
+  if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+}  // namespace ohm
+
+extern "C" {
+
+ohm_status ohm_integrate_depth(ohm_map* map, const float* depth, int32_t width, int32_t height,
+                               const double* intrinsics, const double* pose, double z_min, double z_max,
+                               void* stream) {
+  using namespace ohm;
+  if (!map) return afail(OHM_ERR_INVALID, "integrate_depth: map is NULL");
+  DepthFrame f;
+  if (!frame_from(depth, width, height, intrinsics, pose, z_min, z_max, &f))
+    return afail(OHM_ERR_INVALID, "integrate_depth: bad image, intrinsics, pose or depth range");
+  const long long n = (long long)width * height;
+  if (n > map->p.max_rays) return afail(OHM_ERR_INVALID, "integrate_depth: width * height exceeds max_rays");
+  if (!is_device(depth)) return afail(OHM_ERR_INVALID, "integrate_depth: depth must be device memory");
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != map->device) cudaSetDevice(map->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int blocks = (int)((n + kBlock - 1) / kBlock < 4096 ? (n + kBlock - 1) / kBlock : 4096);
+  k_depth_rays<<<blocks, kBlock, 0, s>>>(f, map->stage_origins, map->stage_endpoints, map->stage_flags);
+  map->launches += 1;
+  CallArgs a;
+  a.origins = map->stage_origins;
+  a.endpoints = map->stage_endpoints;
+  a.flags = map->stage_flags;
+  a.n = n;
+  a.n_origins = 1;
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = launch_integrate(map, a, s);
+  if (prev >= 0 && prev != map->device) cudaSetDevice(prev);
+  if (e != cudaSuccess) return afail(OHM_ERR_CUDA, std::string("integrate_depth: ") + cudaGetErrorString(e));
+  return OHM_OK;
+}
+
+ohm_status ohm_tsdf_backward(ohm_map* map, const float* depth, int32_t width, int32_t height,
+                             const double* intrinsics, const double* pose, double z_min, double z_max,
+                             const float* query_points, const float* grad_query, int64_t n_query, float* grad_depth,
+                             double* grad_twist, void* stream) {
+  using namespace ohm;
+  if (!map) return afail(OHM_ERR_INVALID, "tsdf_backward: map is NULL");
+  if (!(map->p.layers & OHM_LAYER_TSDF)) return afail(OHM_ERR_UNSUPPORTED, "tsdf_backward: map has no TSDF layer");
+  DepthFrame f;
+  if (!frame_from(depth, width, height, intrinsics, pose, z_min, z_max, &f))
+    return afail(OHM_ERR_INVALID, "tsdf_backward: bad image, intrinsics, pose or depth range");
+  if (n_query < 0 || (n_query > 0 && (!query_points || !grad_query)) || !grad_depth || !grad_twist)
+    return afail(OHM_ERR_INVALID, "tsdf_backward: NULL buffer");
+  const void* bufs[] = {depth, grad_depth, grad_twist};
+  for (const void* b : bufs)
+    if (!is_device(b)) return afail(OHM_ERR_INVALID, "tsdf_backward: buffers must be device memory");
+  if (n_query > 0 && (!is_device(query_points) || !is_device(grad_query)))
+    return afail(OHM_ERR_INVALID, "tsdf_backward: buffers must be device memory");
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != map->device) cudaSetDevice(map->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSuccess;
+  if (!map->d.grad) {
+    // per-voxel gradient weights, allocated on the first backward call
+    e = cudaMalloc(reinterpret_cast<void**>(&map->d.grad), sizeof(float) * (size_t)map->p.max_regions * kRegionVoxels);
+    if (e == cudaSuccess) e = cudaMemset(map->d.grad, 0, sizeof(float) * (size_t)map->p.max_regions * kRegionVoxels);
+  }
+  const long long n = (long long)width * height;
+  const int qb = (int)(n_query > 0 ? ((n_query + kBlock - 1) / kBlock < 4096 ? (n_query + kBlock - 1) / kBlock : 4096) : 0);
+  const int pb = (int)((n + kBlock - 1) / kBlock < 4096 ? (n + kBlock - 1) / kBlock : 4096);
+  if (e == cudaSuccess) e = cudaMemsetAsync(grad_twist, 0, 6 * sizeof(double), s);
+  if (e == cudaSuccess && qb) {
+    k_grad_scatter<<<qb, kBlock, 0, s>>>(map->d, query_points, grad_query, n_query, 0);
+    map->launches += 1;
+  }
+  if (e == cudaSuccess) {
+    k_tsdf_backward<<<pb, kBlock, 0, s>>>(map->d, f, grad_depth, grad_twist);
+    map->launches += 1;
+  }
+  if (e == cudaSuccess && qb) {
+    k_grad_scatter<<<qb, kBlock, 0, s>>>(map->d, query_points, grad_query, n_query, 1);
+    map->launches += 1;
+  }
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (prev >= 0 && prev != map->device) cudaSetDevice(prev);
+  if (e != cudaSuccess) return afail(OHM_ERR_CUDA, std::string("tsdf_backward: ") + cudaGetErrorString(e));
+  return OHM_OK;
+}
+
+}  // extern "C"

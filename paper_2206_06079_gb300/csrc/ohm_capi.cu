@@ -63,7 +63,7 @@ void free_map(ohm_map* m) {
   if (!m) return;
   ohm::DeviceMap& d = m->d;
   void* ptrs[] = {d.htab, d.region_count, d.region_coords, d.occ, d.counts, d.ndt_slot, d.ndt_count,
-                  d.ndt, d.tsdf, d.tsdf_cnt, d.tsdf_sum, d.status, d.calls, d.rays, d.trays, d.segs, d.touched,
+                  d.ndt, d.tsdf, d.tsdf_cnt, d.tsdf_sum, d.grad, d.status, d.calls, d.rays, d.trays, d.segs, d.touched,
                   m->stage_origins, m->stage_endpoints, m->stage_flags};
   for (void* p : ptrs)
     if (p) cudaFree(p);

@@ -80,6 +80,7 @@ struct DeviceMap {
   float2* tsdf;                  // [max_regions][32768] (D, W)
   uint32_t* tsdf_cnt;            // [max_regions][32768] per-call scratch, zero between calls
   long long* tsdf_sum;           // [max_regions][32768] per-call scratch, 2^-32 m units
+  float* grad;                   // [max_regions][32768] adjoint weights, allocated by the first backward call
   int32_t* status;
   CallCounters* calls;
   // per-call scratch

@@ -28,7 +28,8 @@ _STATUS_NAMES = {ERR_INVALID: "invalid argument", ERR_CAPACITY: "capacity", ERR_
 EXPORTED = ["ohm_map_create", "ohm_map_destroy", "ohm_integrate_rays", "ohm_integrate_rays_async", "ohm_map_sync",
             "ohm_query_voxels", "ohm_map_region_count", "ohm_map_export", "ohm_map_stats", "ohm_map_profile",
             "ohm_map_profile_read", "ohm_last_error", "ohm_count_rays_noalloc", "ohm_batch_create",
-            "ohm_batch_destroy", "ohm_batch_tune", "ohm_batch_integrate", "ohm_batch_sync", "ohm_batch_stats"]
+            "ohm_batch_destroy", "ohm_batch_tune", "ohm_batch_integrate", "ohm_batch_sync", "ohm_batch_stats",
+            "ohm_integrate_depth", "ohm_tsdf_backward"]
 
 BATCH_MAX_MAPS = 32
 
@@ -134,6 +135,13 @@ def load_library(path: str = LIB_PATH):
     lib.ohm_batch_sync.argtypes = [vp, vp]
     lib.ohm_batch_stats.restype = st
     lib.ohm_batch_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.ohm_integrate_depth.restype = st
+    lib.ohm_integrate_depth.argtypes = [vp, p, ctypes.c_int32, ctypes.c_int32, dp, dp, ctypes.c_double,
+                                        ctypes.c_double, vp]
+    lib.ohm_tsdf_backward.restype = st
+    lib.ohm_tsdf_backward.argtypes = [vp, p, ctypes.c_int32, ctypes.c_int32, dp, dp, ctypes.c_double, ctypes.c_double,
+                                      p, p, i64, p, p, vp]
     lib.ohm_last_error.restype = ctypes.c_char_p
     lib.ohm_last_error.argtypes = []
     _lib = lib
@@ -243,6 +251,42 @@ class Map:
 
     def sync(self, stream=None):
         _check(load_library().ohm_map_sync(self._h, _stream_handle(stream)))
+
+    @staticmethod
+    def _frame_args(K, pose):
+        k = (ctypes.c_double * 4)(*[float(v) for v in K])
+        P = np.asarray(pose, np.float64).reshape(3, 4)
+        p = (ctypes.c_double * 12)(*[float(v) for v in P.reshape(-1)])
+        return k, p
+
+    def integrate_depth(self, depth, K, pose, z_min=0.3, z_max=6.0, stream=None, sync=True):
+        """Integrate a z-depth image (CUDA float32 tensor, height x width) seen
+        from pose (3 x 4 camera-to-world) with intrinsics K = (fx, fy, cx, cy)."""
+        d = depth.contiguous()
+        if d.dtype != torch.float32 or not d.is_cuda:
+            raise TypeError("depth must be a CUDA float32 tensor")
+        k, p = self._frame_args(K, pose)
+        h, w = d.shape
+        _check(load_library().ohm_integrate_depth(self._h, _ptr(d), int(w), int(h), k, p, float(z_min), float(z_max),
+                                                  _stream_handle(stream)))
+        if sync:
+            self.sync(stream)
+
+    def tsdf_backward(self, depth, K, pose, query_points, grad_query, z_min=0.3, z_max=6.0, stream=None):
+        """(dL/d depth (height x width), dL/d twist (6,)) for
+        L = sum_q grad_query[q] * D(query_points[q]) right after
+        integrate_depth of the same frame (voxel sets held fixed)."""
+        d = depth.contiguous()
+        q = _as_points(query_points, "query_points")
+        g = grad_query.contiguous().float()
+        gd = torch.empty_like(d)
+        gt = torch.empty(6, dtype=torch.float64, device=d.device)
+        k, p = self._frame_args(K, pose)
+        h, w = d.shape
+        _check(load_library().ohm_tsdf_backward(self._h, _ptr(d), int(w), int(h), k, p, float(z_min), float(z_max),
+                                                _ptr(q), _ptr(g), int(q.shape[0]), _ptr(gd), _ptr(gt),
+                                                _stream_handle(stream)))
+        return gd, gt
 
     def query(self, points, stream=None, ndt=False, tsdf=False, counts=False):
         """Look up world points; returns a dict of CUDA tensors."""
@@ -385,3 +429,44 @@ class Batch:
         a, b = ctypes.c_int64(), ctypes.c_int64()
         _check(load_library().ohm_batch_stats(self._h, ctypes.byref(a), ctypes.byref(b)))
         return {"kernel_launches": int(a.value), "graph_launches": int(b.value)}
+
+
+def twist_pose(xi, pose0):
+    """exp(xi) applied on the left of a 3 x 4 camera-to-world pose (float64 numpy)."""
+    xi = np.asarray(xi, np.float64)
+    rho, phi = xi[:3], xi[3:]
+    th = float(np.linalg.norm(phi))
+    Kx = np.array([[0, -phi[2], phi[1]], [phi[2], 0, -phi[0]], [-phi[1], phi[0], 0]])
+    if th < 1e-12:
+        R, V = np.eye(3) + Kx, np.eye(3) + 0.5 * Kx
+    else:
+        R = np.eye(3) + np.sin(th) / th * Kx + (1 - np.cos(th)) / th ** 2 * Kx @ Kx
+        V = np.eye(3) + (1 - np.cos(th)) / th ** 2 * Kx + (th - np.sin(th)) / th ** 3 * Kx @ Kx
+    P0 = np.asarray(pose0, np.float64).reshape(3, 4)
+    return np.concatenate([R @ P0[:, :3], (R @ P0[:, 3] + V @ rho)[:, None]], 1)
+
+
+class TsdfFrame(torch.autograd.Function):
+    """D at query points after integrating one depth frame, differentiable in
+    the per-pixel depth and in a pose twist xi applied on the left of pose0.
+
+    forward(depth, xi, gmap, K, pose0, query_points, z_min, z_max) integrates
+    the frame into gmap (a side effect: calling it twice integrates twice) and
+    returns D at the query points.  backward gives dL/d depth and the
+    tangent-space pose gradient at the evaluated pose (the derivative with
+    respect to xi at xi = 0), with the walk's voxel sets held fixed."""
+
+    @staticmethod
+    def forward(ctx, depth, xi, gmap, K, pose0, query_points, z_min=0.3, z_max=6.0):
+        pose = twist_pose(xi.detach().cpu().numpy(), pose0)
+        gmap.integrate_depth(depth.detach(), K, pose, z_min, z_max)
+        out = gmap.query(query_points, tsdf=True)["tsdf"][:, 0]
+        ctx.gmap, ctx.K, ctx.pose, ctx.z = gmap, K, pose, (z_min, z_max)
+        ctx.save_for_backward(depth.detach(), query_points)
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        depth, q = ctx.saved_tensors
+        gd, gt = ctx.gmap.tsdf_backward(depth, ctx.K, ctx.pose, q, grad_out, *ctx.z)
+        return gd, gt.to(grad_out.dtype), None, None, None, None, None, None

@@ -1,0 +1,153 @@
+"""TSDF adjoint on the GPU (ohm_tsdf_backward behind a torch.autograd.Function)
+against the oracle's float64 analytic gradient and central finite
+differences, voxel sets held fixed; tolerance 1e-3 relative."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import adjoint
+from paper_2206_06079_gb300 import ohm, synth, workloads as W
+
+from .parity import compare_dense
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+    assert torch.cuda.is_available()
+
+
+def _intrinsics(w, h):
+    s = w / 640.0
+    return (525.0 * s, 525.0 * s, (w - 1) / 2.0, (h - 1) / 2.0)
+
+
+def _frame(scene, i, w, h):
+    K = _intrinsics(w, h)
+    depth, pos, R = synth.depth_frame(scene, i, width=w, height=h, fx=K[0], fy=K[1], cx=K[2], cy=K[3])
+    return depth.numpy(), np.concatenate([R.numpy(), pos.numpy()[:, None]], 1), K
+
+
+def _continuous(depth, pose, K):
+    fx, fy, cx, cy = K
+    h, w = depth.shape
+    vv, uu = np.meshgrid(np.arange(h, dtype=np.float64), np.arange(w, dtype=np.float64), indexing="ij")
+    z = depth.astype(np.float64).reshape(-1)
+    z = np.where((z > 0.3) & (z <= 6.0), z, 6.0)
+    pc = np.stack([(uu.reshape(-1) - cx) / fx * z, (vv.reshape(-1) - cy) / fy * z, z], 1)
+    return pose[:, 3].astype(np.float64), pc @ pose[:, :3].T + pose[:, 3]
+
+
+def _setup(w, h, n_query=2000, seed=0):
+    scene = synth.depth_scene()
+    p = W.tsdf_params(max_rays=w * h)
+    gm = ohm.Map(**p)
+    om = oracle.OracleMap(**W.oracle_params(p))
+    d0, p0, K = _frame(scene, 2, w, h)
+    gm.integrate_depth(torch.from_numpy(d0).cuda(), K, p0)
+    o, e, f, _ = adjoint.depth_rays(d0, K, p0, 0.3, 6.0)
+    om.integrate(o, e, f)
+    compare_dense(gm, om, occupancy=False, counts=False, tsdf=True)  # depth entry point == oracle rays
+    depth, pose, K = _frame(scene, 6, w, h)
+    o, e, f, pt = adjoint.depth_rays(depth, K, pose, 0.3, 6.0)
+    rng = np.random.default_rng(seed)
+    sel = np.flatnonzero(f == 0)
+    pick = rng.choice(sel, size=n_query, replace=True)
+    u = e[pick] - o[0]
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    qvox = np.floor((e[pick] + rng.uniform(-0.18, 0.18, size=(n_query, 1)) * u) / 0.05).astype(np.int64)
+    qvox = np.unique(qvox, axis=0)
+    g = rng.normal(size=len(qvox)).astype(np.float32)
+    return gm, om, depth, pose, K, (o, e, f, pt), qvox, g
+
+
+@pytest.mark.parametrize("size", [(160, 120), (640, 480)])
+def test_gpu_adjoint_matches_oracle(size):
+    w, h = size
+    gm, om, depth, pose, K, (o, e, f, pt), qvox, g = _setup(w, h)
+    o64, e64 = _continuous(depth, pose, K)
+    L, ge, go = adjoint.frame_eval(om, o[0], e, f, o64, e64, qvox, g.astype(np.float64))
+    gz_ref, gxi_ref = adjoint.chain_to_depth_and_twist(ge, go, e64, o64, pose[:, :3], pt)
+    # GPU forward of the frame, then its adjoint
+    dt = torch.from_numpy(depth).cuda()
+    gm.integrate_depth(dt, K, pose)
+    qpts = torch.from_numpy(((qvox + 0.5) * 0.05).astype(np.float32)).cuda()
+    gd, gxi = gm.tsdf_backward(dt, K, pose, qpts, torch.from_numpy(g).cuda())
+    gd = gd.cpu().numpy().reshape(-1).astype(np.float64)
+    gxi = gxi.cpu().numpy()
+    # the forward still matches the oracle after this frame
+    om.integrate(o, e, f)
+    compare_dense(gm, om, occupancy=False, counts=False, tsdf=True)
+    scale = np.abs(gz_ref).max()
+    assert scale > 0
+    err = np.abs(gd - gz_ref)
+    assert np.linalg.norm(gd - gz_ref) <= 1e-3 * np.linalg.norm(gz_ref)
+    big = np.abs(gz_ref) > 1e-2 * scale
+    # per pixel: relative 1e-3; a pixel may differ where float32 and float64
+    # disagree on whether one of its voxels sits exactly at the clamp
+    frac_ok = np.mean(err[big] <= 1e-3 * np.abs(gz_ref[big]) + 1e-6 * scale)
+    assert frac_ok >= 0.995, frac_ok
+    assert np.linalg.norm(gxi - gxi_ref) <= 1e-3 * np.linalg.norm(gxi_ref), (gxi, gxi_ref)
+
+
+def test_gpu_adjoint_against_finite_differences():
+    """Central differences (h = 1e-4) of the oracle's float64 frozen-set loss."""
+    w, h = 160, 120
+    gm, om, depth, pose, K, (o, e, f, pt), qvox, g = _setup(w, h, seed=1)
+    dt = torch.from_numpy(depth).cuda()
+    gm.integrate_depth(dt, K, pose)
+    qpts = torch.from_numpy(((qvox + 0.5) * 0.05).astype(np.float32)).cuda()
+    gd, gxi = gm.tsdf_backward(dt, K, pose, qpts, torch.from_numpy(g).cuda())
+    gd = gd.cpu().numpy().reshape(-1)
+    g64 = g.astype(np.float64)
+    hstep = 1e-4
+    rng = np.random.default_rng(2)
+    cand = np.flatnonzero((f == 0) & (np.abs(gd) > 1e-3 * np.abs(gd).max()))
+    checked = 0
+    for j in rng.choice(cand, size=min(30, len(cand)), replace=False):
+        fd = []
+        for hh in (hstep, hstep / 2):
+            z = depth.astype(np.float64).reshape(-1).copy()
+            z[j] += hh
+            Lp = adjoint.frame_eval(om, o[0], e, f, *_continuous(z.reshape(depth.shape), pose, K), qvox, g64)[0]
+            z[j] -= 2 * hh
+            Lm = adjoint.frame_eval(om, o[0], e, f, *_continuous(z.reshape(depth.shape), pose, K), qvox, g64)[0]
+            fd.append((Lp - Lm) / (2 * hh))
+        if abs(fd[0] - fd[1]) > 1e-5 * max(1.0, abs(fd[1])):
+            continue  # a clamp kink within h
+        checked += 1
+        assert abs(gd[j] - fd[0]) <= 1e-3 * abs(fd[0]) + 1e-6, (j, gd[j], fd[0])
+    assert checked >= 20
+    o64, e64 = _continuous(depth, pose, K)
+    fdxi = np.zeros(6)
+    for k in range(6):
+        xi = np.zeros(6)
+        xi[k] = hstep
+        Tp, Tm = adjoint.twist_matrix(xi), adjoint.twist_matrix(-xi)
+        Lp = adjoint.frame_eval(om, o[0], e, f, Tp[:3, :3] @ o64 + Tp[:3, 3], e64 @ Tp[:3, :3].T + Tp[:3, 3], qvox, g64)[0]
+        Lm = adjoint.frame_eval(om, o[0], e, f, Tm[:3, :3] @ o64 + Tm[:3, 3], e64 @ Tm[:3, :3].T + Tm[:3, 3], qvox, g64)[0]
+        fdxi[k] = (Lp - Lm) / (2 * hstep)
+    assert np.linalg.norm(gxi.cpu().numpy() - fdxi) <= 2e-3 * np.linalg.norm(fdxi), (gxi, fdxi)
+
+
+def test_autograd_function_wraps_the_kernel():
+    w, h = 160, 120
+    gm, om, depth, pose, K, _, qvox, g = _setup(w, h, seed=3)
+    gm2 = ohm.Map(**W.tsdf_params(max_rays=w * h))
+    scene = synth.depth_scene()
+    d0, p0, _ = _frame(scene, 2, w, h)
+    gm2.integrate_depth(torch.from_numpy(d0).cuda(), K, p0)
+    dt = torch.from_numpy(depth).cuda().requires_grad_(True)
+    xi = torch.zeros(6, dtype=torch.float64, requires_grad=True)
+    qpts = torch.from_numpy(((qvox + 0.5) * 0.05).astype(np.float32)).cuda()
+    gq = torch.from_numpy(g).cuda()
+    out = ohm.TsdfFrame.apply(dt, xi, gm, K, pose, qpts)
+    (out * gq).sum().backward()
+    gm2.integrate_depth(dt.detach(), K, pose)
+    ref_d, ref_xi = gm2.tsdf_backward(dt.detach(), K, pose, qpts, gq)
+    assert torch.equal(dt.grad, ref_d)
+    assert torch.allclose(xi.grad, ref_xi.cpu().to(xi.grad.dtype))
