@@ -462,6 +462,7 @@ class TsdfFrame(torch.autograd.Function):
         gmap.integrate_depth(depth.detach(), K, pose, z_min, z_max)
         out = gmap.query(query_points, tsdf=True)["tsdf"][:, 0]
         ctx.gmap, ctx.K, ctx.pose, ctx.z = gmap, K, pose, (z_min, z_max)
+        ctx.xi_like = (xi.dtype, xi.device)
         ctx.save_for_backward(depth.detach(), query_points)
         return out
 
@@ -469,4 +470,4 @@ class TsdfFrame(torch.autograd.Function):
     def backward(ctx, grad_out):
         depth, q = ctx.saved_tensors
         gd, gt = ctx.gmap.tsdf_backward(depth, ctx.K, ctx.pose, q, grad_out, *ctx.z)
-        return gd, gt.to(grad_out.dtype), None, None, None, None, None, None
+        return gd, gt.to(dtype=ctx.xi_like[0], device=ctx.xi_like[1]), None, None, None, None, None, None
