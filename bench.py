@@ -438,6 +438,73 @@ def run_multimap(args):
     print(json.dumps(out), flush=True)
 
 
+def run_tsdf(args):
+    """Depth-camera TSDF workload: 640 x 480 frames (fx = fy = 525, 0.3-6 m)
+    around a room with 20 boxes and 10 spheres, 0.05 m voxels, tau = 0.2 m.
+    Times the forward integration (ohm_integrate_depth) per frame and, on
+    the same frames, forward + adjoint (ohm_tsdf_backward against 20,000
+    query voxels)."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2206_06079_gb300 import ohm, synth, workloads as W
+
+    dev = torch.device("cuda", 0)
+    scene = synth.depth_scene()
+    w, h = 640, 480
+    K = (525.0, 525.0, 319.5, 239.5)
+    n_frames = min(64, args.warmup + args.steps)
+    frames = []
+    for i in range(n_frames):
+        depth, pos, R = synth.depth_frame(scene, i, width=w, height=h, device=dev)
+        frames.append((depth.contiguous(), np.concatenate([R.numpy(), pos.numpy()[:, None]], 1)))
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    gm = ohm.Map(**W.tsdf_params(device=0))
+    for k in range(args.warmup):
+        d, P = frames[k % n_frames]
+        gm.integrate_depth(d, K, P, sync=False)
+    gm.sync()
+    st0 = gm.stats()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        d, P = frames[(args.warmup + k) % n_frames]
+        gm.integrate_depth(d, K, P, sync=False)
+    e1.record(stream)
+    gm.sync()
+    fwd_ms = e0.elapsed_time(e1) / args.steps
+    st1 = gm.stats()
+    visits = (st1["total_visits"] - st0["total_visits"]) / args.steps
+    # forward + adjoint
+    rng = np.random.default_rng(5)
+    q = torch.from_numpy(rng.uniform([-3, -3, 0], [3, 3, 3], size=(20000, 3)).astype(np.float32)).to(dev)
+    gq = torch.from_numpy(rng.normal(size=20000).astype(np.float32)).to(dev)
+    gm2 = ohm.Map(**W.tsdf_params(device=0))
+    for k in range(args.warmup):
+        d, P = frames[k % n_frames]
+        gm2.integrate_depth(d, K, P, sync=False)
+        gm2.tsdf_backward(d, K, P, q, gq)
+    gm2.sync()
+    e0.record(stream)
+    for k in range(args.steps):
+        d, P = frames[(args.warmup + k) % n_frames]
+        gm2.integrate_depth(d, K, P, sync=False)
+        gm2.tsdf_backward(d, K, P, q, gq)
+    e1.record(stream)
+    gm2.sync()
+    fb_ms = e0.elapsed_time(e1) / args.steps
+    rays = w * h
+    out = {"metric": METRIC, "workload": "tsdf", "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "value": rays / (fwd_ms / 1e3), "ms_per_step": fwd_ms,
+           "voxel_updates_per_s": visits / (fwd_ms / 1e3), "higher_is_better": True,
+           "forward_backward_ms_per_frame": fb_ms, "backward_ms_per_frame": fb_ms - fwd_ms,
+           "config": {"workload": "640x480 depth frames, 0.05 m voxels, tau 0.2 m, TSDF layer", "frames": n_frames,
+                      "band_visits_per_frame": visits, "adjoint_query_voxels": 20000}}
+    print(json.dumps(out), flush=True)
+
+
 def run_reference(args):
     """The oracle as the reference arm: rank 0 only, host cores."""
     ws, rank, local = _dist()
@@ -494,8 +561,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--segment-steps", type=int, default=0, help="ray segment length (0 = library default)")
-    ap.add_argument("--workload", default="tunnel", choices=["tunnel", "multimap"],
-                    help="tunnel: the single-map headline; multimap: 16 maps, single-scan vs batched path")
+    ap.add_argument("--workload", default="tunnel", choices=["tunnel", "multimap", "tsdf"],
+                    help="tunnel: the single-map headline; multimap: 16 maps, single-scan vs batched path; "
+                         "tsdf: depth frames, forward and adjoint")
     ap.add_argument("--profile-case", action="store_true",
                     help="small pools (a few GB on the device), no e2e or CPU leg: the case ncu captures")
     args = ap.parse_args()
@@ -505,6 +573,8 @@ def main():
         run_reference(args)
     elif args.workload == "multimap":
         run_multimap(args)
+    elif args.workload == "tsdf":
+        run_tsdf(args)
     else:
         run_ours(args)
 
