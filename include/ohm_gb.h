@@ -69,6 +69,9 @@ typedef struct {
   float hit;               /* log-odds increment for a sample, log(P(z|occ)/P(z|emp)) (Eq. 3) */
   float miss;              /* log-odds increment for a pass-through (Eq. 3) */
   float l_min, l_max;      /* clamp bounds (Sec. II-B) */
+  float ndt_clear_below;   /* NDT layer: a miss that takes a voxel's log-odds from at or above this
+                              value (or from unknown) to below it clears the voxel's samples
+                              (Sec. II-D); -INFINITY never clears */
   double max_range;        /* rays are truncated to this length and lose their sample (Sec. IV-A) */
   double min_range;        /* TSDF only: samples at or below this range are ignored */
   double tsdf_trunc;       /* TSDF truncation distance tau in metres */

@@ -35,6 +35,7 @@ class OracleParams(ctypes.Structure):
         ("miss", ctypes.c_float),
         ("l_min", ctypes.c_float),
         ("l_max", ctypes.c_float),
+        ("ndt_clear_below", ctypes.c_float),
         ("max_range", ctypes.c_double),
         ("min_range", ctypes.c_double),
         ("tsdf_trunc", ctypes.c_double),
@@ -85,7 +86,7 @@ def default_params(**kw) -> dict:
     p = dict(voxel_size=0.1, map_origin=(0.0, 0.0, 0.0), frac_bits=16,
              layers=LAYER_OCCUPANCY | LAYER_COUNTS,
              hit=float(np.float32(logit(0.7))), miss=float(np.float32(logit(0.4))),
-             l_min=-2.0, l_max=3.5, max_range=20.0, min_range=0.0,
+             l_min=-2.0, l_max=3.5, ndt_clear_below=float("-inf"), max_range=20.0, min_range=0.0,
              tsdf_trunc=0.2, tsdf_wmax=float(1 << 20))
     p.update(kw)
     return p

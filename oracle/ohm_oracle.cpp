@@ -69,6 +69,7 @@ struct OracleParams {
   float miss;            // log-odds increment for a pass-through (Eq. 3)
   float l_min;           // lower clamp (Sec. II-B)
   float l_max;           // upper clamp (Sec. II-B)
+  float ndt_clear_below; // NDT samples are cleared when a miss takes l below this (Sec. II-D)
   double max_range;      // truncation length (Sec. IV-A)
   double min_range;      // TSDF: samples at or below this range are ignored
   double tsdf_trunc;     // TSDF truncation distance tau
@@ -257,7 +258,13 @@ void apply_miss(Map& m, const Voxel& v) {
     float l = r.occupancy[i];
     float l0 = std::isnan(l) ? 0.0f : l;
     float u = l0 + m.p.miss;
-    r.occupancy[i] = std::fmin(std::fmax(u, m.p.l_min), m.p.l_max);
+    float ln = std::fmin(std::fmax(u, m.p.l_min), m.p.l_max);
+    r.occupancy[i] = ln;
+    // Sample clearing (Sec. II-D): falling below the threshold (from at or
+    // above it, or from unknown) drops the voxel's NDT samples.
+    const bool was_above = std::isnan(l) || !(l < m.p.ndt_clear_below);
+    if (was_above && ln < m.p.ndt_clear_below && !r.ndt.empty())
+      for (int k = 0; k < 10; ++k) r.ndt[(size_t)i * 10 + k] = 0;
   }
   if (m.p.layers & kLayerCounts) r.misses[i] += 1u;
 }

@@ -142,6 +142,7 @@ ohm_status ohm_map_create(const ohm_map_params* params, ohm_map** out) {
   const uint32_t all = OHM_LAYER_OCCUPANCY | OHM_LAYER_NDT | OHM_LAYER_TSDF | OHM_LAYER_COUNTS;
   if (p.layers == 0 || (p.layers & ~all)) return fail(OHM_ERR_INVALID, "create: bad layer mask");
   if (!(p.l_min <= p.l_max)) return fail(OHM_ERR_INVALID, "create: l_min > l_max");
+  if (std::isnan(p.ndt_clear_below)) return fail(OHM_ERR_INVALID, "create: ndt_clear_below is NaN");
   if (!(p.max_range > 0.0)) return fail(OHM_ERR_INVALID, "create: max_range must be > 0");
   if (!(p.min_range >= 0.0)) return fail(OHM_ERR_INVALID, "create: min_range must be >= 0");
   if (!(p.tsdf_trunc >= 0.0) || !(p.tsdf_wmax > 0.0)) return fail(OHM_ERR_INVALID, "create: bad TSDF parameters");
@@ -223,6 +224,7 @@ ohm_status ohm_map_create(const ohm_map_params* params, ohm_map** out) {
   d.miss = p.miss;
   d.l_min = p.l_min;
   d.l_max = p.l_max;
+  d.ndt_clear = p.ndt_clear_below;
   d.tau_m = (float)p.tsdf_trunc;
   d.wmax = (float)p.tsdf_wmax;
   cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, p.device);

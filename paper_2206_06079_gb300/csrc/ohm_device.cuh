@@ -99,6 +99,7 @@ struct DeviceMap {
   uint32_t layers;
   int32_t seg_steps;
   float hit, miss, l_min, l_max;
+  float ndt_clear;               // clear NDT samples when a miss crosses below this (-inf: never)
   float tau_m, wmax;
 };
 

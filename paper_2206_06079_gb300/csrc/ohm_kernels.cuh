@@ -110,6 +110,21 @@ __device__ __forceinline__ uint32_t local_morton(int32_t vx, int32_t vy, int32_t
   return morton((uint32_t)(vx & mask), (uint32_t)(vy & mask), (uint32_t)(vz & mask));
 }
 
+// Sample clearing (Sec. II-D): a miss that took voxel `off` from at or above
+// the threshold (or from unknown) to below it clears the voxel's NDT samples.
+// Misses only lower a voxel within the miss phase, so exactly one successful
+// CAS per voxel and call can make this crossing.
+__device__ __forceinline__ void after_miss(const DeviceMap& m, long long off, unsigned int old_bits, unsigned int new_bits) {
+  const float lo = __uint_as_float(old_bits), ln = __uint_as_float(new_bits);
+  if (!(ln < m.ndt_clear) || (lo < m.ndt_clear)) return;  // NaN (unknown) compares false: counts as above
+  if (!(m.layers & kLayerNdt)) return;
+  const int32_t ns = m.ndt_slot[off >> (3 * kRegionShift)];
+  if (ns < 0) return;
+  long long* base = m.ndt + (long long)ns * 10 * kRegionVoxels + (off & (kRegionVoxels - 1));
+#pragma unroll
+  for (int k = 0; k < 10; ++k) base[(long long)k * kRegionVoxels] = 0;
+}
+
 // Retry a clamped log-odds CAS whose first attempt found `cur` instead of
 // the value it expected (see logodds_update).
 static __device__ __noinline__ void logodds_retry(const DeviceMap& m, unsigned int* u, unsigned int cur, float delta) {
@@ -119,7 +134,10 @@ static __device__ __noinline__ void logodds_retry(const DeviceMap& m, unsigned i
     const unsigned int nb = __float_as_uint(fminf(fmaxf(__fadd_rn(l0, delta), m.l_min), m.l_max));
     if (nb == cur) return;
     const unsigned int prev = atomicCAS(u, cur, nb);
-    if (prev == cur) return;
+    if (prev == cur) {
+      if (delta < 0.f) after_miss(m, u - reinterpret_cast<unsigned int*>(m.occ), cur, nb);
+      return;
+    }
     cur = prev;
   }
   atomicOr(m.status, kStatusCasLimit);
@@ -309,8 +327,17 @@ __device__ __forceinline__ void walk_segment(const DeviceMap& m, long long si) {
         prev[j] = atomicCAS(base + off[j], old[j], nb);
       }
 #pragma unroll
-      for (int j = 0; j < kWalkBatch; ++j)
-        if (prev[j] != old[j]) logodds_retry(m, base + off[j], prev[j], miss);
+      for (int j = 0; j < kWalkBatch; ++j) {
+        if (prev[j] != old[j]) {
+          logodds_retry(m, base + off[j], prev[j], miss);
+        } else if ((todo >> j) & 1u) {
+          // this thread's CAS applied the miss (or the voxel was already at the clamp)
+          const float l = __uint_as_float(old[j]);
+          const float l0 = (l != l) ? 0.0f : l;
+          const unsigned int nb = __float_as_uint(fminf(fmaxf(__fadd_rn(l0, miss), m.l_min), m.l_max));
+          if (nb != old[j]) after_miss(m, off[j], old[j], nb);
+        }
+      }
     }
   }
 }

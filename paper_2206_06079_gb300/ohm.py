@@ -55,6 +55,7 @@ class MapParams(ctypes.Structure):
         ("miss", ctypes.c_float),
         ("l_min", ctypes.c_float),
         ("l_max", ctypes.c_float),
+        ("ndt_clear_below", ctypes.c_float),
         ("max_range", ctypes.c_double),
         ("min_range", ctypes.c_double),
         ("tsdf_trunc", ctypes.c_double),
@@ -195,8 +196,8 @@ def default_params(**kw) -> dict:
     import math
     p = dict(voxel_size=0.1, map_origin=(0.0, 0.0, 0.0), frac_bits=16, layers=LAYER_OCCUPANCY,
              hit=float(np.float32(math.log(0.7 / 0.3))), miss=float(np.float32(math.log(0.4 / 0.6))),
-             l_min=-2.0, l_max=3.5, max_range=20.0, min_range=0.0, tsdf_trunc=0.2, tsdf_wmax=float(1 << 20),
-             max_regions=4096, max_ndt_regions=1024, max_rays=1 << 18, segment_steps=0, device=0)
+             l_min=-2.0, l_max=3.5, ndt_clear_below=float("-inf"), max_range=20.0, min_range=0.0, tsdf_trunc=0.2,
+             tsdf_wmax=float(1 << 20), max_regions=4096, max_ndt_regions=1024, max_rays=1 << 18, segment_steps=0, device=0)
     p.update(kw)
     return p
 

@@ -20,7 +20,7 @@ MISS = float(np.float32(math.log(0.4 / 0.6)))   # p = 0.4 -> -0.405
 def room_params(**kw):
     """Single room scan: 32,768 rays, occupancy, 0.1 m voxels, 20 m range."""
     p = dict(voxel_size=0.1, map_origin=(0.0, 0.0, 0.0), frac_bits=16, layers=OCC, hit=HIT, miss=MISS,
-             l_min=-2.0, l_max=3.5, max_range=20.0, min_range=0.0, tsdf_trunc=0.2, tsdf_wmax=float(1 << 20),
+             l_min=-2.0, l_max=3.5, ndt_clear_below=float("-inf"), max_range=20.0, min_range=0.0, tsdf_trunc=0.2, tsdf_wmax=float(1 << 20),
              max_regions=1024, max_ndt_regions=1024, max_rays=32768, segment_steps=0, device=0)
     p.update(kw)
     return p
@@ -35,7 +35,7 @@ def tunnel_params(**kw):
     1024 azimuths), occupancy + NDT-OM, 0.1 m voxels, 50 m maximum range for
     missing returns."""
     p = dict(voxel_size=0.1, map_origin=(0.0, 0.0, 0.0), frac_bits=16, layers=OCC | NDT, hit=HIT, miss=MISS,
-             l_min=-2.0, l_max=3.5, max_range=50.0, min_range=0.0, tsdf_trunc=0.2, tsdf_wmax=float(1 << 20),
+             l_min=-2.0, l_max=3.5, ndt_clear_below=float("-inf"), max_range=50.0, min_range=0.0, tsdf_trunc=0.2, tsdf_wmax=float(1 << 20),
              max_regions=24576, max_ndt_regions=4096, max_rays=131072, segment_steps=0, device=0)
     p.update(kw)
     return p
@@ -51,7 +51,7 @@ TUNNEL_SCANS = 100
 def tsdf_params(**kw):
     """Depth-camera TSDF: 640 x 480 frames, 0.05 m voxels, tau = 0.2 m."""
     p = dict(voxel_size=0.05, map_origin=(0.0, 0.0, 0.0), frac_bits=16, layers=TSDF, hit=HIT, miss=MISS,
-             l_min=-2.0, l_max=3.5, max_range=10.0, min_range=0.0, tsdf_trunc=0.2, tsdf_wmax=float(1 << 20),
+             l_min=-2.0, l_max=3.5, ndt_clear_below=float("-inf"), max_range=10.0, min_range=0.0, tsdf_trunc=0.2, tsdf_wmax=float(1 << 20),
              max_regions=2048, max_ndt_regions=1, max_rays=640 * 480, segment_steps=0, device=0)
     p.update(kw)
     return p
@@ -71,6 +71,6 @@ TSDF_FRAMES = 64
 
 def oracle_params(p):
     """The oracle's parameter names for a map parameter dict."""
-    keys = ("voxel_size", "map_origin", "frac_bits", "layers", "hit", "miss", "l_min", "l_max", "max_range",
-            "min_range", "tsdf_trunc", "tsdf_wmax")
+    keys = ("voxel_size", "map_origin", "frac_bits", "layers", "hit", "miss", "l_min", "l_max", "ndt_clear_below",
+            "max_range", "min_range", "tsdf_trunc", "tsdf_wmax")
     return {k: p[k] for k in keys}

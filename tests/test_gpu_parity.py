@@ -240,3 +240,15 @@ def test_ndt_pool_exhaustion_leaves_map_unchanged():
     _integrate_both(gm, om, tiny)
     compare_dense(gm, om, counts=False)
     compare_ndt(gm, om)
+
+
+@pytest.mark.parametrize("thr", [-1.0, 0.5])
+def test_ndt_sample_clearing_matches_oracle(thr):
+    p = W.tunnel_params(layers=W.OCC | W.NDT | W.COUNTS, ndt_clear_below=thr, max_rays=32768, max_range=20.0,
+                        max_regions=8192)
+    gm, om = _pair(p)
+    for i in range(4):
+        rays = synth.tunnel_scan(3 * i, beams=32, azimuths=1024, max_range=20.0)
+        _integrate_both(gm, om, rays)
+    compare_dense(gm, om)
+    compare_ndt(gm, om)

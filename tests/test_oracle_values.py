@@ -263,3 +263,38 @@ def test_tsdf_skips_no_return_and_out_of_range():
     m.integrate(o, e, f)
     q = m.query(np.array([[1.0, 0, 0], [0, 0.2, 0], [0, 0, 7.0], [0, -1.0, 0]], np.float32))["tsdf"]
     assert q[0, 1] == 1 and q[1, 1] == 0 and q[2, 1] == 0 and q[3, 1] == 0
+
+
+def test_ndt_samples_cleared_when_occupancy_falls_below_threshold():
+    """Sec. II-D: sample data is cleared when the voxel's occupancy falls below
+    a threshold.  Voxel (5, 0, 0) gets 3 samples (l = 3 * 0.847 = 2.54), then
+    scans of k misses each; with threshold 0.5 the samples survive while
+    l >= 0.5 and vanish on the miss that takes l below it; new samples then
+    start a fresh mean."""
+    thr = 0.5
+    m = oracle.OracleMap(layers=LAYER_OCCUPANCY | LAYER_NDT, ndt_clear_below=thr)
+    probe = np.array([[0.55, 0.05, 0.05]], np.float32)
+    o, e = _single_voxel_scan(0, 3)
+    m.integrate(o, e)
+    assert m.query(probe)["ndt"][0, 0] == 3
+    l = float(m.query(probe)["occupancy"][0])
+    for k in (2, 2, 1):
+        o, e = _single_voxel_scan(k, 0)
+        m.integrate(o, e)
+        for _ in range(k):
+            l = max(l + MISS, -2.0)
+        n = m.query(probe)["ndt"][0, 0]
+        assert n == (3 if l >= thr else 0), (l, n)
+    assert n == 0
+    o, e = _single_voxel_scan(0, 2)
+    m.integrate(o, e)
+    assert m.query(probe)["ndt"][0, 0] == 2
+
+
+def test_ndt_clearing_off_by_default():
+    m = oracle.OracleMap(layers=LAYER_OCCUPANCY | LAYER_NDT)
+    o, e = _single_voxel_scan(0, 3)
+    m.integrate(o, e)
+    o, e = _single_voxel_scan(40, 0)
+    m.integrate(o, e)
+    assert m.query(np.array([[0.55, 0.05, 0.05]], np.float32))["ndt"][0, 0] == 3
