@@ -278,7 +278,7 @@ def test_ndt_samples_cleared_when_occupancy_falls_below_threshold():
     m.integrate(o, e)
     assert m.query(probe)["ndt"][0, 0] == 3
     l = float(m.query(probe)["occupancy"][0])
-    for k in (2, 2, 1):
+    for k in (2, 2, 2):
         o, e = _single_voxel_scan(k, 0)
         m.integrate(o, e)
         for _ in range(k):
