@@ -106,7 +106,7 @@ def _peaks():
 
 def _walk_source_hash():
     h = hashlib.sha256()
-    for f in ("ohm_integrate.cu", "ohm_device.cuh"):
+    for f in ("ohm_integrate.cu", "ohm_kernels.cuh", "ohm_device.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2206_06079_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
