@@ -45,7 +45,9 @@ typedef enum {
   OHM_ERR_CAPACITY = 2,    /* region / NDT pool or scratch too small; map unchanged */
   OHM_ERR_CUDA = 3,        /* a CUDA runtime call failed */
   OHM_ERR_PROBE_LIMIT = 4, /* hash probe bound exceeded; map unchanged */
-  OHM_ERR_UNSUPPORTED = 5  /* the map lacks a layer the call needs */
+  OHM_ERR_UNSUPPORTED = 5, /* the map lacks a layer the call needs */
+  OHM_ERR_EVICTED = 6      /* an asynchronous call touched regions evicted to host memory; it changed
+                              nothing: call ohm_map_restore_pending, then repeat it */
 } ohm_status;
 
 /* Layers (Sec. III-A "multiple contiguous layers for each voxel region"). */
@@ -82,6 +84,10 @@ typedef struct {
   int32_t segment_steps;   /* rays are split every this many voxel steps along their
                               dominant axis (Sec. III-B ray segments); 0 = 4 */
   int32_t device;          /* CUDA device ordinal */
+  int32_t evict_when_full; /* nonzero: when ohm_integrate_rays finds the region or NDT pool full it
+                              moves least recently used regions to host memory and repeats the call
+                              (see the region cache below); 0: the call fails with OHM_ERR_CAPACITY */
+  int32_t reserved;        /* must be 0 */
 } ohm_map_params;
 
 /* Create a map.  Fills `*out` on success.  Allocates the region pool, the
@@ -129,6 +135,33 @@ ohm_status ohm_integrate_rays_async(ohm_map* map, const float* origins, int64_t 
 /* Wait for `stream` and return (then clear) the latched device status. */
 ohm_status ohm_map_sync(ohm_map* map, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Region cache (Sec. III-A: regions move between the GPU and host memory).
+ * Every pool region carries the sequence number of the last integrate call
+ * that touched it.  Eviction copies the least recently touched regions to
+ * pinned host memory and frees their pool slots; the keys stay known.  A
+ * later call that reaches an evicted region stops and changes nothing;
+ * ohm_integrate_rays then restores the region and repeats the call by
+ * itself, the asynchronous entry points report OHM_ERR_EVICTED through
+ * ohm_map_sync.  Query and export see resident regions only.
+ * ------------------------------------------------------------------------- */
+
+/* Evict least recently used regions until at most keep_regions remain
+ * resident; *evicted = how many left the device.  Synchronous. */
+ohm_status ohm_map_evict(ohm_map* map, int64_t keep_regions, int64_t* evicted, void* stream);
+
+/* Restore the evicted regions the last call asked for (after OHM_ERR_EVICTED);
+ * evicts other least recently used regions first if the pool is full.  Call it
+ * before the next integrate call on this map.  Synchronous. */
+ohm_status ohm_map_restore_pending(ohm_map* map, int64_t* restored, void* stream);
+
+/* Bring every evicted region back (fails with OHM_ERR_CAPACITY if they do not
+ * all fit).  Synchronous. */
+ohm_status ohm_map_restore_all(ohm_map* map, int64_t* restored, void* stream);
+
+/* Regions resident on the device and regions held in host memory. */
+ohm_status ohm_map_residency(ohm_map* map, int64_t* resident, int64_t* evicted, void* stream);
+
 /* Look up n world points (Sec. III-A: region key then voxel index).  Outputs
  * (device memory only; any may be NULL):
  *   occupancy  n floats, log-odds or NaN when unknown
@@ -141,7 +174,8 @@ ohm_status ohm_map_sync(ohm_map* map, void* stream);
 ohm_status ohm_query_voxels(ohm_map* map, const float* points, int64_t n, float* occupancy, uint8_t* known,
                             float* ndt, float* tsdf, uint32_t* counts, void* stream);
 
-/* Number of regions allocated in the map (synchronises `stream`). */
+/* Number of pool slots ever used by the map, resident or released by eviction
+ * (synchronises `stream`).  Without evictions: the number of regions. */
 ohm_status ohm_map_region_count(ohm_map* map, int64_t* out, void* stream);
 
 /* Copy regions [first, first + count) in allocation order into device buffers

@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libohm_gb.so")
-SOURCES = ["ohm_integrate.cu", "ohm_capi.cu", "ohm_noalloc.cu", "ohm_batch.cu", "ohm_adjoint.cu"]
+SOURCES = ["ohm_integrate.cu", "ohm_capi.cu", "ohm_noalloc.cu", "ohm_batch.cu", "ohm_adjoint.cu", "ohm_cache.cu"]
 HEADERS = ["ohm_device.cuh", "ohm_kernels.cuh", "ohm_host.h", os.path.join("..", "..", "include", "ohm_gb.h")]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",

@@ -64,7 +64,9 @@ void free_map(ohm_map* m) {
   ohm::DeviceMap& d = m->d;
   void* ptrs[] = {d.htab, d.region_count, d.region_coords, d.occ, d.counts, d.ndt_slot, d.ndt_count,
                   d.ndt, d.tsdf, d.tsdf_cnt, d.tsdf_sum, d.grad, d.status, d.calls, d.rays, d.trays, d.segs, d.touched,
+                  d.stamp, d.born, d.ndt_born, d.free_slots, d.ndt_free, d.free_info, d.restore_keys,
                   m->stage_origins, m->stage_endpoints, m->stage_flags};
+  ohm::destroy_host_store(m);
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (m->h_status) cudaFreeHost(m->h_status);
@@ -86,8 +88,10 @@ ohm_status status_from_bits(int bits) {
   if (bits & ohm::kStatusScratch) msg += " internal scratch overflow;";
   if (bits & ohm::kStatusMissing) msg += " internal region lookup failure;";
   if (bits & ohm::kStatusCasLimit) msg += " internal CAS retry limit;";
+  if (bits & ohm::kStatusRestore) msg += " it touched regions evicted to host memory (restore them and repeat it);";
   g_last_error = msg;
   if (bits & ohm::kStatusCapacity) return OHM_ERR_CAPACITY;
+  if (bits == ohm::kStatusRestore) return OHM_ERR_EVICTED;
   if (bits & ohm::kStatusProbe) return OHM_ERR_PROBE_LIMIT;
   return OHM_ERR_CUDA;
 }
@@ -188,9 +192,19 @@ ohm_status ohm_map_create(const ohm_map_params* params, ohm_map** out) {
   chk(alloc(&d.calls, 1, 0));
   chk(alloc(&d.region_coords, 3 * R, 0));
   chk(alloc(&d.ndt_slot, R, 0xFF));
+  chk(alloc(&d.stamp, R, 0));
+  chk(alloc(&d.born, R, 0xFF));
+  chk(alloc(&d.ndt_born, R, 0xFF));
+  chk(alloc(&d.free_slots, R, 0));
+  chk(alloc(&d.free_info, 4, 0));
+  chk(alloc(&d.restore_keys, R, 0));
+  d.max_restore = (int32_t)R;
   if (p.layers & OHM_LAYER_OCCUPANCY) chk(alloc(&d.occ, R * V, 0xFF));  // all-ones float = NaN = unknown
   if (p.layers & OHM_LAYER_COUNTS) chk(alloc(&d.counts, R * V, 0));
-  if (p.layers & OHM_LAYER_NDT) chk(alloc(&d.ndt, (long long)d.max_ndt * 10 * V, 0));
+  if (p.layers & OHM_LAYER_NDT) {
+    chk(alloc(&d.ndt, (long long)d.max_ndt * 10 * V, 0));
+    chk(alloc(&d.ndt_free, d.max_ndt, 0));
+  }
   if (p.layers & OHM_LAYER_TSDF) {
     chk(alloc(&d.tsdf, R * V, 0));
     chk(alloc(&d.tsdf_cnt, R * V, 0));
@@ -265,9 +279,86 @@ ohm_status ohm_map_sync(ohm_map* map, void* stream) {
 
 ohm_status ohm_integrate_rays(ohm_map* map, const float* origins, int64_t n_origins, const float* endpoints,
                               const uint8_t* flags, int64_t n, void* stream) {
-  ohm_status st = ohm_integrate_rays_async(map, origins, n_origins, endpoints, flags, n, stream);
-  if (st != OHM_OK) return st;
-  return ohm_map_sync(map, stream);
+  // A call that reaches evicted regions changes nothing; bring them back and
+  // repeat it (a repeat can only fault on regions evicted to make room, which
+  // are the least recently used, so this ends quickly).
+  for (int attempt = 0; attempt < 8; ++attempt) {
+    ohm_status st = ohm_integrate_rays_async(map, origins, n_origins, endpoints, flags, n, stream);
+    if (st != OHM_OK) return st;
+    st = ohm_map_sync(map, stream);
+    if (st == OHM_ERR_CAPACITY && map->p.evict_when_full) {
+      // Make room: the regions this call touched were just stamped, so the
+      // least recently used ones are others.  Keep three quarters.
+      long long resident = 0, evicted = 0;
+      cudaError_t e = ohm::cache_resident(map, &resident);
+      if (e == cudaSuccess) e = ohm::cache_evict(map, resident * 3 / 4, &evicted);
+      if (e != cudaSuccess) return cuda_fail(e, "integrate: evict");
+      if (evicted == 0) return fail(OHM_ERR_CAPACITY, "integrate: the call alone needs more regions than the pool");
+      continue;
+    }
+    if (st != OHM_ERR_EVICTED) return st;
+    int64_t restored = 0;
+    st = ohm_map_restore_pending(map, &restored, stream);
+    if (st != OHM_OK) return st;
+  }
+  return fail(OHM_ERR_CAPACITY, "integrate: evicted regions could not be kept resident (pool too small)");
+}
+
+ohm_status ohm_map_evict(ohm_map* map, int64_t keep_regions, int64_t* evicted, void* stream) {
+  if (!map || !evicted) return fail(OHM_ERR_INVALID, "evict: NULL argument");
+  if (keep_regions < 0) return fail(OHM_ERR_INVALID, "evict: keep_regions < 0");
+  DeviceGuard guard(map->device);
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  long long ev = 0;
+  if (e == cudaSuccess) e = ohm::cache_evict(map, keep_regions, &ev);
+  if (e != cudaSuccess) return cuda_fail(e, "evict");
+  *evicted = ev;
+  return OHM_OK;
+}
+
+ohm_status ohm_map_restore_pending(ohm_map* map, int64_t* restored, void* stream) {
+  if (!map || !restored) return fail(OHM_ERR_INVALID, "restore_pending: NULL argument");
+  DeviceGuard guard(map->device);
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  std::vector<long long> keys;
+  long long r = 0;
+  if (e == cudaSuccess) e = ohm::cache_pending(map, &keys);
+  if (e == cudaSuccess) e = ohm::cache_restore(map, keys, &r);
+  if (e == cudaErrorMemoryAllocation) return fail(OHM_ERR_CAPACITY, "restore_pending: pool or host memory too small");
+  if (e != cudaSuccess) return cuda_fail(e, "restore_pending");
+  *restored = r;
+  return OHM_OK;
+}
+
+ohm_status ohm_map_restore_all(ohm_map* map, int64_t* restored, void* stream) {
+  if (!map || !restored) return fail(OHM_ERR_INVALID, "restore_all: NULL argument");
+  DeviceGuard guard(map->device);
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  long long r = 0;
+  if (e == cudaSuccess) {
+    const std::vector<long long> keys = ohm::cache_all_keys(map);
+    long long resident = 0;
+    e = ohm::cache_resident(map, &resident);
+    if (e == cudaSuccess && resident + (long long)keys.size() > map->p.max_regions)
+      return fail(OHM_ERR_CAPACITY, "restore_all: resident and evicted regions exceed max_regions");
+    if (e == cudaSuccess) e = ohm::cache_restore(map, keys, &r);
+  }
+  if (e == cudaErrorMemoryAllocation) return fail(OHM_ERR_CAPACITY, "restore_all: pool too small");
+  if (e != cudaSuccess) return cuda_fail(e, "restore_all");
+  *restored = r;
+  return OHM_OK;
+}
+
+ohm_status ohm_map_residency(ohm_map* map, int64_t* resident, int64_t* evicted, void* stream) {
+  if (!map || !resident || !evicted) return fail(OHM_ERR_INVALID, "residency: NULL argument");
+  DeviceGuard guard(map->device);
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  long long r = 0;
+  if (e == cudaSuccess) e = ohm::cache_resident(map, &r);
+  if (e != cudaSuccess) return cuda_fail(e, "residency");
+  *resident = r;
+  *evicted = ohm::cache_host_regions(map);
+  return OHM_OK;
 }
 
 ohm_status ohm_query_voxels(ohm_map* map, const float* points, int64_t n, float* occupancy, uint8_t* known,

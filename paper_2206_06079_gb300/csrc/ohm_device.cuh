@@ -29,6 +29,12 @@ constexpr int kStatusProbe = 2;      // hash probe bound exceeded
 constexpr int kStatusScratch = 4;    // per-call scratch too small (a library bug)
 constexpr int kStatusMissing = 8;    // a region expected in the table was not found (a library bug)
 constexpr int kStatusCasLimit = 16;  // a CAS loop gave up (a library bug)
+constexpr int kStatusRestore = 32;   // the call touched evicted regions: restore them, then repeat it
+
+// Hash-entry slot values below zero.
+constexpr long long kSlotPending = -1;    // inserted by this kernel, slot not yet written (or none left)
+constexpr long long kSlotEvicted = -3;    // region evicted to host memory
+constexpr long long kSlotRestoring = -4;  // evicted, and a restore was requested by the current call
 
 // Ray record written by the occupancy prepare kernel.
 struct __align__(16) RayRec {
@@ -59,6 +65,11 @@ struct CallCounters {
   int32_t ndt_start;
   unsigned long long rays;
   unsigned long long total_visits;  // every call since the map was made
+  int32_t seq;                      // sequence number of the current call (LRU stamps, birth marks)
+  int32_t free_used_start;          // free-list positions when the call began (rollback point)
+  int32_t ndt_free_used_start;
+  int32_t pad;
+  unsigned long long restores;      // evicted region keys this call asked to restore
 };
 
 // Everything a kernel needs, passed by value.
@@ -83,6 +94,15 @@ struct DeviceMap {
   float* grad;                   // [max_regions][32768] adjoint weights, allocated by the first backward call
   int32_t* status;
   CallCounters* calls;
+  // region cache (Sec. III-A: regions move between device and host memory)
+  int32_t* stamp;                // [max_regions] seq of the last call that touched the region
+  int32_t* born;                 // [max_regions] seq of the call that inserted the region
+  int32_t* ndt_born;             // [max_regions] seq of the call that gave the region its NDT block
+  int32_t* free_slots;           // [max_regions] region slots released by eviction
+  int32_t* ndt_free;             // [max_ndt] NDT blocks released by eviction
+  int32_t* free_info;            // [0] free slots, [1] used, [2] free NDT blocks, [3] used
+  long long* restore_keys;       // [max_restore] evicted keys touched by the current call
+  int32_t max_restore;
   // per-call scratch
   RayRec* rays;
   TsdfRec* trays;
@@ -145,32 +165,73 @@ __device__ __forceinline__ int32_t find_region(const DeviceMap& m, long long key
   return -1;
 }
 
-// Insert a region if absent.  The inserting thread takes a pool slot; other
-// threads only learn that the key exists (slots are read after this kernel).
-// The first probe may read a stale cached entry: a key once written never
-// changes within a call, and a stale "empty" only sends us to the CAS below.
+// A pool slot for a new region: a slot released by eviction if any is left,
+// else the next never-used one; -1 when the pool is full.
+__device__ __forceinline__ int32_t alloc_region_slot(const DeviceMap& m) {
+  const int32_t i = atomicAdd(&m.free_info[1], 1);
+  if (i < m.free_info[0]) return m.free_slots[i];
+  const int32_t s = atomicAdd(m.region_count, 1);
+  return s < m.max_regions ? s : -1;
+}
+
+// An NDT block for a region, the same way.
+__device__ __forceinline__ int32_t alloc_ndt_block(const DeviceMap& m) {
+  const int32_t i = atomicAdd(&m.free_info[3], 1);
+  if (i < m.free_info[2]) return m.ndt_free[i];
+  const int32_t s = atomicAdd(m.ndt_count, 1);
+  return s < m.max_ndt ? s : -1;
+}
+
+// Insert a region if absent, and mark it used by the current call.  The
+// inserting thread takes a pool slot; other threads only learn that the key
+// exists (slots are read after this kernel).  A key whose region was evicted
+// to host memory is queued for restoring and the call is stopped (it will be
+// repeated once the region is back).  The first probe may read a stale cached
+// entry: a key once written never changes within a call, and a stale "empty"
+// only sends us to the CAS below.
 __device__ inline void insert_region(const DeviceMap& m, int rx, int ry, int rz) {
   const long long key = pack_region(rx, ry, rz);
+  const int32_t seq = m.calls->seq;
   uint32_t h = hash_key(key) & m.hmask;
   for (int i = 0; i < m.max_probe; ++i) {
-    long long k = m.htab[h].x;
-    if (k == key) return;
+    const longlong2 e = m.htab[h];
+    long long k = e.x;
     if (k == kEmptyKey) {
-      long long prev = (long long)atomicCAS((unsigned long long*)&m.htab[h].x, (unsigned long long)kEmptyKey,
-                                            (unsigned long long)key);
+      const long long prev = (long long)atomicCAS((unsigned long long*)&m.htab[h].x, (unsigned long long)kEmptyKey,
+                                                  (unsigned long long)key);
       if (prev == kEmptyKey) {
-        int32_t s = atomicAdd(m.region_count, 1);
-        if (s < m.max_regions) {
+        const int32_t s = alloc_region_slot(m);
+        if (s >= 0) {
           m.htab[h].y = s;
           m.region_coords[3 * s + 0] = rx;
           m.region_coords[3 * s + 1] = ry;
           m.region_coords[3 * s + 2] = rz;
+          m.born[s] = seq;
+          m.stamp[s] = seq;
         } else {
           atomicOr(m.status, kStatusCapacity);
         }
         return;
       }
-      if (prev == key) return;
+      if (prev != key) {
+        h = (h + 1) & m.hmask;
+        continue;
+      }
+      return;  // another thread inserted it just now; it stamps the slot
+    }
+    if (k == key) {
+      const long long slot = e.y;
+      if (slot >= 0) {
+        m.stamp[slot] = seq;
+      } else if (slot == kSlotEvicted || slot == kSlotRestoring) {
+        if (atomicCAS((unsigned long long*)&m.htab[h].y, (unsigned long long)kSlotEvicted,
+                      (unsigned long long)kSlotRestoring) == (unsigned long long)kSlotEvicted) {
+          const unsigned long long r = atomicAdd(&m.calls->restores, 1ULL);
+          if (r < (unsigned long long)m.max_restore) m.restore_keys[r] = key;
+        }
+        atomicOr(m.status, kStatusRestore);
+      }
+      return;
     }
     h = (h + 1) & m.hmask;
   }

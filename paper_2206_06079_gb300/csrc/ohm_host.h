@@ -11,6 +11,10 @@
 #include "../../include/ohm_gb.h"
 #include "ohm_device.cuh"
 
+namespace ohm {
+struct HostStore;
+}
+
 struct ohm_map {
   ohm_map_params p;
   ohm::DeviceMap d;
@@ -33,6 +37,7 @@ struct ohm_map {
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
   double stage_ms[OHM_STAGE_COUNT];
   long long stage_launches[OHM_STAGE_COUNT];
+  ohm::HostStore* store;    // evicted regions in pinned host memory
 };
 
 namespace ohm {
@@ -44,6 +49,15 @@ cudaError_t launch_query(ohm_map* map, const float* points, long long n, float* 
 cudaError_t launch_export(ohm_map* map, long long first, long long count, int32_t* keys, float* occupancy,
                           uint32_t* counts, long long* ndt, float* tsdf, cudaStream_t stream);
 int walk_blocks_per_sm();
+
+// Region cache (ohm_cache.cu).
+cudaError_t cache_evict(ohm_map* m, long long target, long long* evicted);
+cudaError_t cache_restore(ohm_map* m, const std::vector<long long>& keys, long long* restored);
+cudaError_t cache_pending(ohm_map* m, std::vector<long long>* keys);
+cudaError_t cache_resident(ohm_map* m, long long* resident);
+long long cache_host_regions(ohm_map* m);
+std::vector<long long> cache_all_keys(ohm_map* m);
+void destroy_host_store(ohm_map* m);
 
 // Set the message ohm_last_error() returns on this thread.
 void set_last_error(const std::string& msg);

@@ -155,9 +155,13 @@ constexpr int kWalkBatch = OHM_WALK_BATCH;
 __device__ __forceinline__ void begin_call(const DeviceMap& m, long long n) {
   m.calls->region_start = *m.region_count;
   m.calls->ndt_start = *m.ndt_count;
+  m.calls->free_used_start = m.free_info[1];
+  m.calls->ndt_free_used_start = m.free_info[3];
+  m.calls->seq += 1;
   m.calls->segments = 0;
   m.calls->visits = 0;
   m.calls->touched = 0;
+  m.calls->restores = 0;
   m.calls->rays = (unsigned long long)n;
 }
 
@@ -238,11 +242,13 @@ __device__ __forceinline__ void ndt_alloc_ray(const DeviceMap& m, long long i) {
   }
   if (*(volatile int32_t*)&m.ndt_slot[slot] != -1) return;
   if (atomicCAS(&m.ndt_slot[slot], -1, -2) == -1) {
-    const int32_t id = atomicAdd(m.ndt_count, 1);
-    if (id < m.max_ndt)
+    const int32_t id = alloc_ndt_block(m);
+    if (id >= 0) {
+      m.ndt_born[slot] = m.calls->seq;
       m.ndt_slot[slot] = id;
-    else
+    } else {
       atomicOr(m.status, kStatusCapacity);
+    }
   }
 }
 
@@ -497,22 +503,29 @@ __device__ __forceinline__ long long touched_count(const DeviceMap& m) {
 }
 
 // Undo the allocations of a failed call (threads t0, t0 + stride, ...): keys
-// inserted by it become tombstones, its NDT slots are released, the pool
-// counters are restored.
+// inserted by it become tombstones, keys it asked to restore go back to
+// "evicted", its NDT blocks are released, and the pool counters and free-list
+// positions are restored.  Stamps stay: regions the call touched count as
+// recently used.
 __device__ __forceinline__ void rollback_call(const DeviceMap& m, long long t0, long long stride) {
-  const int32_t rs = m.calls->region_start, ns = m.calls->ndt_start;
+  const int32_t seq = m.calls->seq;
   for (long long h = t0; h <= (long long)m.hmask; h += stride) {
     const longlong2 e = m.htab[h];
     if (e.x == kEmptyKey || e.x == kTombKey) continue;
-    if (e.y < 0 || e.y >= rs) m.htab[h] = make_longlong2(kTombKey, -1);
+    if (e.y == kSlotRestoring)
+      m.htab[h].y = kSlotEvicted;
+    else if (e.y == kSlotPending || (e.y >= 0 && m.born[e.y] == seq))
+      m.htab[h] = make_longlong2(kTombKey, -1);
   }
   for (long long s = t0; s < m.max_regions; s += stride) {
     const int32_t v = m.ndt_slot[s];
-    if (s >= rs || v == -2 || v >= ns) m.ndt_slot[s] = -1;
+    if (v == -2 || (v >= 0 && (m.ndt_born[s] == seq || m.born[s] == seq))) m.ndt_slot[s] = -1;
   }
   if (t0 == 0) {
-    *m.region_count = rs;
-    *m.ndt_count = ns;
+    *m.region_count = m.calls->region_start;
+    *m.ndt_count = m.calls->ndt_start;
+    m.free_info[1] = m.calls->free_used_start;
+    m.free_info[3] = m.calls->ndt_free_used_start;
   }
 }
 

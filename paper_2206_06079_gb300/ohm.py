@@ -16,20 +16,21 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 # tile parameters (used when tuning); by default the in-tree build is loaded.
 LIB_PATH = os.environ.get("OHM_GB_LIB") or os.path.join(_HERE, "_lib", "libohm_gb.so")
 
-OK, ERR_INVALID, ERR_CAPACITY, ERR_CUDA, ERR_PROBE_LIMIT, ERR_UNSUPPORTED = range(6)
+OK, ERR_INVALID, ERR_CAPACITY, ERR_CUDA, ERR_PROBE_LIMIT, ERR_UNSUPPORTED, ERR_EVICTED = range(7)
 LAYER_OCCUPANCY, LAYER_NDT, LAYER_TSDF, LAYER_COUNTS = 1, 2, 4, 8
 FLAG_NO_RETURN = 1
 REGION_VOXELS = 32768
 
 _STATUS_NAMES = {ERR_INVALID: "invalid argument", ERR_CAPACITY: "capacity", ERR_CUDA: "CUDA error",
-                 ERR_PROBE_LIMIT: "hash probe limit", ERR_UNSUPPORTED: "unsupported"}
+                 ERR_PROBE_LIMIT: "hash probe limit", ERR_UNSUPPORTED: "unsupported", ERR_EVICTED: "evicted"}
 
 # Every symbol include/ohm_gb.h declares.
 EXPORTED = ["ohm_map_create", "ohm_map_destroy", "ohm_integrate_rays", "ohm_integrate_rays_async", "ohm_map_sync",
             "ohm_query_voxels", "ohm_map_region_count", "ohm_map_export", "ohm_map_stats", "ohm_map_profile",
             "ohm_map_profile_read", "ohm_last_error", "ohm_count_rays_noalloc", "ohm_batch_create",
             "ohm_batch_destroy", "ohm_batch_tune", "ohm_batch_integrate", "ohm_batch_sync", "ohm_batch_stats",
-            "ohm_integrate_depth", "ohm_tsdf_backward"]
+            "ohm_integrate_depth", "ohm_tsdf_backward", "ohm_map_evict", "ohm_map_restore_pending",
+            "ohm_map_restore_all", "ohm_map_residency"]
 
 BATCH_MAX_MAPS = 32
 
@@ -65,6 +66,8 @@ class MapParams(ctypes.Structure):
         ("max_rays", ctypes.c_int64),
         ("segment_steps", ctypes.c_int32),
         ("device", ctypes.c_int32),
+        ("evict_when_full", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -143,6 +146,16 @@ def load_library(path: str = LIB_PATH):
     lib.ohm_tsdf_backward.restype = st
     lib.ohm_tsdf_backward.argtypes = [vp, p, ctypes.c_int32, ctypes.c_int32, dp, dp, ctypes.c_double, ctypes.c_double,
                                       p, p, i64, p, p, vp]
+    for name in ("ohm_map_evict",):
+        f = getattr(lib, name)
+        f.restype = st
+        f.argtypes = [vp, i64, ctypes.POINTER(i64), vp]
+    for name in ("ohm_map_restore_pending", "ohm_map_restore_all"):
+        f = getattr(lib, name)
+        f.restype = st
+        f.argtypes = [vp, ctypes.POINTER(i64), vp]
+    lib.ohm_map_residency.restype = st
+    lib.ohm_map_residency.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), vp]
     lib.ohm_last_error.restype = ctypes.c_char_p
     lib.ohm_last_error.argtypes = []
     _lib = lib
@@ -197,7 +210,8 @@ def default_params(**kw) -> dict:
     p = dict(voxel_size=0.1, map_origin=(0.0, 0.0, 0.0), frac_bits=16, layers=LAYER_OCCUPANCY,
              hit=float(np.float32(math.log(0.7 / 0.3))), miss=float(np.float32(math.log(0.4 / 0.6))),
              l_min=-2.0, l_max=3.5, ndt_clear_below=float("-inf"), max_range=20.0, min_range=0.0, tsdf_trunc=0.2,
-             tsdf_wmax=float(1 << 20), max_regions=4096, max_ndt_regions=1024, max_rays=1 << 18, segment_steps=0, device=0)
+             tsdf_wmax=float(1 << 20), max_regions=4096, max_ndt_regions=1024, max_rays=1 << 18, segment_steps=0, device=0,
+             evict_when_full=0, reserved=0)
     p.update(kw)
     return p
 
@@ -306,6 +320,29 @@ class Map:
                                                _ptr(out.get("ndt")), _ptr(out.get("tsdf")), _ptr(out.get("counts")),
                                                _stream_handle(stream)))
         return out
+
+    def evict(self, keep_regions: int, stream=None) -> int:
+        """Move least recently used regions to host memory until at most
+        keep_regions stay resident; returns how many moved."""
+        n = ctypes.c_int64()
+        _check(load_library().ohm_map_evict(self._h, int(keep_regions), ctypes.byref(n), _stream_handle(stream)))
+        return int(n.value)
+
+    def restore_pending(self, stream=None) -> int:
+        n = ctypes.c_int64()
+        _check(load_library().ohm_map_restore_pending(self._h, ctypes.byref(n), _stream_handle(stream)))
+        return int(n.value)
+
+    def restore_all(self, stream=None) -> int:
+        n = ctypes.c_int64()
+        _check(load_library().ohm_map_restore_all(self._h, ctypes.byref(n), _stream_handle(stream)))
+        return int(n.value)
+
+    def residency(self, stream=None):
+        """(regions resident on the device, regions held in host memory)"""
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        _check(load_library().ohm_map_residency(self._h, ctypes.byref(a), ctypes.byref(b), _stream_handle(stream)))
+        return int(a.value), int(b.value)
 
     def region_count(self, stream=None) -> int:
         c = ctypes.c_int64()
