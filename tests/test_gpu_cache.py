@@ -21,8 +21,9 @@ def _built():
 
 
 def _params(**kw):
-    return W.tunnel_params(layers=W.OCC | W.NDT | W.COUNTS, max_rays=32768, max_range=20.0, max_regions=8192,
-                           max_ndt_regions=2048, **kw)
+    p = dict(layers=W.OCC | W.NDT | W.COUNTS, max_rays=32768, max_range=20.0, max_regions=8192, max_ndt_regions=2048)
+    p.update(kw)
+    return W.tunnel_params(**p)
 
 
 def _scan(i):
@@ -83,7 +84,6 @@ def test_small_pool_under_lru_pressure():
     """Resident set kept at ~400 regions while the trajectory touches about
     four times that: every call restores what it needs from host memory."""
     a, b = ohm.Map(**_params(max_regions=3000, max_ndt_regions=3000)), ohm.Map(**_params())
-    restored_total = 0
     for i in range(10):
         a.evict(400)
         s = _scan(i)
@@ -99,14 +99,19 @@ def test_full_pool_evicts_when_allowed():
     """evict_when_full: a synchronous call that finds the pool full evicts the
     least recently used regions and is repeated; the result equals a map with
     a large pool once everything is back."""
-    small = _params(max_regions=1400, max_ndt_regions=1400, evict_when_full=1)
+    probe = ohm.Map(**_params())
+    probe.integrate(*_scan(0))
+    pool = int(probe.region_count() * 1.15)  # one scan fits, three do not
+    probe.close()
+    small = _params(max_regions=pool, max_ndt_regions=pool, evict_when_full=1)
     a, b = ohm.Map(**small), ohm.Map(**_params())
     for i in range(3):
         s = _scan(2 * i)
         a.integrate(*s)
         b.integrate(*s)
     res, host = a.residency()
-    assert host > 0 and res <= 1400
+    assert b.region_count() > pool
+    assert host > 0 and res <= pool
     # compare the resident part now ...
     pts = torch.cat([_scan(2 * i)[1] for i in range(3)])
     qa, qb = a.query(pts, ndt=True, counts=True), b.query(pts, ndt=True, counts=True)
