@@ -418,3 +418,75 @@ def mixed_scan(scene: str, kind: str, seed: int, device="cpu", max_range: float 
         rng = torch.where(no_ret, 6.0 / zscale, t)
     e = o[None] + rng[:, None] * u
     return RaySet(o[None].float(), e.float(), no_ret.to(torch.uint8) * FLAG_NO_RETURN)
+
+
+# ---------------------------------------------------------------------------
+# An outdoor world for the served stream: ground plane and box buildings.
+# ---------------------------------------------------------------------------
+@dataclass
+class World:
+    boxes_lo: torch.Tensor   # (nb, 3)
+    boxes_hi: torch.Tensor
+    half: float              # the world spans [-half, half]^2 in x, y
+
+
+def world_scene(seed: int = 0x0A16, n_boxes: int = 160, half: float = 100.0) -> World:
+    """Ground plane z = 0 and n_boxes axis-aligned buildings (footprint
+    U[2, 12] m, height U[2, 25] m) scattered over [-half, half]^2."""
+    g = _gen(seed)
+    c = (torch.rand(n_boxes, 2, generator=g, dtype=torch.float64) * 2 - 1) * (half - 10)
+    size = 2 + 10 * torch.rand(n_boxes, 2, generator=g, dtype=torch.float64)
+    hgt = 2 + 23 * torch.rand(n_boxes, generator=g, dtype=torch.float64)
+    lo = torch.cat([c - size / 2, torch.zeros(n_boxes, 1, dtype=torch.float64)], 1)
+    hi = torch.cat([c + size / 2, hgt[:, None]], 1)
+    return World(lo, hi, half)
+
+
+def robot_pose(robot: int, t: float, half: float = 100.0):
+    """Position and heading of robot `robot` at time t: a Lissajous path at
+    about 1 m/s, 1 m above the ground, kept inside the world."""
+    a = 0.8 * (half - 20)
+    w1, w2 = 0.011 + 0.0013 * robot, 0.007 + 0.0017 * robot
+    ph = 0.9 * robot
+    x = a * math.sin(w1 * t + ph)
+    y = a * math.sin(w2 * t + 2 * ph)
+    dx, dy = a * w1 * math.cos(w1 * t + ph), a * w2 * math.cos(w2 * t + 2 * ph)
+    return (x, y, 1.0), math.atan2(dy, dx)
+
+
+def world_scan(world: World, robot: int, t: float, kind: str, camera: int = 0, device="cpu",
+               max_range: float = 30.0, seed: int = 0) -> RaySet:
+    """A lidar scan ('lidar128x1024') or a depth frame ('depth424x240',
+    camera 0 looks ahead, camera 1 to the left) of robot `robot` at time t."""
+    pos, yaw = robot_pose(robot, t, world.half)
+    o = torch.tensor(pos, dtype=torch.float64, device=device)
+    if kind.startswith("lidar"):
+        beams, az = (int(v) for v in kind[5:].split("x"))
+        d = lidar_directions(beams, az, 22.5, device=device)
+        cy, sy = math.cos(yaw), math.sin(yaw)
+        u = torch.stack([cy * d[:, 0] - sy * d[:, 1], sy * d[:, 0] + cy * d[:, 1], d[:, 2]], dim=1)
+        zscale = None
+    else:
+        w, h = (int(v) for v in kind[5:].split("x"))
+        heading = yaw + (math.pi / 2 if camera else 0.0)
+        cy, sy = math.cos(heading), math.sin(heading)
+        f = torch.tensor([cy, sy, -0.2], dtype=torch.float64)
+        f = f / f.norm()
+        r = torch.tensor([sy, -cy, 0.0], dtype=torch.float64)
+        dn = torch.linalg.cross(f, r)
+        u, zscale = pinhole_directions(w, h, torch.stack([r, dn, f], dim=1), fx=525.0 * w / 640.0, device=device)
+    t_ground = torch.where(u[:, 2] < 0, -o[2] / torch.where(u[:, 2] < 0, u[:, 2], -torch.ones_like(u[:, 2])),
+                           torch.full_like(u[:, 2], float("inf")))
+    t_box = _ray_box_entry(o, u, world.boxes_lo.to(device), world.boxes_hi.to(device)).min(1).values
+    t = torch.minimum(t_ground, t_box)
+    g = _gen(seed)
+    noise = (torch.randn(u.shape[0], generator=g, dtype=torch.float64) * 0.02).to(device)
+    if zscale is None:
+        no_ret = t >= max_range
+        rng = torch.where(no_ret, torch.full_like(t, max_range), t + noise)
+    else:
+        z = t * zscale
+        no_ret = (z <= 0.3) | (z > 6.0)
+        rng = torch.where(no_ret, 6.0 / zscale, t)
+    e = o[None] + rng[:, None] * u
+    return RaySet(o[None].float(), e.float(), no_ret.to(torch.uint8) * FLAG_NO_RETURN)

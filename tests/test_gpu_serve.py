@@ -1,0 +1,66 @@
+"""Served stream: continuous batching of mixed-sensor scans from several
+robots into resident maps gives, map for map, exactly what integrating each
+robot's scans alone and in order gives -- with and without eviction to host
+memory."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2206_06079_gb300 import ohm, serve, synth, workloads as W
+
+from .parity import assert_maps_identical
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+    assert torch.cuda.is_available()
+
+
+def _params():
+    return W.tunnel_params(layers=W.OCC | W.NDT, voxel_size=0.1, max_range=30.0, max_rays=131072,
+                           max_regions=8192, max_ndt_regions=4096)
+
+
+def _requests(n_robots, duration, seed=0):
+    world = synth.world_scene()
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for rb in range(n_robots):
+        for kind, cam, rate in (("lidar64x512", 0, 10.0), ("depth212x120", 0, 30.0), ("depth212x120", 1, 30.0)):
+            for t in serve.poisson_times(rate, duration, rng):
+                r = synth.world_scan(world, rb, float(t), kind, camera=cam, device="cuda", max_range=30.0,
+                                     seed=int(t * 1e6) + rb)
+                reqs.append(serve.Request(rb, float(t), (r.origins, r.endpoints, r.flags), kind))
+    return reqs
+
+
+@pytest.mark.parametrize("budget", [None, 150])
+def test_served_maps_equal_maps_integrated_alone(budget):
+    n = 3
+    reqs = _requests(n, 1.0)
+    torch.cuda.synchronize()
+    served = [ohm.Map(**_params()) for _ in range(n)]
+    loop = serve.ServeLoop(served, budget_regions=budget)
+    stats = loop.run(list(reqs), realtime=False)
+    assert len(stats.latencies_ms) == len(reqs)
+    if budget is not None:
+        assert stats.evicted_regions > 0
+    alone = [ohm.Map(**_params()) for _ in range(n)]
+    for r in sorted(reqs, key=lambda r: (r.map_index, r.arrival)):
+        alone[r.map_index].integrate(*r.rays)
+    for a, b in zip(served, alone):
+        a.restore_all()
+        assert_maps_identical(a, b)
+
+
+def test_realtime_loop_reports_latency():
+    reqs = _requests(2, 0.5, seed=1)
+    torch.cuda.synchronize()
+    maps = [ohm.Map(**_params()) for _ in range(2)]
+    s = serve.ServeLoop(maps).run(reqs, realtime=True).summary()
+    assert s["requests"] == len(reqs)
+    assert 0 < s["latency_ms"]["p50"] <= s["latency_ms"]["p99"] < 500
