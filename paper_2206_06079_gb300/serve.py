@@ -70,6 +70,7 @@ class ServeLoop:
         self.budget = budget_regions
         self.queues = [collections.deque() for _ in self.maps]
         self.stats = ServeStats()
+        self._visible = {}
 
     def _admit_memory(self):
         if self.budget is None:
@@ -108,7 +109,7 @@ class ServeLoop:
                 continue
             self.queues[i].popleft()
             r.done = now
-            self.stats.latencies_ms.append(1e3 * (r.done - r.arrival))
+            self.stats.latencies_ms.append(1e3 * (r.done - self._visible.get(id(r), r.arrival)))
             self.stats.rays += r.n
         self.stats.steps += 1
 
@@ -117,25 +118,23 @@ class ServeLoop:
         visible at their arrival times on the wall clock; otherwise all are
         visible at once (arrival 0) and the loop runs as fast as it can."""
         reqs = sorted(requests, key=lambda r: r.arrival)
-        if not realtime:
-            for r in reqs:
-                r.arrival = 0.0
+        visible = [r.arrival if realtime else 0.0 for r in reqs]
         t0 = time.perf_counter()
         k = 0
         pending = 0
         while k < len(reqs) or pending:
             now = time.perf_counter() - t0
-            while k < len(reqs) and reqs[k].arrival <= now:
+            while k < len(reqs) and visible[k] <= now:
+                self._visible[id(reqs[k])] = visible[k]
                 self.queues[reqs[k].map_index].append(reqs[k])
                 k += 1
                 pending += 1
             if pending:
-                before = self.stats.steps
                 n_before = len(self.stats.latencies_ms)
                 self._step(t0)
                 pending -= len(self.stats.latencies_ms) - n_before
             elif k < len(reqs):
-                time.sleep(max(0.0, min(0.0005, reqs[k].arrival - now)))
+                time.sleep(max(0.0, min(0.0005, visible[k] - now)))
         self.stats.wall_s = time.perf_counter() - t0
         return self.stats
 
