@@ -36,15 +36,32 @@ constexpr long long kSlotPending = -1;    // inserted by this kernel, slot not y
 constexpr long long kSlotEvicted = -3;    // region evicted to host memory
 constexpr long long kSlotRestoring = -4;  // evicted, and a restore was requested by the current call
 
-// Ray record written by the occupancy prepare kernel.
+// Ray record written by the occupancy prepare kernel: the walk from a to b
+// (fixed point) reduced to per-axis 32-bit constants, so that every segment of
+// the ray starts from them without redoing the 64-bit set-up.
+//   v0  voxel of a;  A = |b - a|  (< 2^30, see Walker);  d0 = distance from a
+//   to the first boundary crossed (0 .. 2^F);  n = steps along the axis;
+//   sign bit k (flags bit kRaySignShift + k) set when b_k < a_k.
 struct __align__(16) RayRec {
-  long long a[3];          // walk start (sensor origin), fixed point
-  long long b[3];          // walk end (sample or truncation point), fixed point
-  unsigned long long inv;  // reciprocal64 of the dominant axis' |b - a| (0 if unset)
-  int32_t flags;           // kRayValid | kRaySample | dominant axis << kRayAxisShift
+  int32_t v0[3];
+  int32_t A[3];
+  int32_t d0[3];
+  int32_t n[3];
+  unsigned long long inv;  // reciprocal64 of A[dominant axis] (0 if that is 0)
+  int32_t flags;           // kRayValid | kRaySample | dominant axis << kRayAxisShift | signs
   int32_t nseg;            // number of segments
 };
-constexpr int32_t kRayValid = 1, kRaySample = 2, kRayAxisShift = 4;
+constexpr int32_t kRayValid = 1, kRaySample = 2, kRayAxisShift = 4, kRaySignShift = 8;
+
+// A ray kept as its two fixed-point end points (the allocation-free entry
+// point's record).
+struct __align__(16) EndpointRec {
+  long long a[3];
+  long long b[3];
+  unsigned long long inv;
+  int32_t flags;
+  int32_t nseg;
+};
 
 // Ray record written by the TSDF prepare kernel: the walk covers the band
 // [max(0, d - tau), d + tau] of the ray from the sensor to the sample e.
@@ -428,6 +445,73 @@ OHM_UNROLL
   w.cxy = dist[0] * A[1] - dist[1] * A[0];
   w.cxz = dist[0] * A[2] - dist[2] * A[0];
   w.cyz = dist[1] * A[2] - dist[2] * A[1];
+  w.total = w.nx + w.ny + w.nz;
+}
+
+// Per-ray walk constants of the walk from a to b (see RayRec); keeps the
+// other fields of r.
+__host__ __device__ inline void ray_constants(const long long a[3], const long long b[3], int F, RayRec* r) {
+  const long long U = 1LL << F;
+  int32_t signs = 0;
+OHM_UNROLL
+  for (int k = 0; k < 3; ++k) {
+    const long long delta = b[k] - a[k];
+    const long long va = a[k] >> F, vb = b[k] >> F;
+    const long long nt = vb - va;
+    r->v0[k] = (int32_t)va;
+    r->A[k] = (int32_t)(delta < 0 ? -delta : delta);
+    r->d0[k] = (int32_t)(delta < 0 ? (a[k] - va * U) : ((va + 1) * U - a[k]));
+    r->n[k] = (int32_t)(nt < 0 ? -nt : nt);
+    if (delta < 0) signs |= 1 << k;
+  }
+  r->flags = (r->flags & ~(7 << kRaySignShift)) | (signs << kRaySignShift);
+}
+
+// The end point b of a ray, from its constants.
+__host__ __device__ inline void ray_end(const RayRec& r, int F, long long b[3]) {
+  const long long U = 1LL << F;
+OHM_UNROLL
+  for (int k = 0; k < 3; ++k) {
+    const bool neg = (r.flags >> (kRaySignShift + k)) & 1;
+    const long long a = neg ? (long long)r.v0[k] * U + r.d0[k] : ((long long)r.v0[k] + 1) * U - r.d0[k];
+    b[k] = neg ? a - r.A[k] : a + r.A[k];
+  }
+}
+
+// walker_init from the per-ray constants (same state, cheaper set-up).
+__host__ __device__ inline void walker_init_rec(Walker& w, const RayRec& r, int F, int M, long long K) {
+  const long long U = 1LL << F;
+  const long long d0M = M == 0 ? r.d0[0] : (M == 1 ? r.d0[1] : r.d0[2]);
+  const long long AM = M == 0 ? r.A[0] : (M == 1 ? r.A[1] : r.A[2]);
+  long long cnt[3];
+OHM_UNROLL
+  for (int k = 0; k < 3; ++k) {
+    if (K == 0)
+      cnt[k] = 0;
+    else if (k == M)
+      cnt[k] = K;
+    else
+      cnt[k] = crossings_before(r.d0[k], r.A[k], d0M, AM, F, K, k > M, r.n[k], r.inv);
+  }
+  const int32_t sx = ((r.flags >> kRaySignShift) & 1) ? -1 : 1;
+  const int32_t sy = ((r.flags >> (kRaySignShift + 1)) & 1) ? -1 : 1;
+  const int32_t sz = ((r.flags >> (kRaySignShift + 2)) & 1) ? -1 : 1;
+  const long long dx = r.d0[0] + cnt[0] * U, dy = r.d0[1] + cnt[1] * U, dz = r.d0[2] + cnt[2] * U;
+  w.vx = r.v0[0] + sx * (int32_t)cnt[0];
+  w.vy = r.v0[1] + sy * (int32_t)cnt[1];
+  w.vz = r.v0[2] + sz * (int32_t)cnt[2];
+  w.nx = r.n[0] - (int32_t)cnt[0];
+  w.ny = r.n[1] - (int32_t)cnt[1];
+  w.nz = r.n[2] - (int32_t)cnt[2];
+  w.sx = sx;
+  w.sy = sy;
+  w.sz = sz;
+  w.ua = U * r.A[0];
+  w.ub = U * r.A[1];
+  w.uc = U * r.A[2];
+  w.cxy = dx * r.A[1] - dy * r.A[0];
+  w.cxz = dx * r.A[2] - dz * r.A[0];
+  w.cyz = dy * r.A[2] - dz * r.A[1];
   w.total = w.nx + w.ny + w.nz;
 }
 

@@ -196,17 +196,13 @@ __device__ __forceinline__ void prepare_occ_ray(const DeviceMap& m, const CallAr
       ok = in_extent(qo, F) && in_extent(qe, F);
     }
     if (ok) {
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        r.a[k] = qo[k];
-        r.b[k] = qe[k];
-      }
       int32_t nmaj;
       const int M = dominant_axis(qo, qe, F, &nmaj);
       nseg = (unsigned int)segment_count(nmaj, m.seg_steps);
       const long long am = sel3(M, qe[0] - qo[0], qe[1] - qo[1], qe[2] - qo[2]);
       r.inv = reciprocal64((unsigned long long)(am < 0 ? -am : am));
       r.flags = kRayValid | (sample ? kRaySample : 0) | (M << kRayAxisShift);
+      ray_constants(qo, qe, F, &r);
       r.nseg = (int32_t)nseg;
       long long l1 = 0;
 #pragma unroll
@@ -235,7 +231,10 @@ __device__ __forceinline__ void ndt_alloc_ray(const DeviceMap& m, long long i) {
   const int F = m.frac_bits;
   const RayRec r = m.rays[i];
   if (!(r.flags & kRaySample)) return;
-  const int32_t slot = region_slot_of(m, (int32_t)(r.b[0] >> F), (int32_t)(r.b[1] >> F), (int32_t)(r.b[2] >> F));
+  const int32_t vx = r.v0[0] + (((r.flags >> kRaySignShift) & 1) ? -r.n[0] : r.n[0]);
+  const int32_t vy = r.v0[1] + (((r.flags >> (kRaySignShift + 1)) & 1) ? -r.n[1] : r.n[1]);
+  const int32_t vz = r.v0[2] + (((r.flags >> (kRaySignShift + 2)) & 1) ? -r.n[2] : r.n[2]);
+  const int32_t slot = region_slot_of(m, vx, vy, vz);
   if (slot < 0) {
     atomicOr(m.status, kStatusMissing);
     return;
@@ -272,7 +271,7 @@ __device__ __forceinline__ void walk_segment(const DeviceMap& m, long long si) {
   const bool last = sg.y == r.nseg - 1;
   const bool sample = (r.flags & kRaySample) != 0;
   Walker w;
-  walker_init(w, r.a, r.b, F, M, (long long)sg.y * S, r.inv);
+  walker_init_rec(w, r, F, M, (long long)sg.y * S);
   int32_t mrem = last ? INT_MAX : S - 1;
   int32_t slot = region_slot_of(m, w.vx, w.vy, w.vz);
   if (slot < 0) {
@@ -358,7 +357,9 @@ __device__ __forceinline__ void hit_ray(const DeviceMap& m, long long i) {
   const long long U = 1LL << F;
   const RayRec r = m.rays[i];
   if (!(r.flags & kRaySample)) return;
-  const int32_t vx = (int32_t)(r.b[0] >> F), vy = (int32_t)(r.b[1] >> F), vz = (int32_t)(r.b[2] >> F);
+  long long b[3];
+  ray_end(r, F, b);
+  const int32_t vx = (int32_t)(b[0] >> F), vy = (int32_t)(b[1] >> F), vz = (int32_t)(b[2] >> F);
   const int32_t slot = region_slot_of(m, vx, vy, vz);
   if (slot < 0) {
     atomicOr(m.status, kStatusMissing);
@@ -374,9 +375,9 @@ __device__ __forceinline__ void hit_ray(const DeviceMap& m, long long i) {
       atomicOr(m.status, kStatusMissing);
       return;
     }
-    const long long px = r.b[0] - (long long)vx * U;
-    const long long py = r.b[1] - (long long)vy * U;
-    const long long pz = r.b[2] - (long long)vz * U;
+    const long long px = b[0] - (long long)vx * U;
+    const long long py = b[1] - (long long)vy * U;
+    const long long pz = b[2] - (long long)vz * U;
     unsigned long long* base = reinterpret_cast<unsigned long long*>(m.ndt) + (long long)ns * 10 * kRegionVoxels + mo;
     const long long vals[10] = {1, px, py, pz, px * px, px * py, px * pz, py * py, py * pz, pz * pz};
 #pragma unroll

@@ -33,7 +33,7 @@ constexpr int kNoAllocBlock = 256;
 
 // Layout of the static array: [counter (256 B)] [ray records] [segments].
 constexpr size_t kCounterBytes = 256;
-constexpr size_t kRaysBytes = sizeof(RayRec) * kNoAllocMaxRays;
+constexpr size_t kRaysBytes = sizeof(EndpointRec) * kNoAllocMaxRays;
 constexpr size_t kSegsBytes = sizeof(int2) * kNoAllocMaxSegments;
 constexpr size_t kNoAllocScratchBytes = kCounterBytes + kRaysBytes + kSegsBytes;
 
@@ -71,12 +71,12 @@ __device__ __forceinline__ bool na_in_extent(const long long q[3], int F) {
 // Per ray: quantise, truncate to the maximum range, append its segments.
 __global__ void __launch_bounds__(kNoAllocBlock) k_noalloc_prepare(CountGrid g, NoAllocArgs a, unsigned char* scratch) {
   unsigned long long* nseg_total = reinterpret_cast<unsigned long long*>(scratch);
-  RayRec* rays = reinterpret_cast<RayRec*>(scratch + kCounterBytes);
+  EndpointRec* rays = reinterpret_cast<EndpointRec*>(scratch + kCounterBytes);
   int2* segs = reinterpret_cast<int2*>(scratch + kCounterBytes + kRaysBytes);
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int F = g.frac_bits;
   unsigned int nseg = 0;
-  RayRec r;
+  EndpointRec r;
   r.flags = 0;
   r.nseg = 0;
   if (i < a.n) {
@@ -138,7 +138,7 @@ __device__ __forceinline__ void na_count(const CountGrid& g, uint32_t* arr, int3
 __global__ void __launch_bounds__(kNoAllocBlock) k_noalloc_walk(CountGrid g, unsigned char* scratch, uint32_t* hits,
                                                                 uint32_t* misses) {
   const unsigned long long* nseg_total = reinterpret_cast<const unsigned long long*>(scratch);
-  const RayRec* rays = reinterpret_cast<const RayRec*>(scratch + kCounterBytes);
+  const EndpointRec* rays = reinterpret_cast<const EndpointRec*>(scratch + kCounterBytes);
   const int2* segs = reinterpret_cast<const int2*>(scratch + kCounterBytes + kRaysBytes);
   long long nseg = (long long)*nseg_total;
   if (nseg > kNoAllocMaxSegments) nseg = kNoAllocMaxSegments;
@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(kNoAllocBlock) k_noalloc_walk(CountGrid g, uns
   for (long long si = (long long)blockIdx.x * blockDim.x + threadIdx.x; si < nseg;
        si += (long long)gridDim.x * blockDim.x) {
     const int2 sg = segs[si];
-    const RayRec r = rays[sg.x];
+    const EndpointRec r = rays[sg.x];
     int32_t nmaj;
     const int M = dominant_axis(r.a, r.b, F, &nmaj);
     const bool last = sg.y == r.nseg - 1;

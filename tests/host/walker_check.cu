@@ -27,7 +27,19 @@ int main(int argc, char** argv) {
       ohm::Walker w;
       const long long am = b[M] - a[M];
       const unsigned long long inv = use_inv ? ohm::reciprocal64((unsigned long long)(am < 0 ? -am : am)) : 0ULL;
-      ohm::walker_init(w, a, b, F, M, (long long)j * S, inv);
+      if (use_inv) {
+        // the kernels' path: per-ray constants, then the segment's state
+        ohm::RayRec rec;
+        rec.flags = 0;
+        rec.inv = inv;
+        ohm::ray_constants(a, b, F, &rec);
+        long long bb[3];
+        ohm::ray_end(rec, F, bb);
+        if (bb[0] != b[0] || bb[1] != b[1] || bb[2] != b[2]) return 3;
+        ohm::walker_init_rec(w, rec, F, M, (long long)j * S);
+      } else {
+        ohm::walker_init(w, a, b, F, M, (long long)j * S, inv);
+      }
       const bool last = j == nseg - 1;
       int mrem = last ? INT_MAX : S - 1;
       uint32_t mo = ohm::morton((uint32_t)(w.vx & 31), (uint32_t)(w.vy & 31), (uint32_t)(w.vz & 31));
