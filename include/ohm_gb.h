@@ -55,7 +55,10 @@ enum {
   OHM_LAYER_OCCUPANCY = 1, /* float log-odds per voxel, NaN = unknown (Sec. II-B) */
   OHM_LAYER_NDT = 2,       /* int64 sample moments per voxel (Sec. II-D, III-C) */
   OHM_LAYER_TSDF = 4,      /* float signed distance + weight per voxel (Sec. II-F) */
-  OHM_LAYER_COUNTS = 8     /* uint32 hits H_i and misses M_i per voxel (Sec. II-D) */
+  OHM_LAYER_COUNTS = 8,    /* uint32 hits H_i and misses M_i per voxel (Sec. II-D) */
+  OHM_LAYER_DECAY = 16     /* decay-rate map (Sec. II-E): per voxel the summed length of the rays'
+                              paths through it, uint64 in units of 2^-20 m; with OHM_LAYER_COUNTS
+                              the reflection rate is lambda = H / sum d */
 };
 
 /* Per-ray flag bits. */
@@ -103,6 +106,11 @@ ohm_status ohm_map_create(const ohm_map_params* params, ohm_map** out);
 void ohm_map_destroy(ohm_map* map);
 
 /* Integrate one ray set (Sec. III-B; one call is one "scan").
+ * Decay layer: every voxel the walk visits gains the length of the ray inside
+ * it, (t_out - t_in) L with L the ray length in metres (float) and t_in, t_out
+ * the ray parameters where the walk enters and leaves it (0 at the start, 1 at
+ * the end point; a crossing of axis k at t = dist_k / A_k, evaluated in float
+ * with one rounding per operation), rounded to 2^-20 m.
  *   origins    n_origins x 3 float world positions, x y z interleaved;
  *              n_origins is 1 (a shared sensor origin) or n.
  *   endpoints  n x 3 float world positions of the samples.
@@ -170,9 +178,10 @@ ohm_status ohm_map_residency(ohm_map* map, int64_t* resident, int64_t* evicted, 
  *              population covariance xx xy xz yy yz zz (m^2); zeros if none
  *   tsdf       n x 2 floats: D, W (zeros if unobserved)
  *   counts     n x 2 uint32: hits H, misses M
+ *   path_sum   n uint64: summed ray path length through the voxel, 2^-20 m units
  * `points` may be host or device memory.  Returns once enqueued. */
 ohm_status ohm_query_voxels(ohm_map* map, const float* points, int64_t n, float* occupancy, uint8_t* known,
-                            float* ndt, float* tsdf, uint32_t* counts, void* stream);
+                            float* ndt, float* tsdf, uint32_t* counts, uint64_t* path_sum, void* stream);
 
 /* Number of pool slots ever used by the map, resident or released by eviction
  * (synchronises `stream`).  Without evictions: the number of regions. */
@@ -187,9 +196,11 @@ ohm_status ohm_map_region_count(ohm_map* map, int64_t* out, void* stream);
  *              Syz, Szz), positions in fixed-point units relative to the
  *              voxel's lower corner
  *   tsdf       count x 32768 x 2 float (D, W)
+ *   path_sum   count x 32768 uint64 summed path length, 2^-20 m units
+ * A non-NULL buffer for a layer the map lacks is OHM_ERR_UNSUPPORTED.
  * Returns once enqueued. */
 ohm_status ohm_map_export(ohm_map* map, int64_t first, int64_t count, int32_t* keys, float* occupancy,
-                          uint32_t* counts, int64_t* ndt, float* tsdf, void* stream);
+                          uint32_t* counts, int64_t* ndt, float* tsdf, uint64_t* path_sum, void* stream);
 
 typedef struct {
   int64_t rays;          /* rays passed to the last integrate call */

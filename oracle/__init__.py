@@ -21,6 +21,8 @@ LAYER_OCCUPANCY = 1
 LAYER_NDT = 2
 LAYER_TSDF = 4
 LAYER_COUNTS = 8
+LAYER_DECAY = 16
+PATH_UNITS_PER_METRE = float(1 << 20)
 
 FLAG_NO_RETURN = 1
 
@@ -59,14 +61,16 @@ def _load():
         lib.oracle_region_count.restype = i64
         lib.oracle_region_count.argtypes = [vp]
         lib.oracle_export.restype = ctypes.c_int
-        lib.oracle_export.argtypes = [vp, i64, i64, p, p, p, p, p, p]
+        lib.oracle_export.argtypes = [vp, i64, i64, p, p, p, p, p, p, p]
         lib.oracle_ndt_region_count.restype = i64
         lib.oracle_ndt_region_count.argtypes = [vp]
         lib.oracle_ndt_sparse.restype = i64
         lib.oracle_ndt_sparse.argtypes = [vp, i64, p, p]
-        lib.oracle_query.argtypes = [vp, p, i64, p, p, p, p]
+        lib.oracle_query.argtypes = [vp, p, i64, p, p, p, p, p]
         lib.oracle_walk.restype = i64
         lib.oracle_walk.argtypes = [p, p, ctypes.c_int32, p, i64]
+        lib.oracle_walk_timed.restype = i64
+        lib.oracle_walk_timed.argtypes = [p, p, ctypes.c_int32, p, p, i64]
         lib.oracle_prepare.argtypes = [vp, p, i64, p, p, i64, p, p, p, p]
         _lib = lib
     return _lib
@@ -135,7 +139,7 @@ class OracleMap:
     def ndt_region_count(self) -> int:
         return int(_load().oracle_ndt_region_count(self._h))
 
-    def export(self, first=0, count=None, occupancy=True, counts=True, ndt=True, tsdf=True):
+    def export(self, first=0, count=None, occupancy=True, counts=True, ndt=True, tsdf=True, path=True):
         """Regions [first, first + count) in (rx, ry, rz) order: a dict of numpy
         arrays (a layer the map lacks, or one not asked for, is None)."""
         total = self.region_count()
@@ -149,11 +153,12 @@ class OracleMap:
         misses = np.zeros((n, REGION_VOXELS), np.uint32) if (L & LAYER_COUNTS and counts) else None
         nd = np.zeros((n, REGION_VOXELS, 10), np.int64) if (L & LAYER_NDT and ndt) else None
         ts = np.zeros((n, REGION_VOXELS, 2), np.float64) if (L & LAYER_TSDF and tsdf) else None
+        ps = np.zeros((n, REGION_VOXELS), np.uint64) if (L & LAYER_DECAY and path) else None
         rc = _load().oracle_export(self._h, first, n, _ptr(keys), _ptr(occ), _ptr(hits), _ptr(misses), _ptr(nd),
-                                   _ptr(ts))
+                                   _ptr(ts), _ptr(ps))
         if rc:
             raise OverflowError("NDT moment sum exceeds int64")
-        return dict(keys=keys, occupancy=occ, hits=hits, misses=misses, ndt=nd, tsdf=ts)
+        return dict(keys=keys, occupancy=occ, hits=hits, misses=misses, ndt=nd, tsdf=ts, path=ps)
 
     def ndt_sparse(self):
         """(voxels (k, 3) int64, moments (k, 10) int64) of every voxel holding
@@ -172,8 +177,9 @@ class OracleMap:
         known = np.zeros(n, np.uint8)
         ndt = np.zeros((n, 10), np.float64)
         tsdf = np.zeros((n, 2), np.float64)
-        _load().oracle_query(self._h, _ptr(pts), n, _ptr(occ), _ptr(known), _ptr(ndt), _ptr(tsdf))
-        return dict(occupancy=occ, known=known, ndt=ndt, tsdf=tsdf)
+        path = np.zeros(n, np.uint64)
+        _load().oracle_query(self._h, _ptr(pts), n, _ptr(occ), _ptr(known), _ptr(ndt), _ptr(tsdf), _ptr(path))
+        return dict(occupancy=occ, known=known, ndt=ndt, tsdf=tsdf, path=path)
 
     def prepare(self, origins, endpoints, flags=None):
         o = np.ascontiguousarray(origins, dtype=np.float32).reshape(-1, 3)
@@ -197,3 +203,16 @@ def walk(a, b, frac_bits: int = 16):
     out = np.zeros((max(n, 1), 3), np.int64)
     lib.oracle_walk(_ptr(a), _ptr(b), frac_bits, _ptr(out), n)
     return out[:n]
+
+
+def walk_timed(a, b, frac_bits: int = 16):
+    """walk() plus each voxel's (t_in, t_out) ray parameters as uint64
+    fractions of 2^32, the decay-rate layer's distance bookkeeping (Sec. II-E)."""
+    a = np.ascontiguousarray(a, dtype=np.int64).reshape(3)
+    b = np.ascontiguousarray(b, dtype=np.int64).reshape(3)
+    lib = _load()
+    n = lib.oracle_walk_timed(_ptr(a), _ptr(b), frac_bits, None, None, 0)
+    out = np.zeros((max(n, 1), 3), np.int64)
+    t = np.zeros((max(n, 1), 2), np.uint64)
+    lib.oracle_walk_timed(_ptr(a), _ptr(b), frac_bits, _ptr(out), _ptr(t), n)
+    return out[:n], t[:n]

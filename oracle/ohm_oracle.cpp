@@ -27,6 +27,19 @@
 //   * NDT-OM: per-voxel count, sum and outer-product sum of the sample positions
 //     (Sec. II-D, III-C), from which mean and covariance are the sample
 //     statistics of the points that fell in the voxel.
+//   * Decay rate (Sec. II-E): per voxel the summed distance sum_j d_i(j) that
+//     the rays travel through it, the denominator of lambda_i = H_i / sum d_i;
+//     with the counts layer H_i is the numerator.  A ray from a to b with
+//     length L (after truncation) is parametrised by t in [0, 1]; it enters a
+//     voxel at the crossing time of the boundary it last stepped (t = dist /
+//     |delta| of that axis, Amanatides & Woo's tMax) and leaves at the next
+//     crossing, or at t = 1 in the voxel of b; d = (t_out - t_in) L.
+//     Reading (the paper gives no precision): distances are integers in units
+//     of 2^-20 m.  L = rint(|b - a| * voxel_size / 2^F * 2^20) in double; a
+//     crossing's t is floor(2^32 dist / |delta|) / 2^32 and its position along
+//     the ray P(t) = rint(t L); d = P(t_out) - P(t_in).  P is monotone, so
+//     no d is negative, the d of one ray add up to exactly L, and the sums
+//     do not depend on the order of the rays.
 //   * TSDF: projective signed distance s = d - (c - o).u along the ray,
 //     truncated to [-tau, tau], for the voxels the walk visits between ranges
 //     max(0, d - tau) and d + tau; per call the voxel keeps the running
@@ -52,6 +65,9 @@ constexpr int kLayerOccupancy = 1;
 constexpr int kLayerNdt = 2;
 constexpr int kLayerTsdf = 4;
 constexpr int kLayerCounts = 8;
+constexpr int kLayerDecay = 16;
+
+constexpr double kPathUnitsPerMetre = 1048576.0;  // 2^20
 
 constexpr uint8_t kFlagNoReturn = 1;
 
@@ -105,6 +121,7 @@ struct Region {
   std::vector<__int128> ndt;        // 10 per voxel: n, Sx, Sy, Sz, Sxx, Sxy, Sxz, Syy, Syz, Szz
   std::vector<double> tsdf_d;       // running signed distance
   std::vector<double> tsdf_w;       // running weight
+  std::vector<uint64_t> path;       // decay rate: sum_j d_i(j) in 2^-20 m
 };
 
 struct Map {
@@ -142,6 +159,7 @@ Region& region_for(Map& m, const Voxel& v) {
     r.tsdf_d.assign(kRegionVoxels, 0.0);
     r.tsdf_w.assign(kRegionVoxels, 0.0);
   }
+  if (L & kLayerDecay) r.path.assign(kRegionVoxels, 0ull);
   return m.regions.emplace(k, std::move(r)).first->second;
 }
 
@@ -207,6 +225,57 @@ std::vector<Voxel> walk(const int64_t a[3], const int64_t b[3], int64_t unit) {
   return out;
 }
 
+// One voxel of a walk with the ray parameters at which the ray enters and
+// leaves it (Sec. II-E needs the distance travelled inside each voxel), as
+// fractions of 2^32: t = 2^32 means the end point b.
+struct TimedVoxel {
+  Voxel v;
+  uint64_t t_in, t_out;
+};
+
+// The same walk as walk(), also reporting each voxel's entry and exit times.
+// The crossing of axis k happens at t = dist[k] / |delta_k|, kept as
+// floor(2^32 dist[k] / |delta_k|).
+std::vector<TimedVoxel> walk_timed(const int64_t a[3], const int64_t b[3], int64_t unit) {
+  Voxel v = voxel_of(a, unit);
+  const Voxel end = voxel_of(b, unit);
+  int64_t remaining[3], step[3], adelta[3], dist[3];
+  for (int k = 0; k < 3; ++k) {
+    int64_t delta = b[k] - a[k];
+    adelta[k] = delta < 0 ? -delta : delta;
+    step[k] = delta < 0 ? -1 : 1;
+    remaining[k] = end.v[k] - v.v[k];
+    if (remaining[k] < 0) remaining[k] = -remaining[k];
+    if (step[k] > 0)
+      dist[k] = (v.v[k] + 1) * unit - a[k];
+    else
+      dist[k] = a[k] - v.v[k] * unit;
+  }
+  std::vector<TimedVoxel> out;
+  uint64_t t = 0;
+  while (remaining[0] + remaining[1] + remaining[2] > 0) {
+    int best = -1;
+    for (int k = 2; k >= 0; --k) {
+      if (remaining[k] == 0) continue;
+      if (best < 0) {
+        best = k;
+        continue;
+      }
+      __int128 tk = (__int128)dist[k] * adelta[best];
+      __int128 tb = (__int128)dist[best] * adelta[k];
+      if (tk < tb) best = k;
+    }
+    const uint64_t t_cross = (uint64_t)(((__int128)dist[best] << 32) / adelta[best]);
+    out.push_back(TimedVoxel{v, t, t_cross});
+    t = t_cross;
+    v.v[best] += step[best];
+    dist[best] += unit;
+    remaining[best] -= 1;
+  }
+  out.push_back(TimedVoxel{v, t, (uint64_t)1 << 32});
+  return out;
+}
+
 struct PreparedRay {
   int64_t qo[3];
   int64_t qe[3];
@@ -267,6 +336,28 @@ void apply_miss(Map& m, const Voxel& v) {
       for (int k = 0; k < 10; ++k) r.ndt[(size_t)i * 10 + k] = 0;
   }
   if (m.p.layers & kLayerCounts) r.misses[i] += 1u;
+}
+
+// Length of the walk from qo to qe in 2^-20 m (the L of Sec. II-E).
+uint64_t walk_length(const Map& m, const int64_t qo[3], const int64_t qe[3]) {
+  double d[3];
+  for (int a = 0; a < 3; ++a) d[a] = (double)(qe[a] - qo[a]);
+  double len2 = d[0] * d[0];
+  len2 = len2 + d[1] * d[1];
+  len2 = len2 + d[2] * d[2];
+  const double metres = std::sqrt(len2) * (m.p.voxel_size / (double)m.unit);
+  return (uint64_t)std::llrint(metres * kPathUnitsPerMetre);
+}
+
+// Position along the ray, in 2^-20 m, at parameter t (a fraction of 2^32).
+uint64_t ray_position(uint64_t t, uint64_t length) {
+  return (uint64_t)(((unsigned __int128)t * length + ((unsigned __int128)1 << 31)) >> 32);
+}
+
+// Decay rate (Sec. II-E): add the distance a ray travels inside the voxel.
+void apply_path(Map& m, const TimedVoxel& tv, uint64_t length) {
+  Region& r = region_for(m, tv.v);
+  r.path[local_index(tv.v)] += ray_position(tv.t_out, length) - ray_position(tv.t_in, length);
 }
 
 void apply_hit(Map& m, const Voxel& v, const int64_t qe[3]) {
@@ -378,7 +469,7 @@ int64_t oracle_integrate(void* h, const float* origins, int64_t n_origins, const
     if (prepare_ray(m, o, endpoints + 3 * i, flags ? flags[i] : 0, &r)) rays.push_back(r);
   }
   int64_t visits = 0;
-  const int occ_like = kLayerOccupancy | kLayerCounts | kLayerNdt;
+  const int occ_like = kLayerOccupancy | kLayerCounts | kLayerNdt | kLayerDecay;
   if (m.p.layers & occ_like) {
     // Phase 1: every pass-through (miss) of every ray.
     for (const PreparedRay& r : rays) {
@@ -387,6 +478,10 @@ int64_t oracle_integrate(void* h, const float* origins, int64_t n_origins, const
       size_t count = vox.size();
       if (r.has_sample) count -= 1;  // the sample voxel gets the hit instead
       for (size_t j = 0; j < count; ++j) apply_miss(m, vox[j]);
+      if (m.p.layers & kLayerDecay) {
+        const uint64_t length = walk_length(m, r.qo, r.qe);
+        for (const TimedVoxel& tv : walk_timed(r.qo, r.qe, m.unit)) apply_path(m, tv, length);
+      }
     }
     // Phase 2: every sample (hit).
     for (const PreparedRay& r : rays) {
@@ -426,10 +521,11 @@ int64_t oracle_region_count(void* h) { return (int64_t)static_cast<Map*>(h)->reg
 // Any output pointer may be null.  Per region: keys 3 x int64; occupancy 32768
 // float; hits, misses 32768 uint32; ndt 32768 x 10 int64 (n, Sx, Sy, Sz, Sxx,
 // Sxy, Sxz, Syy, Syz, Szz; zeros for a region without samples); tsdf 32768 x 2
-// double (D, W).  Voxel order inside a region: x fastest.  Returns 0, or 1 if an
-// NDT sum does not fit in int64.
+// double (D, W); path 32768 uint64 (decay rate: summed distance, 2^-20 m).
+// Voxel order inside a region: x fastest.  Returns 0, or 1 if an NDT sum does
+// not fit in int64.
 int oracle_export(void* h, int64_t first, int64_t count, int64_t* keys, float* occupancy, uint32_t* hits,
-                  uint32_t* misses, int64_t* ndt, double* tsdf) {
+                  uint32_t* misses, int64_t* ndt, double* tsdf, uint64_t* path) {
   Map& m = *static_cast<Map*>(h);
   int rc = 0;
   int64_t pos = 0;
@@ -463,6 +559,7 @@ int oracle_export(void* h, int64_t first, int64_t count, int64_t* keys, float* o
         tsdf[(idx * kRegionVoxels + j) * 2 + 1] = r.tsdf_w[j];
       }
     }
+    if (path && !r.path.empty()) std::memcpy(path + idx * kRegionVoxels, r.path.data(), sizeof(uint64_t) * kRegionVoxels);
     ++idx;
   }
   return rc;
@@ -503,7 +600,7 @@ int64_t oracle_ndt_region_count(void* h) {
 // (count, mean xyz in metres, covariance xx xy xz yy yz zz in m^2; zeros if no
 // sample); tsdf: n x 2 (D, W).  Any output may be null.
 void oracle_query(void* h, const float* pts, int64_t n, float* occupancy, uint8_t* known, double* ndt,
-                  double* tsdf) {
+                  double* tsdf, uint64_t* path) {
   Map& m = *static_cast<Map*>(h);
   const double cell = m.p.voxel_size / (double)m.unit;  // metres per fixed-point unit
   for (int64_t i = 0; i < n; ++i) {
@@ -538,6 +635,7 @@ void oracle_query(void* h, const float* pts, int64_t n, float* occupancy, uint8_
       tsdf[2 * i] = (r && !r->tsdf_d.empty()) ? r->tsdf_d[li] : 0.0;
       tsdf[2 * i + 1] = (r && !r->tsdf_w.empty()) ? r->tsdf_w[li] : 0.0;
     }
+    if (path) path[i] = (r && !r->path.empty()) ? r->path[li] : 0ull;
   }
 }
 
@@ -661,6 +759,19 @@ int64_t oracle_walk(const int64_t* a, const int64_t* b, int32_t frac_bits, int64
   std::vector<Voxel> vox = walk(a, b, (int64_t)1 << frac_bits);
   for (int64_t i = 0; i < (int64_t)vox.size() && i < cap; ++i)
     for (int k = 0; k < 3; ++k) out[3 * i + k] = vox[(size_t)i].v[k];
+  return (int64_t)vox.size();
+}
+
+// The timed walk alone, for tests: voxels (cap x 3) and their (t_in, t_out)
+// (cap x 2, fractions of 2^32).  Returns the number of voxels.
+int64_t oracle_walk_timed(const int64_t* a, const int64_t* b, int32_t frac_bits, int64_t* out, uint64_t* times,
+                          int64_t cap) {
+  std::vector<TimedVoxel> vox = walk_timed(a, b, (int64_t)1 << frac_bits);
+  for (int64_t i = 0; i < (int64_t)vox.size() && i < cap; ++i) {
+    for (int k = 0; k < 3; ++k) out[3 * i + k] = vox[(size_t)i].v.v[k];
+    times[2 * i] = vox[(size_t)i].t_in;
+    times[2 * i + 1] = vox[(size_t)i].t_out;
+  }
   return (int64_t)vox.size();
 }
 

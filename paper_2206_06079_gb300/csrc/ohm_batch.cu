@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(kBlock) k_batch_prepare(const BatchDesc* desc,
     const bool active = i < a.n;
     if (tsdf) {
       if (m.layers & kLayerTsdf) prepare_tsdf_ray(m, a, i, active);
-    } else if (m.layers & (kLayerOcc | kLayerCounts | kLayerNdt)) {
+    } else if (m.layers & (kLayerOcc | kLayerCounts | kLayerNdt | kLayerDecay)) {
       prepare_occ_ray(m, a, i, active);
     }
   }
@@ -138,13 +138,7 @@ __global__ void __launch_bounds__(kBlock, OHM_WALK_MIN_BLOCKS) k_batch_walk(cons
     const int mi = batch_find(sh, g);
     const DeviceMap& m = sh.maps[mi];
     const long long si = g - sh.pref[mi];
-    const bool occ = (m.layers & kLayerOcc) != 0, cnt = (m.layers & kLayerCounts) != 0;
-    if (occ && cnt)
-      walk_segment<true, true>(m, si);
-    else if (occ)
-      walk_segment<true, false>(m, si);
-    else if (cnt)
-      walk_segment<false, true>(m, si);
+    walk_segment_any(m, si);
   }
 }
 
@@ -320,7 +314,7 @@ ohm_status ohm_batch_create(ohm_map* const* maps, int32_t n_maps, ohm_batch** ou
   for (int i = 0; i < n_maps; ++i) {
     b->maps[i] = maps[i];
     const uint32_t L = maps[i]->p.layers;
-    b->any_occ = b->any_occ || (L & (OHM_LAYER_OCCUPANCY | OHM_LAYER_COUNTS));
+    b->any_occ = b->any_occ || (L & (OHM_LAYER_OCCUPANCY | OHM_LAYER_COUNTS | OHM_LAYER_DECAY));
     b->any_ndt = b->any_ndt || (L & OHM_LAYER_NDT);
     b->any_tsdf = b->any_tsdf || (L & OHM_LAYER_TSDF);
   }

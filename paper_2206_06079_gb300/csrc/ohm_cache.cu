@@ -54,6 +54,7 @@ struct HostRegion {
   int32_t coords[3];
   void* occ = nullptr;
   void* counts = nullptr;
+  void* decay = nullptr;
   void* ndt = nullptr;
   void* tsdf = nullptr;
 };
@@ -61,6 +62,7 @@ struct HostRegion {
 struct HostStore {
   PinnedSlab occ{sizeof(float) * kRegionVoxels};
   PinnedSlab counts{sizeof(unsigned long long) * kRegionVoxels};
+  PinnedSlab decay{sizeof(unsigned long long) * kRegionVoxels};
   PinnedSlab ndt{sizeof(long long) * 10 * kRegionVoxels};
   PinnedSlab tsdf{sizeof(float2) * kRegionVoxels};
   std::unordered_map<long long, HostRegion> regions;
@@ -122,6 +124,7 @@ __global__ void k_reset_slots(DeviceMap m, const int32_t* slots, int n, const in
       const long long off = (long long)slots[r] * per + v;
       if (m.occ) reinterpret_cast<unsigned int*>(m.occ)[off] = 0xFFFFFFFFu;
       if (m.counts) m.counts[off] = 0ULL;
+      if (m.decay) m.decay[off] = 0ULL;
       if (m.tsdf) m.tsdf[off] = make_float2(0.f, 0.f);
       if (v == 0) m.ndt_slot[slots[r]] = -1;
     } else {
@@ -244,6 +247,11 @@ cudaError_t cache_evict(ohm_map* m, long long target, long long* evicted) {
       if (!r.counts) return cudaErrorMemoryAllocation;
       e = cudaMemcpyAsync(r.counts, d.counts + off, sizeof(unsigned long long) * kRegionVoxels, cudaMemcpyDeviceToHost, 0);
     }
+    if (e == cudaSuccess && d.decay) {
+      r.decay = hs->decay.get();
+      if (!r.decay) return cudaErrorMemoryAllocation;
+      e = cudaMemcpyAsync(r.decay, d.decay + off, sizeof(unsigned long long) * kRegionVoxels, cudaMemcpyDeviceToHost, 0);
+    }
     if (e == cudaSuccess && d.tsdf) {
       r.tsdf = hs->tsdf.get();
       if (!r.tsdf) return cudaErrorMemoryAllocation;
@@ -336,6 +344,8 @@ cudaError_t cache_restore(ohm_map* m, const std::vector<long long>& want, long l
       e = cudaMemcpyAsync(d.counts + off, r.counts, sizeof(unsigned long long) * kRegionVoxels, cudaMemcpyHostToDevice, 0);
     if (e == cudaSuccess && r.tsdf)
       e = cudaMemcpyAsync(d.tsdf + off, r.tsdf, sizeof(float2) * kRegionVoxels, cudaMemcpyHostToDevice, 0);
+    if (e == cudaSuccess && r.decay)
+      e = cudaMemcpyAsync(d.decay + off, r.decay, sizeof(unsigned long long) * kRegionVoxels, cudaMemcpyHostToDevice, 0);
     if (e == cudaSuccess && r.ndt)
       e = cudaMemcpyAsync(d.ndt + (long long)nb * 10 * kRegionVoxels, r.ndt, sizeof(long long) * 10 * kRegionVoxels,
                           cudaMemcpyHostToDevice, 0);
@@ -360,6 +370,7 @@ cudaError_t cache_restore(ohm_map* m, const std::vector<long long>& want, long l
     HostRegion& r = hs->regions[k];
     hs->occ.put(r.occ);
     hs->counts.put(r.counts);
+    hs->decay.put(r.decay);
     hs->ndt.put(r.ndt);
     hs->tsdf.put(r.tsdf);
     hs->regions.erase(k);

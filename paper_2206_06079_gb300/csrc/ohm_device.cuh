@@ -3,6 +3,7 @@
 // exact fixed-point voxel walk shared by every kernel.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -20,7 +21,8 @@ constexpr int kRegionVoxels = 1 << (3 * kRegionShift);
 constexpr long long kEmptyKey = -1;              // never a packed key (packed keys are < 2^63)
 constexpr long long kTombKey = -2;               // a key removed by a rolled-back call
 
-constexpr uint32_t kLayerOcc = 1, kLayerNdt = 2, kLayerTsdf = 4, kLayerCounts = 8;
+constexpr uint32_t kLayerOcc = 1, kLayerNdt = 2, kLayerTsdf = 4, kLayerCounts = 8, kLayerDecay = 16;
+constexpr float kDecayUnits = 1048576.0f;  // path lengths are summed in 2^-20 m
 constexpr uint8_t kFlagNoReturn = 1;
 
 // Status bits latched in device memory (0 = fine).
@@ -35,6 +37,8 @@ constexpr int kStatusRestore = 32;   // the call touched evicted regions: restor
 constexpr long long kSlotPending = -1;    // inserted by this kernel, slot not yet written (or none left)
 constexpr long long kSlotEvicted = -3;    // region evicted to host memory
 constexpr long long kSlotRestoring = -4;  // evicted, and a restore was requested by the current call
+
+constexpr int32_t kRayValid = 1, kRaySample = 2, kRayAxisShift = 4, kRaySignShift = 8;
 
 // Ray record written by the occupancy prepare kernel: the walk from a to b
 // (fixed point) reduced to per-axis 32-bit constants, so that every segment of
@@ -51,7 +55,35 @@ struct __align__(16) RayRec {
   int32_t flags;           // kRayValid | kRaySample | dominant axis << kRayAxisShift | signs
   int32_t nseg;            // number of segments
 };
-constexpr int32_t kRayValid = 1, kRaySample = 2, kRayAxisShift = 4, kRaySignShift = 8;
+
+// Decay-rate record of a ray (written only for maps with the decay layer):
+// reciprocal64 of A per axis and the walk length L in 2^-20 m.
+struct __align__(16) DecayRec {
+  unsigned long long inv[3];
+  unsigned long long length;
+};
+
+// Length of the walk from a to b in units of 2^-20 m (the decay layer's L):
+// rint(sqrt(|b - a|^2) * voxel_size / 2^F * 2^20), double, one rounding per
+// operation.
+__host__ __device__ __forceinline__ unsigned long long walk_length_units(const long long a[3], const long long b[3],
+                                                                         double voxel_size, int F) {
+  double d[3];
+OHM_UNROLL
+  for (int k = 0; k < 3; ++k) d[k] = (double)(b[k] - a[k]);
+  const double per_unit = voxel_size / (double)(1LL << F);
+#ifdef __CUDA_ARCH__
+  double l2 = __dmul_rn(d[0], d[0]);
+  l2 = __dadd_rn(l2, __dmul_rn(d[1], d[1]));
+  l2 = __dadd_rn(l2, __dmul_rn(d[2], d[2]));
+  return (unsigned long long)__double2ll_rn(__dmul_rn(__dmul_rn(__dsqrt_rn(l2), per_unit), 1048576.0));
+#else
+  double l2 = d[0] * d[0];
+  l2 = l2 + d[1] * d[1];
+  l2 = l2 + d[2] * d[2];
+  return (unsigned long long)std::llrint((std::sqrt(l2) * per_unit) * 1048576.0);
+#endif
+}
 
 // A ray kept as its two fixed-point end points (the allocation-free entry
 // point's record).
@@ -101,6 +133,7 @@ struct DeviceMap {
   int32_t* region_coords;        // [max_regions][3]
   float* occ;                    // [max_regions][32768], Morton order inside a region
   unsigned long long* counts;    // [max_regions][32768], hits << 32 | misses
+  unsigned long long* decay;     // [max_regions][32768], summed path length, 2^-20 m
   int32_t* ndt_slot;             // [max_regions], -1 = no NDT layer yet
   int32_t* ndt_count;
   int32_t max_ndt;
@@ -122,6 +155,7 @@ struct DeviceMap {
   int32_t max_restore;
   // per-call scratch
   RayRec* rays;
+  DecayRec* decay_rays;  // [max_rays], decay layer only
   TsdfRec* trays;
   int2* segs;                    // (ray, segment index)
   long long max_segs;

@@ -35,11 +35,11 @@ __global__ void __launch_bounds__(kBlock) k_ndt_alloc(DeviceMap m, long long n) 
   OHM_GRID_STRIDE(i, n) ndt_alloc_ray(m, i);
 }
 
-template <bool kOcc, bool kCounts>
+template <bool kOcc, bool kCounts, bool kDecay>
 __global__ void __launch_bounds__(kBlock, OHM_WALK_MIN_BLOCKS) k_walk_miss(DeviceMap m) {
   if (latched(m)) return;
   const long long nseg = (long long)m.calls->segments;
-  OHM_GRID_STRIDE(si, nseg) walk_segment<kOcc, kCounts>(m, si);
+  OHM_GRID_STRIDE(si, nseg) walk_segment<kOcc, kCounts, kDecay>(m, si);
 }
 
 template <bool kOcc, bool kCounts, bool kNdt>
@@ -73,7 +73,8 @@ __global__ void k_end(DeviceMap m) {
 // Query and export.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kBlock) k_query(DeviceMap m, const float* pts, long long n, float* occupancy,
-                                                   uint8_t* known, float* ndt, float* tsdf, uint32_t* counts) {
+                                                   uint8_t* known, float* ndt, float* tsdf, uint32_t* counts,
+                                                   unsigned long long* path_sum) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int F = m.frac_bits;
@@ -99,6 +100,7 @@ __global__ void __launch_bounds__(kBlock) k_query(DeviceMap m, const float* pts,
     if (occupancy) occupancy[i] = l;
     if (known) known[i] = (l == l) ? 1 : 0;
   }
+  if (path_sum) path_sum[i] = (slot >= 0 && (m.layers & kLayerDecay)) ? m.decay[off] : 0ULL;
   if (counts) {
     unsigned long long c = 0;
     if (slot >= 0 && (m.layers & kLayerCounts)) c = m.counts[off];
@@ -144,7 +146,8 @@ __global__ void __launch_bounds__(kBlock) k_query(DeviceMap m, const float* pts,
 }
 
 __global__ void __launch_bounds__(kBlock) k_export(DeviceMap m, long long first, long long count, int32_t* keys,
-                                                    float* occupancy, uint32_t* counts, long long* ndt, float* tsdf) {
+                                                    float* occupancy, uint32_t* counts, long long* ndt, float* tsdf,
+                                                    unsigned long long* path_sum) {
   const long long total = count * kRegionVoxels;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
@@ -160,6 +163,7 @@ __global__ void __launch_bounds__(kBlock) k_export(DeviceMap m, long long first,
       counts[2 * t + 0] = (uint32_t)(c >> 32);
       counts[2 * t + 1] = (uint32_t)(c & 0xffffffffu);
     }
+    if (path_sum) path_sum[t] = (m.layers & kLayerDecay) ? m.decay[off] : 0ULL;
     if (tsdf) {
       const float2 dw = (m.layers & kLayerTsdf) ? m.tsdf[off] : make_float2(0.f, 0.f);
       tsdf[2 * t + 0] = dw.x;
@@ -179,7 +183,7 @@ __global__ void __launch_bounds__(kBlock) k_export(DeviceMap m, long long first,
 // ---------------------------------------------------------------------------
 int walk_blocks_per_sm() {
   int b = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_walk_miss<true, true>, kBlock, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_walk_miss<true, true, false>, kBlock, 0);
   return b > 0 ? b : 1;
 }
 
@@ -199,24 +203,30 @@ cudaError_t launch_integrate(ohm_map* map, const CallArgs& args, cudaStream_t st
   DeviceMap& m = map->d;
   const bool occ = (m.layers & kLayerOcc) != 0, cnt = (m.layers & kLayerCounts) != 0, ndt = (m.layers & kLayerNdt) != 0;
   const bool tsdf = (m.layers & kLayerTsdf) != 0;
+  const bool occ_like = occ || cnt || ndt || (m.layers & kLayerDecay);
   const long long n = args.n;
   const int grid = map->walk_blocks;
   const long long per_ray_blocks = blocks_for(n) > 0 ? blocks_for(n) : 1;
   const int ray_grid = (int)(per_ray_blocks < grid ? per_ray_blocks : grid);
   const unsigned prb = (unsigned)per_ray_blocks;
   OHM_LAUNCH(OHM_STAGE_BEGIN, k_begin<<<1, 1, 0, stream>>>(m, n));
-  if (occ || cnt || ndt) {
+  if (occ_like) {
     OHM_LAUNCH(OHM_STAGE_PREPARE, k_prepare_occ<<<prb, kBlock, 0, stream>>>(m, args));
     if (ndt) OHM_LAUNCH(OHM_STAGE_NDT_ALLOC, k_ndt_alloc<<<ray_grid, kBlock, 0, stream>>>(m, n));
   }
   if (tsdf) OHM_LAUNCH(OHM_STAGE_PREPARE_TSDF, k_prepare_tsdf<<<prb, kBlock, 0, stream>>>(m, args));
-  if (occ || cnt) {
-    if (occ && cnt)
-      OHM_LAUNCH(OHM_STAGE_WALK, k_walk_miss<true, true><<<grid, kBlock, 0, stream>>>(m));
-    else if (occ)
-      OHM_LAUNCH(OHM_STAGE_WALK, k_walk_miss<true, false><<<grid, kBlock, 0, stream>>>(m));
-    else
-      OHM_LAUNCH(OHM_STAGE_WALK, k_walk_miss<false, true><<<grid, kBlock, 0, stream>>>(m));
+  const bool dec = (m.layers & kLayerDecay) != 0;
+  if (occ || cnt || dec) {
+    const int sel = (occ ? 4 : 0) | (cnt ? 2 : 0) | (dec ? 1 : 0);
+    switch (sel) {
+      case 7: OHM_LAUNCH(OHM_STAGE_WALK, k_walk_miss<true, true, true><<<grid, kBlock, 0, stream>>>(m)); break;
+      case 6: OHM_LAUNCH(OHM_STAGE_WALK, k_walk_miss<true, true, false><<<grid, kBlock, 0, stream>>>(m)); break;
+      case 5: OHM_LAUNCH(OHM_STAGE_WALK, k_walk_miss<true, false, true><<<grid, kBlock, 0, stream>>>(m)); break;
+      case 4: OHM_LAUNCH(OHM_STAGE_WALK, k_walk_miss<true, false, false><<<grid, kBlock, 0, stream>>>(m)); break;
+      case 3: OHM_LAUNCH(OHM_STAGE_WALK, k_walk_miss<false, true, true><<<grid, kBlock, 0, stream>>>(m)); break;
+      case 2: OHM_LAUNCH(OHM_STAGE_WALK, k_walk_miss<false, true, false><<<grid, kBlock, 0, stream>>>(m)); break;
+      default: OHM_LAUNCH(OHM_STAGE_WALK, k_walk_miss<false, false, true><<<grid, kBlock, 0, stream>>>(m)); break;
+    }
   }
   if (occ || cnt || ndt) {
     const int sel = (occ ? 4 : 0) | (cnt ? 2 : 0) | (ndt ? 1 : 0);
@@ -240,18 +250,20 @@ cudaError_t launch_integrate(ohm_map* map, const CallArgs& args, cudaStream_t st
 }
 
 cudaError_t launch_query(ohm_map* map, const float* points, long long n, float* occupancy, uint8_t* known, float* ndt,
-                         float* tsdf, uint32_t* counts, cudaStream_t stream) {
+                         float* tsdf, uint32_t* counts, unsigned long long* path_sum, cudaStream_t stream) {
   if (n > 0)
-    k_query<<<(unsigned)blocks_for(n), kBlock, 0, stream>>>(map->d, points, n, occupancy, known, ndt, tsdf, counts);
+    k_query<<<(unsigned)blocks_for(n), kBlock, 0, stream>>>(map->d, points, n, occupancy, known, ndt, tsdf, counts,
+                                                            path_sum);
   return cudaGetLastError();
 }
 
 cudaError_t launch_export(ohm_map* map, long long first, long long count, int32_t* keys, float* occupancy,
-                          uint32_t* counts, long long* ndt, float* tsdf, cudaStream_t stream) {
+                          uint32_t* counts, long long* ndt, float* tsdf, unsigned long long* path_sum,
+                          cudaStream_t stream) {
   if (count > 0) {
     long long b = blocks_for(count * kRegionVoxels);
     if (b > 65535LL * 16) b = 65535LL * 16;
-    k_export<<<(unsigned)b, kBlock, 0, stream>>>(map->d, first, count, keys, occupancy, counts, ndt, tsdf);
+    k_export<<<(unsigned)b, kBlock, 0, stream>>>(map->d, first, count, keys, occupancy, counts, ndt, tsdf, path_sum);
   }
   return cudaGetLastError();
 }

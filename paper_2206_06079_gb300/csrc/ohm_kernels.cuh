@@ -204,6 +204,13 @@ __device__ __forceinline__ void prepare_occ_ray(const DeviceMap& m, const CallAr
       r.flags = kRayValid | (sample ? kRaySample : 0) | (M << kRayAxisShift);
       ray_constants(qo, qe, F, &r);
       r.nseg = (int32_t)nseg;
+      if (m.layers & kLayerDecay) {
+        DecayRec dr;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) dr.inv[k] = reciprocal64((unsigned long long)r.A[k]);
+        dr.length = walk_length_units(qo, qe, m.voxel_size, F);
+        m.decay_rays[i] = dr;
+      }
       long long l1 = 0;
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
@@ -228,7 +235,6 @@ __device__ __forceinline__ void prepare_occ_ray(const DeviceMap& m, const CallAr
 
 // Per sample: give the sample's region an NDT layer.
 __device__ __forceinline__ void ndt_alloc_ray(const DeviceMap& m, long long i) {
-  const int F = m.frac_bits;
   const RayRec r = m.rays[i];
   if (!(r.flags & kRaySample)) return;
   const int32_t vx = r.v0[0] + (((r.flags >> kRaySignShift) & 1) ? -r.n[0] : r.n[0]);
@@ -260,7 +266,21 @@ __device__ __forceinline__ void ndt_alloc_ray(const DeviceMap& m, long long i) {
 // write of each voxel in global memory.  So the thread walks kWalkBatch voxels
 // ahead, then issues all their loads at once, then all their CASes at once,
 // keeping that many memory operations in flight instead of one.
-template <bool kOcc, bool kCounts>
+// Decay layer: distance along the ray, in 2^-20 m, at which the walk crosses
+// a boundary of an axis that has taken `done` steps.  The crossing happens at
+// t = dist / A with dist = d0 + done U; t is taken as floor(2^32 dist / A) /
+// 2^32 (exact, by the reciprocal inv = reciprocal64(A); 2^32 dist < 2^62) and
+// the distance as rint(t L).  Monotone in t, so per-voxel differences are
+// never negative, and they add up to L over the ray.
+__device__ __forceinline__ unsigned long long decay_position(long long dist, int32_t A, unsigned long long inv,
+                                                             unsigned long long length) {
+  const unsigned long long tq = div_by_inv((unsigned long long)dist << 32, (unsigned long long)A, inv);
+  const unsigned long long lo = tq * length, hi = __umul64hi(tq, length);
+  const unsigned long long lo2 = lo + (1ULL << 31);
+  return ((hi + (lo2 < lo ? 1ULL : 0ULL)) << 32) | (lo2 >> 32);
+}
+
+template <bool kOcc, bool kCounts, bool kDecay>
 __device__ __forceinline__ void walk_segment(const DeviceMap& m, long long si) {
   const int F = m.frac_bits;
   const int32_t S = m.seg_steps;
@@ -279,6 +299,17 @@ __device__ __forceinline__ void walk_segment(const DeviceMap& m, long long si) {
     return;
   }
   uint32_t mo = local_morton(w.vx, w.vy, w.vz);
+  // decay layer: position (2^-20 m along the ray) where the walk entered the current voxel
+  DecayRec dr;
+  unsigned long long pos_in = 0;
+  if (kDecay) {
+    dr = m.decay_rays[sg.x];
+    if (sg.y > 0) {
+      const int32_t d0M = M == 0 ? r.d0[0] : (M == 1 ? r.d0[1] : r.d0[2]);
+      const int32_t AM = M == 0 ? r.A[0] : (M == 1 ? r.A[1] : r.A[2]);
+      pos_in = decay_position((long long)d0M + ((long long)(sg.y * S - 1) << F), AM, r.inv, dr.length);
+    }
+  }
   bool done = false;
   while (!done) {
     uint32_t off[kWalkBatch];  // voxel offsets (< 2^31: at most 2^16 regions of 2^15 voxels)
@@ -294,10 +325,21 @@ __device__ __forceinline__ void walk_segment(const DeviceMap& m, long long si) {
         if (kCounts) atomicAdd(m.counts + off[j], 1ULL);
       }
       if (w.total == 0) {
+        if (kDecay && dr.length != pos_in) atomicAdd(m.decay + off[j], dr.length - pos_in);
         done = true;
         continue;
       }
       const int axis = walker_choose(w);
+      if (kDecay) {
+        const int32_t d0a = axis == 0 ? r.d0[0] : (axis == 1 ? r.d0[1] : r.d0[2]);
+        const int32_t Aa = axis == 0 ? r.A[0] : (axis == 1 ? r.A[1] : r.A[2]);
+        const int32_t taken = axis == 0 ? r.n[0] - w.nx : (axis == 1 ? r.n[1] - w.ny : r.n[2] - w.nz);
+        const unsigned long long inv = axis == 0 ? dr.inv[0] : (axis == 1 ? dr.inv[1] : dr.inv[2]);
+        const unsigned long long pos_out = decay_position((long long)d0a + ((long long)taken << F), Aa, inv, dr.length);
+        const unsigned long long d = pos_out - pos_in;
+        if (d) atomicAdd(m.decay + off[j], d);
+        pos_in = pos_out;
+      }
       if (axis == M) {
         if (mrem == 0) {
           done = true;
@@ -344,6 +386,21 @@ __device__ __forceinline__ void walk_segment(const DeviceMap& m, long long si) {
         }
       }
     }
+  }
+}
+
+// Miss-phase walk of one segment with the map's layers chosen at run time.
+__device__ __forceinline__ void walk_segment_any(const DeviceMap& m, long long si) {
+  const int sel = ((m.layers & kLayerOcc) ? 4 : 0) | ((m.layers & kLayerCounts) ? 2 : 0) | ((m.layers & kLayerDecay) ? 1 : 0);
+  switch (sel) {
+    case 7: walk_segment<true, true, true>(m, si); break;
+    case 6: walk_segment<true, true, false>(m, si); break;
+    case 5: walk_segment<true, false, true>(m, si); break;
+    case 4: walk_segment<true, false, false>(m, si); break;
+    case 3: walk_segment<false, true, true>(m, si); break;
+    case 2: walk_segment<false, true, false>(m, si); break;
+    case 1: walk_segment<false, false, true>(m, si); break;
+    default: break;
   }
 }
 

@@ -17,7 +17,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.environ.get("OHM_GB_LIB") or os.path.join(_HERE, "_lib", "libohm_gb.so")
 
 OK, ERR_INVALID, ERR_CAPACITY, ERR_CUDA, ERR_PROBE_LIMIT, ERR_UNSUPPORTED, ERR_EVICTED = range(7)
-LAYER_OCCUPANCY, LAYER_NDT, LAYER_TSDF, LAYER_COUNTS = 1, 2, 4, 8
+LAYER_OCCUPANCY, LAYER_NDT, LAYER_TSDF, LAYER_COUNTS, LAYER_DECAY = 1, 2, 4, 8, 16
+DECAY_UNITS = float(1 << 20)   # path_sum units per metre
 FLAG_NO_RETURN = 1
 REGION_VOXELS = 32768
 
@@ -113,11 +114,11 @@ def load_library(path: str = LIB_PATH):
     lib.ohm_map_sync.restype = st
     lib.ohm_map_sync.argtypes = [vp, vp]
     lib.ohm_query_voxels.restype = st
-    lib.ohm_query_voxels.argtypes = [vp, p, i64, p, p, p, p, p, vp]
+    lib.ohm_query_voxels.argtypes = [vp, p, i64, p, p, p, p, p, p, vp]
     lib.ohm_map_region_count.restype = st
     lib.ohm_map_region_count.argtypes = [vp, ctypes.POINTER(i64), vp]
     lib.ohm_map_export.restype = st
-    lib.ohm_map_export.argtypes = [vp, i64, i64, p, p, p, p, p, vp]
+    lib.ohm_map_export.argtypes = [vp, i64, i64, p, p, p, p, p, p, vp]
     lib.ohm_map_stats.restype = st
     lib.ohm_map_stats.argtypes = [vp, ctypes.POINTER(CallStats), vp]
     lib.ohm_map_profile.restype = st
@@ -303,8 +304,9 @@ class Map:
                                                 _stream_handle(stream)))
         return gd, gt
 
-    def query(self, points, stream=None, ndt=False, tsdf=False, counts=False):
-        """Look up world points; returns a dict of CUDA tensors."""
+    def query(self, points, stream=None, ndt=False, tsdf=False, counts=False, path_sum=False):
+        """Look up world points; returns a dict of CUDA tensors (path_sum:
+        int64 summed path length in 2^-20 m units, the decay layer)."""
         p = _as_points(points, "points")
         n = int(p.shape[0])
         dev = self.device
@@ -316,9 +318,11 @@ class Map:
             out["tsdf"] = torch.empty((n, 2), dtype=torch.float32, device=dev)
         if counts:
             out["counts"] = torch.empty((n, 2), dtype=torch.int32, device=dev)
+        if path_sum:
+            out["path_sum"] = torch.empty(n, dtype=torch.int64, device=dev)
         _check(load_library().ohm_query_voxels(self._h, _ptr(p), n, _ptr(out["occupancy"]), _ptr(out["known"]),
                                                _ptr(out.get("ndt")), _ptr(out.get("tsdf")), _ptr(out.get("counts")),
-                                               _stream_handle(stream)))
+                                               _ptr(out.get("path_sum")), _stream_handle(stream)))
         return out
 
     def evict(self, keep_regions: int, stream=None) -> int:
@@ -368,7 +372,8 @@ class Map:
         _check(load_library().ohm_map_profile_read(self._h, STAGES.index(stage), ctypes.byref(ms), ctypes.byref(n)))
         return float(ms.value), int(n.value)
 
-    def export(self, occupancy=True, counts=False, ndt=False, tsdf=False, first=0, count=None, stream=None):
+    def export(self, occupancy=True, counts=False, ndt=False, tsdf=False, path_sum=False, first=0, count=None,
+               stream=None):
         """Regions [first, first + count) in allocation order as CUDA tensors;
         voxels x fastest inside a region."""
         if count is None:
@@ -383,9 +388,11 @@ class Map:
             out["ndt"] = torch.empty((count, REGION_VOXELS, 10), dtype=torch.int64, device=dev)
         if tsdf:
             out["tsdf"] = torch.empty((count, REGION_VOXELS, 2), dtype=torch.float32, device=dev)
+        if path_sum:
+            out["path_sum"] = torch.empty((count, REGION_VOXELS), dtype=torch.int64, device=dev)
         _check(load_library().ohm_map_export(self._h, first, count, _ptr(out["keys"]), _ptr(out.get("occupancy")),
                                              _ptr(out.get("counts")), _ptr(out.get("ndt")), _ptr(out.get("tsdf")),
-                                             _stream_handle(stream)))
+                                             _ptr(out.get("path_sum")), _stream_handle(stream)))
         return out
 
 

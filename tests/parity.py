@@ -15,22 +15,25 @@ def gpu_region_order(gm: ohm.Map):
 
 
 def compare_dense(gm: ohm.Map, om: oracle.OracleMap, occupancy=True, counts=True, tsdf=False,
-                  tsdf_atol=1e-5, batch=1024):
+                  tsdf_atol=1e-5, batch=1024, path=False):
     """Region set equal; occupancy bit-exact; hit/miss counts exact; TSDF D
-    within tsdf_atol and W exact.  Returns the number of regions compared."""
+    within tsdf_atol and W exact; decay-rate path sums exact (both sides
+    round each visit's distance to 2^-20 m in float the same way).  Returns
+    the number of regions compared."""
     keys, order = gpu_region_order(gm)
     n = len(order)
     assert n == om.region_count(), (n, om.region_count())
     for i0 in range(0, n, batch):
         i1 = min(n, i0 + batch)
-        ref = om.export(first=i0, count=i1 - i0, occupancy=occupancy, counts=counts, ndt=False, tsdf=tsdf)
+        ref = om.export(first=i0, count=i1 - i0, occupancy=occupancy, counts=counts, ndt=False, tsdf=tsdf,
+                        path=path)
         assert np.array_equal(keys[order[i0:i1]], ref["keys"]), "region keys differ"
         slots = torch.from_numpy(order[i0:i1]).cuda()
         for s0 in range(0, i1 - i0, 256):
             sl = slots[s0:s0 + 256]
             # export contiguous GPU slots covering this batch, then gather
             lo, hi = int(sl.min()), int(sl.max()) + 1
-            ex = gm.export(occupancy=occupancy, counts=counts, tsdf=tsdf, first=lo, count=hi - lo)
+            ex = gm.export(occupancy=occupancy, counts=counts, tsdf=tsdf, path_sum=path, first=lo, count=hi - lo)
             idx = sl - lo
             r = slice(s0, s0 + len(sl))
             if occupancy:
@@ -43,6 +46,9 @@ def compare_dense(gm: ohm.Map, om: oracle.OracleMap, occupancy=True, counts=True
                 c = ex["counts"][idx].cpu().numpy().view(np.uint32)
                 assert np.array_equal(c[..., 0], ref["hits"][r]), "hit counts differ"
                 assert np.array_equal(c[..., 1], ref["misses"][r]), "miss counts differ"
+            if path:
+                ps = ex["path_sum"][idx].cpu().numpy().view(np.uint64)
+                assert np.array_equal(ps, ref["path"][r]), "decay path sums differ"
             if tsdf:
                 t = ex["tsdf"][idx].cpu().numpy().astype(np.float64)
                 assert np.array_equal(t[..., 1], ref["tsdf"][r][..., 1]), "TSDF weights differ"
@@ -85,9 +91,12 @@ def compare_ndt(gm: ohm.Map, om: oracle.OracleMap):
 
 
 def compare_query(gm: ohm.Map, om: oracle.OracleMap, pts: np.ndarray, ndt=False, tsdf=False, ndt_rtol=1e-4,
-                  tsdf_atol=1e-5):
-    g = gm.query(torch.from_numpy(np.ascontiguousarray(pts, dtype=np.float32)).cuda(), ndt=ndt, tsdf=tsdf)
+                  tsdf_atol=1e-5, path=False):
+    g = gm.query(torch.from_numpy(np.ascontiguousarray(pts, dtype=np.float32)).cuda(), ndt=ndt, tsdf=tsdf,
+                 path_sum=path)
     r = om.query(pts)
+    if path:
+        assert np.array_equal(g["path_sum"].cpu().numpy().view(np.uint64), r["path"]), "decay path sums differ"
     assert np.array_equal(g["known"].cpu().numpy(), r["known"]), "known flags differ"
     k = r["known"] == 1
     go = g["occupancy"].cpu().numpy()
@@ -113,7 +122,7 @@ def export_sorted(gm: ohm.Map):
     """Every layer of every region, regions sorted by key (CPU tensors)."""
     L = gm.params["layers"]
     ex = gm.export(occupancy=bool(L & ohm.LAYER_OCCUPANCY), counts=bool(L & ohm.LAYER_COUNTS),
-                   ndt=bool(L & ohm.LAYER_NDT), tsdf=bool(L & ohm.LAYER_TSDF))
+                   ndt=bool(L & ohm.LAYER_NDT), tsdf=bool(L & ohm.LAYER_TSDF), path_sum=bool(L & ohm.LAYER_DECAY))
     keys = ex["keys"].cpu().numpy()
     order = torch.from_numpy(np.lexsort((keys[:, 2], keys[:, 1], keys[:, 0]))).to(ex["keys"].device)
     out = {}

@@ -22,8 +22,9 @@ def _built():
 def _map_specs():
     return [
         W.tunnel_params(layers=W.OCC | W.NDT, max_rays=32768, max_regions=8192, max_ndt_regions=512, max_range=20.0),
-        W.tunnel_params(layers=W.OCC | W.COUNTS, voxel_size=0.05, max_rays=32768, max_regions=8192, max_range=20.0),
-        W.room_params(layers=W.OCC, max_rays=32768),
+        W.tunnel_params(layers=W.OCC | W.COUNTS | W.DECAY, voxel_size=0.05, max_rays=32768, max_regions=8192,
+                        max_range=20.0),
+        W.room_params(layers=W.DECAY, max_rays=32768),
         W.tsdf_params(layers=W.TSDF, max_rays=160 * 120),
         W.room_params(layers=W.OCC | W.COUNTS | W.NDT, max_rays=32768, voxel_size=0.05, max_regions=4096),
         W.tsdf_params(layers=W.TSDF | W.OCC, max_rays=160 * 120),

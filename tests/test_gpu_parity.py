@@ -182,7 +182,7 @@ def test_per_ray_origins_and_async_sync():
 
 
 def test_edge_cases():
-    p = W.room_params(layers=W.OCC | W.COUNTS | W.NDT, max_rays=64)
+    p = W.room_params(layers=W.OCC | W.COUNTS | W.NDT | W.DECAY, max_rays=64)
     gm, om = _pair(p)
     gm.integrate(np.zeros((1, 3), np.float32), np.zeros((0, 3), np.float32))  # empty ray set
     assert gm.region_count() == 0
@@ -196,13 +196,13 @@ def test_edge_cases():
                   [0.3, -0.3, 0.3]], np.float32)  # exact diagonal
     f = np.array([0, 0, 0, 0, 0, 0, 1], np.uint8)
     _integrate_both(gm, om, synth.RaySet(torch.from_numpy(o), torch.from_numpy(e), torch.from_numpy(f)))
-    compare_dense(gm, om)
+    compare_dense(gm, om, path=True)
     compare_ndt(gm, om)
     # all rays skipped
     bad = np.full((5, 3), np.inf, np.float32)
     gm.integrate(o, bad)
     om.integrate(o, bad)
-    compare_dense(gm, om)
+    compare_dense(gm, om, path=True)
     with pytest.raises(ohm.OhmError):
         gm.integrate(o, np.zeros((65, 3), np.float32))  # more than max_rays
 
@@ -252,3 +252,40 @@ def test_ndt_sample_clearing_matches_oracle(thr):
         _integrate_both(gm, om, rays)
     compare_dense(gm, om)
     compare_ndt(gm, om)
+
+
+@pytest.mark.parametrize("seed", [4, 5])
+def test_decay_layer_matches_oracle(seed):
+    """Decay rate (Sec. II-E): per-voxel summed path lengths bit-exact, with
+    occupancy and counts (H_i) in the same map."""
+    p = W.room_params(layers=W.OCC | W.COUNTS | W.DECAY, max_regions=4096, max_rays=4096, max_range=2.5)
+    gm, om = _pair(p)
+    for scan in range(3):
+        rays = synth.fuzz_rays(seed * 100 + scan, 3000)
+        _integrate_both(gm, om, rays)
+    compare_dense(gm, om, path=True)
+    compare_query(gm, om, _sample_points(rays), path=True)
+
+
+@pytest.mark.parametrize("steps", [1, 3, 100000])
+def test_decay_layer_segment_splits(steps):
+    """A segment that starts mid-ray takes its entry distance from the
+    dominant axis' crossing: every split gives the unsplit sums."""
+    p = W.tunnel_params(layers=W.DECAY | W.COUNTS, segment_steps=steps, max_rays=16384, max_regions=16384)
+    gm, om = _pair(p)
+    for i in range(2):
+        rays = synth.tunnel_scan(i + 20, beams=16, azimuths=1024)
+        _integrate_both(gm, om, rays)
+    compare_dense(gm, om, occupancy=False, path=True)
+
+
+def test_decay_layer_tunnel_full_size():
+    """The tunnel workload (131,072 rays, 50 m truncation) with the decay
+    layer: sampled voxels through query, every ray's total via the export."""
+    p = W.tunnel_params(layers=W.OCC | W.NDT | W.COUNTS | W.DECAY)
+    gm, om = _pair(p)
+    rays = W.tunnel_rays(30)
+    _integrate_both(gm, om, rays)
+    compare_query(gm, om, _sample_points(rays, k=50000), ndt=True, path=True)
+    compare_dense(gm, om, batch=512, path=True)
+
