@@ -56,9 +56,12 @@ enum {
   OHM_LAYER_NDT = 2,       /* int64 sample moments per voxel (Sec. II-D, III-C) */
   OHM_LAYER_TSDF = 4,      /* float signed distance + weight per voxel (Sec. II-F) */
   OHM_LAYER_COUNTS = 8,    /* uint32 hits H_i and misses M_i per voxel (Sec. II-D) */
-  OHM_LAYER_DECAY = 16     /* decay-rate map (Sec. II-E): per voxel the summed length of the rays'
+  OHM_LAYER_DECAY = 16,    /* decay-rate map (Sec. II-E): per voxel the summed length of the rays'
                               paths through it, uint64 in units of 2^-20 m; with OHM_LAYER_COUNTS
                               the reflection rate is lambda = H / sum d */
+  OHM_LAYER_MEAN = 32      /* voxel mean (Sec. III-C): per voxel a uint64 word, sample count n in
+                              the high 32 bits, the mean sample position inside the voxel in the
+                              low 30 (10 bits per axis, x lowest, in 1/1024 of the voxel) */
 };
 
 /* Per-ray flag bits. */
@@ -107,10 +110,19 @@ void ohm_map_destroy(ohm_map* map);
 
 /* Integrate one ray set (Sec. III-B; one call is one "scan").
  * Decay layer: every voxel the walk visits gains the length of the ray inside
- * it, (t_out - t_in) L with L the ray length in metres (float) and t_in, t_out
- * the ray parameters where the walk enters and leaves it (0 at the start, 1 at
- * the end point; a crossing of axis k at t = dist_k / A_k, evaluated in float
- * with one rounding per operation), rounded to 2^-20 m.
+ * it, P(t_out) - P(t_in): t_in, t_out are the ray parameters where the walk
+ * enters and leaves it (0 at the start, 1 at the end point; a crossing of axis
+ * k at t = dist_k / A_k with dist_k the fixed-point distance from the start to
+ * the crossed boundary along k and A_k = |b_k - a_k|), kept as
+ * floor(2^32 t) / 2^32, and P(t) = rint(t L) with L = rint(|b - a| voxel_size
+ * 2^(20 - F)) the walked length in 2^-20 m (double).  Each ray adds exactly L
+ * over the voxels it visits.
+ * Mean layer: a sample's position inside its voxel is quantised to 10 bits
+ * per axis (p = floor(offset * 1024 / 2^F)); per call, with c samples of sum
+ * S in a voxel holding count n and mean m, every axis takes
+ * m <- floor((m n + S + floor((n + c) / 2)) / (n + c)) and n <- min(n + c,
+ * 2^32 - 1), so the result does not depend on the order of the samples.
+ * Requires max_rays <= 2^22.
  *   origins    n_origins x 3 float world positions, x y z interleaved;
  *              n_origins is 1 (a shared sensor origin) or n.
  *   endpoints  n x 3 float world positions of the samples.
@@ -179,9 +191,15 @@ ohm_status ohm_map_residency(ohm_map* map, int64_t* resident, int64_t* evicted, 
  *   tsdf       n x 2 floats: D, W (zeros if unobserved)
  *   counts     n x 2 uint32: hits H, misses M
  *   path_sum   n uint64: summed ray path length through the voxel, 2^-20 m units
- * `points` may be host or device memory.  Returns once enqueued. */
+ *   mean       n x 4 floats: voxel-mean position x y z (metres, world: the
+ *              voxel's lower corner + (m + 0.5) / 1024 voxels) and the sample
+ *              count; NaN position and count 0 without samples
+ * A non-NULL buffer for a layer the map lacks is OHM_ERR_UNSUPPORTED
+ * (path_sum, mean).  `points` may be host or device memory.  Returns once
+ * enqueued. */
 ohm_status ohm_query_voxels(ohm_map* map, const float* points, int64_t n, float* occupancy, uint8_t* known,
-                            float* ndt, float* tsdf, uint32_t* counts, uint64_t* path_sum, void* stream);
+                            float* ndt, float* tsdf, uint32_t* counts, uint64_t* path_sum, float* mean,
+                            void* stream);
 
 /* Number of pool slots ever used by the map, resident or released by eviction
  * (synchronises `stream`).  Without evictions: the number of regions. */
@@ -197,10 +215,12 @@ ohm_status ohm_map_region_count(ohm_map* map, int64_t* out, void* stream);
  *              voxel's lower corner
  *   tsdf       count x 32768 x 2 float (D, W)
  *   path_sum   count x 32768 uint64 summed path length, 2^-20 m units
+ *   mean       count x 32768 uint64 voxel-mean words (see OHM_LAYER_MEAN)
  * A non-NULL buffer for a layer the map lacks is OHM_ERR_UNSUPPORTED.
  * Returns once enqueued. */
 ohm_status ohm_map_export(ohm_map* map, int64_t first, int64_t count, int32_t* keys, float* occupancy,
-                          uint32_t* counts, int64_t* ndt, float* tsdf, uint64_t* path_sum, void* stream);
+                          uint32_t* counts, int64_t* ndt, float* tsdf, uint64_t* path_sum, uint64_t* mean,
+                          void* stream);
 
 typedef struct {
   int64_t rays;          /* rays passed to the last integrate call */
@@ -227,7 +247,8 @@ typedef enum {
   OHM_STAGE_TSDF_WALK = 6,    /* TSDF band walk */
   OHM_STAGE_TSDF_APPLY = 7,   /* TSDF weighted average */
   OHM_STAGE_END = 8,          /* rollback of a failed call */
-  OHM_STAGE_COUNT = 9
+  OHM_STAGE_MEAN_APPLY = 9,   /* voxel-mean per-call update */
+  OHM_STAGE_COUNT = 10
 } ohm_stage;
 
 /* Record CUDA events around the kernels of the stages whose bit (1 << stage)

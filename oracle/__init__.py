@@ -22,6 +22,7 @@ LAYER_NDT = 2
 LAYER_TSDF = 4
 LAYER_COUNTS = 8
 LAYER_DECAY = 16
+LAYER_MEAN = 32
 PATH_UNITS_PER_METRE = float(1 << 20)
 
 FLAG_NO_RETURN = 1
@@ -61,12 +62,12 @@ def _load():
         lib.oracle_region_count.restype = i64
         lib.oracle_region_count.argtypes = [vp]
         lib.oracle_export.restype = ctypes.c_int
-        lib.oracle_export.argtypes = [vp, i64, i64, p, p, p, p, p, p, p]
+        lib.oracle_export.argtypes = [vp, i64, i64, p, p, p, p, p, p, p, p]
         lib.oracle_ndt_region_count.restype = i64
         lib.oracle_ndt_region_count.argtypes = [vp]
         lib.oracle_ndt_sparse.restype = i64
         lib.oracle_ndt_sparse.argtypes = [vp, i64, p, p]
-        lib.oracle_query.argtypes = [vp, p, i64, p, p, p, p, p]
+        lib.oracle_query.argtypes = [vp, p, i64, p, p, p, p, p, p]
         lib.oracle_walk.restype = i64
         lib.oracle_walk.argtypes = [p, p, ctypes.c_int32, p, i64]
         lib.oracle_walk_timed.restype = i64
@@ -139,7 +140,7 @@ class OracleMap:
     def ndt_region_count(self) -> int:
         return int(_load().oracle_ndt_region_count(self._h))
 
-    def export(self, first=0, count=None, occupancy=True, counts=True, ndt=True, tsdf=True, path=True):
+    def export(self, first=0, count=None, occupancy=True, counts=True, ndt=True, tsdf=True, path=True, mean=True):
         """Regions [first, first + count) in (rx, ry, rz) order: a dict of numpy
         arrays (a layer the map lacks, or one not asked for, is None)."""
         total = self.region_count()
@@ -154,11 +155,12 @@ class OracleMap:
         nd = np.zeros((n, REGION_VOXELS, 10), np.int64) if (L & LAYER_NDT and ndt) else None
         ts = np.zeros((n, REGION_VOXELS, 2), np.float64) if (L & LAYER_TSDF and tsdf) else None
         ps = np.zeros((n, REGION_VOXELS), np.uint64) if (L & LAYER_DECAY and path) else None
+        mn = np.zeros((n, REGION_VOXELS, 4), np.uint32) if (L & LAYER_MEAN and mean) else None
         rc = _load().oracle_export(self._h, first, n, _ptr(keys), _ptr(occ), _ptr(hits), _ptr(misses), _ptr(nd),
-                                   _ptr(ts), _ptr(ps))
+                                   _ptr(ts), _ptr(ps), _ptr(mn))
         if rc:
             raise OverflowError("NDT moment sum exceeds int64")
-        return dict(keys=keys, occupancy=occ, hits=hits, misses=misses, ndt=nd, tsdf=ts, path=ps)
+        return dict(keys=keys, occupancy=occ, hits=hits, misses=misses, ndt=nd, tsdf=ts, path=ps, mean=mn)
 
     def ndt_sparse(self):
         """(voxels (k, 3) int64, moments (k, 10) int64) of every voxel holding
@@ -178,8 +180,10 @@ class OracleMap:
         ndt = np.zeros((n, 10), np.float64)
         tsdf = np.zeros((n, 2), np.float64)
         path = np.zeros(n, np.uint64)
-        _load().oracle_query(self._h, _ptr(pts), n, _ptr(occ), _ptr(known), _ptr(ndt), _ptr(tsdf), _ptr(path))
-        return dict(occupancy=occ, known=known, ndt=ndt, tsdf=tsdf, path=path)
+        mean = np.zeros((n, 4), np.float64)
+        _load().oracle_query(self._h, _ptr(pts), n, _ptr(occ), _ptr(known), _ptr(ndt), _ptr(tsdf), _ptr(path),
+                             _ptr(mean))
+        return dict(occupancy=occ, known=known, ndt=ndt, tsdf=tsdf, path=path, mean=mean)
 
     def prepare(self, origins, endpoints, flags=None):
         o = np.ascontiguousarray(origins, dtype=np.float32).reshape(-1, 3)

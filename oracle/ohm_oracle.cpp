@@ -40,6 +40,14 @@
 //     the ray P(t) = rint(t L); d = P(t_out) - P(t_in).  P is monotone, so
 //     no d is negative, the d of one ray add up to exactly L, and the sums
 //     do not depend on the order of the rays.
+//   * Voxel mean (Sec. III-C): per voxel a sample count n and the mean sample
+//     position inside the voxel, 10 bits per axis packed in 32 bits (the
+//     paper's footnote).  A sample's position is quantised down to 1/1024 of
+//     the voxel.  Reading (the paper updates the mean per sample by CAS, whose
+//     rounding depends on thread order): per call, with c samples of summed
+//     positions S in the voxel, m <- round-half-up((m n + S) / (n + c)),
+//     n <- n + c (saturating at 2^32 - 1), the running mean taken one call at
+//     a time like the TSDF average below.
 //   * TSDF: projective signed distance s = d - (c - o).u along the ray,
 //     truncated to [-tau, tau], for the voxels the walk visits between ranges
 //     max(0, d - tau) and d + tau; per call the voxel keeps the running
@@ -48,6 +56,7 @@
 //
 // Build: g++ -std=c++17 -O2 -ffp-contract=off -fPIC -shared (oracle/build.py).
 
+#include <array>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -66,6 +75,7 @@ constexpr int kLayerNdt = 2;
 constexpr int kLayerTsdf = 4;
 constexpr int kLayerCounts = 8;
 constexpr int kLayerDecay = 16;
+constexpr int kLayerMean = 32;
 
 constexpr double kPathUnitsPerMetre = 1048576.0;  // 2^20
 
@@ -122,6 +132,8 @@ struct Region {
   std::vector<double> tsdf_d;       // running signed distance
   std::vector<double> tsdf_w;       // running weight
   std::vector<uint64_t> path;       // decay rate: sum_j d_i(j) in 2^-20 m
+  std::vector<uint32_t> mean_n;     // voxel mean: sample count
+  std::vector<uint32_t> mean_m;     // voxel mean: 3 per voxel, position in 1/1024 voxel
 };
 
 struct Map {
@@ -160,6 +172,10 @@ Region& region_for(Map& m, const Voxel& v) {
     r.tsdf_w.assign(kRegionVoxels, 0.0);
   }
   if (L & kLayerDecay) r.path.assign(kRegionVoxels, 0ull);
+  if (L & kLayerMean) {
+    r.mean_n.assign(kRegionVoxels, 0u);
+    r.mean_m.assign((size_t)kRegionVoxels * 3, 0u);
+  }
   return m.regions.emplace(k, std::move(r)).first->second;
 }
 
@@ -469,7 +485,7 @@ int64_t oracle_integrate(void* h, const float* origins, int64_t n_origins, const
     if (prepare_ray(m, o, endpoints + 3 * i, flags ? flags[i] : 0, &r)) rays.push_back(r);
   }
   int64_t visits = 0;
-  const int occ_like = kLayerOccupancy | kLayerCounts | kLayerNdt | kLayerDecay;
+  const int occ_like = kLayerOccupancy | kLayerCounts | kLayerNdt | kLayerDecay | kLayerMean;
   if (m.p.layers & occ_like) {
     // Phase 1: every pass-through (miss) of every ray.
     for (const PreparedRay& r : rays) {
@@ -484,9 +500,30 @@ int64_t oracle_integrate(void* h, const float* origins, int64_t n_origins, const
       }
     }
     // Phase 2: every sample (hit).
+    std::map<std::tuple<int64_t, int64_t, int64_t>, std::array<uint64_t, 4>> mean_acc;  // c, Sx, Sy, Sz
     for (const PreparedRay& r : rays) {
       if (!r.has_sample) continue;
-      apply_hit(m, voxel_of(r.qe, m.unit), r.qe);
+      const Voxel v = voxel_of(r.qe, m.unit);
+      apply_hit(m, v, r.qe);
+      if (m.p.layers & kLayerMean) {
+        auto& acc = mean_acc[std::make_tuple(v.v[0], v.v[1], v.v[2])];
+        acc[0] += 1;
+        for (int a = 0; a < 3; ++a) acc[1 + a] += (uint64_t)(((r.qe[a] - v.v[a] * m.unit) * 1024) / m.unit);
+      }
+    }
+    for (const auto& kv : mean_acc) {
+      Voxel v;
+      v.v[0] = std::get<0>(kv.first);
+      v.v[1] = std::get<1>(kv.first);
+      v.v[2] = std::get<2>(kv.first);
+      Region& reg = region_for(m, v);
+      const int i = local_index(v);
+      const uint64_t n = reg.mean_n[i], c = kv.second[0], total = n + c;
+      for (int a = 0; a < 3; ++a) {
+        const uint64_t num = (uint64_t)reg.mean_m[(size_t)i * 3 + a] * n + kv.second[1 + a];
+        reg.mean_m[(size_t)i * 3 + a] = (uint32_t)((2 * num + total) / (2 * total));  // round half up
+      }
+      reg.mean_n[i] = (uint32_t)(total < 0xffffffffull ? total : 0xffffffffull);
     }
   }
   if (m.p.layers & kLayerTsdf) {
@@ -521,11 +558,12 @@ int64_t oracle_region_count(void* h) { return (int64_t)static_cast<Map*>(h)->reg
 // Any output pointer may be null.  Per region: keys 3 x int64; occupancy 32768
 // float; hits, misses 32768 uint32; ndt 32768 x 10 int64 (n, Sx, Sy, Sz, Sxx,
 // Sxy, Sxz, Syy, Syz, Szz; zeros for a region without samples); tsdf 32768 x 2
-// double (D, W); path 32768 uint64 (decay rate: summed distance, 2^-20 m).
+// double (D, W); path 32768 uint64 (decay rate: summed distance, 2^-20 m);
+// mean 32768 x 4 uint32 (voxel mean: count, mx, my, mz in 1/1024 voxel).
 // Voxel order inside a region: x fastest.  Returns 0, or 1 if an NDT sum does
 // not fit in int64.
 int oracle_export(void* h, int64_t first, int64_t count, int64_t* keys, float* occupancy, uint32_t* hits,
-                  uint32_t* misses, int64_t* ndt, double* tsdf, uint64_t* path) {
+                  uint32_t* misses, int64_t* ndt, double* tsdf, uint64_t* path, uint32_t* mean) {
   Map& m = *static_cast<Map*>(h);
   int rc = 0;
   int64_t pos = 0;
@@ -560,6 +598,13 @@ int oracle_export(void* h, int64_t first, int64_t count, int64_t* keys, float* o
       }
     }
     if (path && !r.path.empty()) std::memcpy(path + idx * kRegionVoxels, r.path.data(), sizeof(uint64_t) * kRegionVoxels);
+    if (mean && !r.mean_n.empty()) {
+      for (int j = 0; j < kRegionVoxels; ++j) {
+        uint32_t* o = mean + (idx * kRegionVoxels + j) * 4;
+        o[0] = r.mean_n[j];
+        for (int a = 0; a < 3; ++a) o[1 + a] = r.mean_m[(size_t)j * 3 + a];
+      }
+    }
     ++idx;
   }
   return rc;
@@ -600,7 +645,7 @@ int64_t oracle_ndt_region_count(void* h) {
 // (count, mean xyz in metres, covariance xx xy xz yy yz zz in m^2; zeros if no
 // sample); tsdf: n x 2 (D, W).  Any output may be null.
 void oracle_query(void* h, const float* pts, int64_t n, float* occupancy, uint8_t* known, double* ndt,
-                  double* tsdf, uint64_t* path) {
+                  double* tsdf, uint64_t* path, double* mean) {
   Map& m = *static_cast<Map*>(h);
   const double cell = m.p.voxel_size / (double)m.unit;  // metres per fixed-point unit
   for (int64_t i = 0; i < n; ++i) {
@@ -636,6 +681,15 @@ void oracle_query(void* h, const float* pts, int64_t n, float* occupancy, uint8_
       tsdf[2 * i + 1] = (r && !r->tsdf_w.empty()) ? r->tsdf_w[li] : 0.0;
     }
     if (path) path[i] = (r && !r->path.empty()) ? r->path[li] : 0ull;
+    if (mean) {
+      // voxel-mean position: lower corner + (m + 1/2) / 1024 of the voxel; NaN without samples
+      const uint32_t cnt = (r && !r->mean_n.empty()) ? r->mean_n[li] : 0u;
+      for (int a = 0; a < 3; ++a)
+        mean[4 * i + a] = cnt ? m.p.map_origin[a] +
+                                    ((double)v.v[a] + ((double)r->mean_m[(size_t)li * 3 + a] + 0.5) / 1024.0) * m.p.voxel_size
+                              : std::nan("");
+      mean[4 * i + 3] = (double)cnt;
+    }
   }
 }
 

@@ -45,7 +45,7 @@ struct BatchShared {
   int32_t n_maps;
 };
 
-enum PrefixKind { kRaysPadded, kRays, kSegments, kTouched };
+enum PrefixKind { kRaysPadded, kRays, kSegments, kTouched, kMeanTouched };
 
 // Load the descriptors and build the prefix table of the requested kind.
 __device__ void batch_stage(BatchShared& sh, const BatchDesc* desc, const BatchStep* step, PrefixKind kind) {
@@ -68,6 +68,8 @@ __device__ void batch_stage(BatchShared& sh, const BatchDesc* desc, const BatchS
         c = live ? step->n[i] : 0;
       else if (kind == kSegments)
         c = live ? (long long)m.calls->segments : 0;
+      else if (kind == kMeanTouched)
+        c = (m.layers & kLayerMean) ? mean_touched_count(m) : 0;  // failed maps too: their sums are cleared
       else
         c = live ? touched_count(m) : 0;
       acc += c;
@@ -113,7 +115,7 @@ __global__ void __launch_bounds__(kBlock) k_batch_prepare(const BatchDesc* desc,
     const bool active = i < a.n;
     if (tsdf) {
       if (m.layers & kLayerTsdf) prepare_tsdf_ray(m, a, i, active);
-    } else if (m.layers & (kLayerOcc | kLayerCounts | kLayerNdt | kLayerDecay)) {
+    } else if (m.layers & (kLayerOcc | kLayerCounts | kLayerNdt | kLayerDecay | kLayerMean)) {
       prepare_occ_ray(m, a, i, active);
     }
   }
@@ -159,8 +161,21 @@ __global__ void __launch_bounds__(kBlock) k_batch_hits(const BatchDesc* desc, co
       case 3: hit_ray<false, true, true>(m, i); break;
       case 2: hit_ray<false, true, false>(m, i); break;
       case 1: hit_ray<false, false, true>(m, i); break;
-      default: break;
+      default:
+        if (m.layers & kLayerMean) hit_ray<false, false, false>(m, i);
+        break;
     }
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_batch_mean_apply(const BatchDesc* desc, const BatchStep* step) {
+  __shared__ BatchShared sh;
+  batch_stage(sh, desc, step, kMeanTouched);
+  const long long total = sh.pref[sh.n_maps];
+  OHM_BATCH_STRIDE(g, total) {
+    const int mi = batch_find(sh, g);
+    const DeviceMap& m = sh.maps[mi];
+    mean_apply_one(m, g - sh.pref[mi], !latched(m));
   }
 }
 
@@ -212,7 +227,7 @@ struct ohm_batch {
   cudaGraph_t graph;
   cudaGraphExec_t exec;
   bool have_exec;
-  bool any_ndt, any_tsdf, any_occ;
+  bool any_ndt, any_tsdf, any_occ, any_mean;
   long long launches;
   long long graph_launches;
   int graph_kernels;           // kernel nodes in the captured step
@@ -249,7 +264,7 @@ cudaError_t enqueue_step(ohm_batch* b, cudaStream_t s, int* count) {
   const int ray_grid = b->num_sms * 4;
   k_batch_begin<<<1, kMaxBatchMaps, 0, s>>>(b->d_desc, b->d_step);
   int n = 1;
-  if (b->any_occ || b->any_ndt) {
+  if (b->any_occ || b->any_ndt || b->any_mean) {
     k_batch_prepare<<<ray_grid, kBlock, 0, s>>>(b->d_desc, b->d_step, 0);
     ++n;
     if (b->any_ndt) {
@@ -265,8 +280,12 @@ cudaError_t enqueue_step(ohm_batch* b, cudaStream_t s, int* count) {
     k_batch_walk<<<grid, kBlock, 0, s>>>(b->d_desc, b->d_step);
     ++n;
   }
-  if (b->any_occ || b->any_ndt) {
+  if (b->any_occ || b->any_ndt || b->any_mean) {
     k_batch_hits<<<ray_grid, kBlock, 0, s>>>(b->d_desc, b->d_step);
+    ++n;
+  }
+  if (b->any_mean) {
+    k_batch_mean_apply<<<ray_grid, kBlock, 0, s>>>(b->d_desc, b->d_step);
     ++n;
   }
   if (b->any_tsdf) {
@@ -317,6 +336,7 @@ ohm_status ohm_batch_create(ohm_map* const* maps, int32_t n_maps, ohm_batch** ou
     b->any_occ = b->any_occ || (L & (OHM_LAYER_OCCUPANCY | OHM_LAYER_COUNTS | OHM_LAYER_DECAY));
     b->any_ndt = b->any_ndt || (L & OHM_LAYER_NDT);
     b->any_tsdf = b->any_tsdf || (L & OHM_LAYER_TSDF);
+    b->any_mean = b->any_mean || (L & OHM_LAYER_MEAN);
   }
   b->walk_blocks_per_sm = ohm::walk_blocks_per_sm();
   cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);

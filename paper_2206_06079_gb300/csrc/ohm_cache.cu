@@ -55,6 +55,7 @@ struct HostRegion {
   void* occ = nullptr;
   void* counts = nullptr;
   void* decay = nullptr;
+  void* vmean = nullptr;
   void* ndt = nullptr;
   void* tsdf = nullptr;
 };
@@ -63,6 +64,7 @@ struct HostStore {
   PinnedSlab occ{sizeof(float) * kRegionVoxels};
   PinnedSlab counts{sizeof(unsigned long long) * kRegionVoxels};
   PinnedSlab decay{sizeof(unsigned long long) * kRegionVoxels};
+  PinnedSlab vmean{sizeof(unsigned long long) * kRegionVoxels};
   PinnedSlab ndt{sizeof(long long) * 10 * kRegionVoxels};
   PinnedSlab tsdf{sizeof(float2) * kRegionVoxels};
   std::unordered_map<long long, HostRegion> regions;
@@ -125,6 +127,7 @@ __global__ void k_reset_slots(DeviceMap m, const int32_t* slots, int n, const in
       if (m.occ) reinterpret_cast<unsigned int*>(m.occ)[off] = 0xFFFFFFFFu;
       if (m.counts) m.counts[off] = 0ULL;
       if (m.decay) m.decay[off] = 0ULL;
+      if (m.vmean) m.vmean[off] = 0ULL;
       if (m.tsdf) m.tsdf[off] = make_float2(0.f, 0.f);
       if (v == 0) m.ndt_slot[slots[r]] = -1;
     } else {
@@ -252,6 +255,11 @@ cudaError_t cache_evict(ohm_map* m, long long target, long long* evicted) {
       if (!r.decay) return cudaErrorMemoryAllocation;
       e = cudaMemcpyAsync(r.decay, d.decay + off, sizeof(unsigned long long) * kRegionVoxels, cudaMemcpyDeviceToHost, 0);
     }
+    if (e == cudaSuccess && d.vmean) {
+      r.vmean = hs->vmean.get();
+      if (!r.vmean) return cudaErrorMemoryAllocation;
+      e = cudaMemcpyAsync(r.vmean, d.vmean + off, sizeof(unsigned long long) * kRegionVoxels, cudaMemcpyDeviceToHost, 0);
+    }
     if (e == cudaSuccess && d.tsdf) {
       r.tsdf = hs->tsdf.get();
       if (!r.tsdf) return cudaErrorMemoryAllocation;
@@ -346,6 +354,8 @@ cudaError_t cache_restore(ohm_map* m, const std::vector<long long>& want, long l
       e = cudaMemcpyAsync(d.tsdf + off, r.tsdf, sizeof(float2) * kRegionVoxels, cudaMemcpyHostToDevice, 0);
     if (e == cudaSuccess && r.decay)
       e = cudaMemcpyAsync(d.decay + off, r.decay, sizeof(unsigned long long) * kRegionVoxels, cudaMemcpyHostToDevice, 0);
+    if (e == cudaSuccess && r.vmean)
+      e = cudaMemcpyAsync(d.vmean + off, r.vmean, sizeof(unsigned long long) * kRegionVoxels, cudaMemcpyHostToDevice, 0);
     if (e == cudaSuccess && r.ndt)
       e = cudaMemcpyAsync(d.ndt + (long long)nb * 10 * kRegionVoxels, r.ndt, sizeof(long long) * 10 * kRegionVoxels,
                           cudaMemcpyHostToDevice, 0);
@@ -371,6 +381,7 @@ cudaError_t cache_restore(ohm_map* m, const std::vector<long long>& want, long l
     hs->occ.put(r.occ);
     hs->counts.put(r.counts);
     hs->decay.put(r.decay);
+    hs->vmean.put(r.vmean);
     hs->ndt.put(r.ndt);
     hs->tsdf.put(r.tsdf);
     hs->regions.erase(k);

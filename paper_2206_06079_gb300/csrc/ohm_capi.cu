@@ -62,7 +62,7 @@ long long next_pow2(long long x) {
 void free_map(ohm_map* m) {
   if (!m) return;
   ohm::DeviceMap& d = m->d;
-  void* ptrs[] = {d.htab, d.region_count, d.region_coords, d.occ, d.counts, d.decay, d.ndt_slot, d.ndt_count,
+  void* ptrs[] = {d.htab, d.region_count, d.region_coords, d.occ, d.counts, d.decay, d.vmean, d.vmean_acc, d.mean_list, d.ndt_slot, d.ndt_count,
                   d.ndt, d.tsdf, d.tsdf_cnt, d.tsdf_sum, d.grad, d.status, d.calls, d.rays, d.decay_rays, d.trays, d.segs, d.touched,
                   d.stamp, d.born, d.ndt_born, d.free_slots, d.ndt_free, d.free_info, d.restore_keys,
                   m->stage_origins, m->stage_endpoints, m->stage_flags};
@@ -143,7 +143,7 @@ ohm_status ohm_map_create(const ohm_map_params* params, ohm_map** out) {
   if (p.segment_steps == 0) p.segment_steps = 4;
   if (!(p.voxel_size > 0.0) || !std::isfinite(p.voxel_size)) return fail(OHM_ERR_INVALID, "create: voxel_size must be > 0");
   if (p.frac_bits < 8 || p.frac_bits > 20) return fail(OHM_ERR_INVALID, "create: frac_bits must be in [8, 20]");
-  const uint32_t all = OHM_LAYER_OCCUPANCY | OHM_LAYER_NDT | OHM_LAYER_TSDF | OHM_LAYER_COUNTS | OHM_LAYER_DECAY;
+  const uint32_t all = OHM_LAYER_OCCUPANCY | OHM_LAYER_NDT | OHM_LAYER_TSDF | OHM_LAYER_COUNTS | OHM_LAYER_DECAY | OHM_LAYER_MEAN;
   if (p.layers == 0 || (p.layers & ~all)) return fail(OHM_ERR_INVALID, "create: bad layer mask");
   if (!(p.l_min <= p.l_max)) return fail(OHM_ERR_INVALID, "create: l_min > l_max");
   if (std::isnan(p.ndt_clear_below)) return fail(OHM_ERR_INVALID, "create: ndt_clear_below is NaN");
@@ -153,6 +153,8 @@ ohm_status ohm_map_create(const ohm_map_params* params, ohm_map** out) {
   if (p.max_regions < 1 || p.max_regions > (1LL << 16)) return fail(OHM_ERR_INVALID, "create: max_regions must be in [1, 65536]");
   if (p.max_rays < 1 || p.max_rays > (1LL << 30)) return fail(OHM_ERR_INVALID, "create: max_rays out of range");
   if (p.segment_steps < 1) return fail(OHM_ERR_INVALID, "create: segment_steps must be >= 1");
+  if ((p.layers & OHM_LAYER_MEAN) && p.max_rays > (1LL << 22))
+    return fail(OHM_ERR_INVALID, "create: the mean layer needs max_rays <= 2^22 (per-call 32-bit sums)");
   if ((p.layers & OHM_LAYER_NDT) && (p.max_ndt_regions < 1 || p.max_ndt_regions > p.max_regions))
     return fail(OHM_ERR_INVALID, "create: max_ndt_regions must be in [1, max_regions]");
   for (int k = 0; k < 3; ++k)
@@ -202,6 +204,10 @@ ohm_status ohm_map_create(const ohm_map_params* params, ohm_map** out) {
   if (p.layers & OHM_LAYER_OCCUPANCY) chk(alloc(&d.occ, R * V, 0xFF));  // all-ones float = NaN = unknown
   if (p.layers & OHM_LAYER_COUNTS) chk(alloc(&d.counts, R * V, 0));
   if (p.layers & OHM_LAYER_DECAY) chk(alloc(&d.decay, R * V, 0));
+  if (p.layers & OHM_LAYER_MEAN) {
+    chk(alloc(&d.vmean, R * V, 0));
+    chk(alloc(&d.vmean_acc, 2 * R * V, 0));
+  }
   if (p.layers & OHM_LAYER_NDT) {
     chk(alloc(&d.ndt, (long long)d.max_ndt * 10 * V, 0));
     chk(alloc(&d.ndt_free, d.max_ndt, 0));
@@ -215,6 +221,7 @@ ohm_status ohm_map_create(const ohm_map_params* params, ohm_map** out) {
   }
   chk(alloc(&d.rays, p.max_rays, 0));
   if (p.layers & OHM_LAYER_DECAY) chk(alloc(&d.decay_rays, p.max_rays, 0));
+  if (p.layers & OHM_LAYER_MEAN) chk(alloc(&d.mean_list, p.max_rays, 0));
   chk(alloc(&d.segs, d.max_segs, 0));
   chk(alloc(&m->stage_origins, 3 * p.max_rays, 0));
   chk(alloc(&m->stage_endpoints, 3 * p.max_rays, 0));
@@ -364,15 +371,17 @@ ohm_status ohm_map_residency(ohm_map* map, int64_t* resident, int64_t* evicted, 
 }
 
 ohm_status ohm_query_voxels(ohm_map* map, const float* points, int64_t n, float* occupancy, uint8_t* known,
-                            float* ndt, float* tsdf, uint32_t* counts, uint64_t* path_sum, void* stream) {
+                            float* ndt, float* tsdf, uint32_t* counts, uint64_t* path_sum, float* mean,
+                            void* stream) {
   if (!map) return fail(OHM_ERR_INVALID, "query: map is NULL");
   if (n < 0) return fail(OHM_ERR_INVALID, "query: n < 0");
   if (n == 0) return OHM_OK;
   if (!points) return fail(OHM_ERR_INVALID, "query: points is NULL");
-  void* outs[] = {occupancy, known, ndt, tsdf, counts, path_sum};
+  void* outs[] = {occupancy, known, ndt, tsdf, counts, path_sum, mean};
   for (void* o : outs)
     if (o && !is_device_pointer(o)) return fail(OHM_ERR_INVALID, "query: outputs must be device memory");
   if (path_sum && !(map->p.layers & OHM_LAYER_DECAY)) return fail(OHM_ERR_UNSUPPORTED, "query: map has no decay layer");
+  if (mean && !(map->p.layers & OHM_LAYER_MEAN)) return fail(OHM_ERR_UNSUPPORTED, "query: map has no mean layer");
   if (ndt && !(map->p.layers & OHM_LAYER_NDT)) return fail(OHM_ERR_UNSUPPORTED, "query: map has no NDT layer");
   if (tsdf && !(map->p.layers & OHM_LAYER_TSDF)) return fail(OHM_ERR_UNSUPPORTED, "query: map has no TSDF layer");
   DeviceGuard guard(map->device);
@@ -388,7 +397,7 @@ ohm_status ohm_query_voxels(ohm_map* map, const float* points, int64_t n, float*
     pts = staged;
   }
   e = ohm::launch_query(map, pts, n, occupancy, known, ndt, tsdf, counts,
-                        reinterpret_cast<unsigned long long*>(path_sum), s);
+                        reinterpret_cast<unsigned long long*>(path_sum), mean, s);
   if (staged) cudaFreeAsync(staged, s);
   if (e != cudaSuccess) return cuda_fail(e, "query: launch");
   return OHM_OK;
@@ -407,14 +416,16 @@ ohm_status ohm_map_region_count(ohm_map* map, int64_t* out, void* stream) {
 }
 
 ohm_status ohm_map_export(ohm_map* map, int64_t first, int64_t count, int32_t* keys, float* occupancy,
-                          uint32_t* counts, int64_t* ndt, float* tsdf, uint64_t* path_sum, void* stream) {
+                          uint32_t* counts, int64_t* ndt, float* tsdf, uint64_t* path_sum, uint64_t* mean,
+                          void* stream) {
   if (!map) return fail(OHM_ERR_INVALID, "export: map is NULL");
   if (first < 0 || count < 0 || first + count > map->p.max_regions)
     return fail(OHM_ERR_INVALID, "export: region range outside the pool");
-  void* outs[] = {keys, occupancy, counts, ndt, tsdf, path_sum};
+  void* outs[] = {keys, occupancy, counts, ndt, tsdf, path_sum, mean};
   for (void* o : outs)
     if (o && !is_device_pointer(o)) return fail(OHM_ERR_INVALID, "export: outputs must be device memory");
   if (path_sum && !(map->p.layers & OHM_LAYER_DECAY)) return fail(OHM_ERR_UNSUPPORTED, "export: no decay layer");
+  if (mean && !(map->p.layers & OHM_LAYER_MEAN)) return fail(OHM_ERR_UNSUPPORTED, "export: no mean layer");
   if (occupancy && !(map->p.layers & OHM_LAYER_OCCUPANCY)) return fail(OHM_ERR_UNSUPPORTED, "export: no occupancy layer");
   if (counts && !(map->p.layers & OHM_LAYER_COUNTS)) return fail(OHM_ERR_UNSUPPORTED, "export: no counts layer");
   if (ndt && !(map->p.layers & OHM_LAYER_NDT)) return fail(OHM_ERR_UNSUPPORTED, "export: no NDT layer");
@@ -422,7 +433,7 @@ ohm_status ohm_map_export(ohm_map* map, int64_t first, int64_t count, int32_t* k
   DeviceGuard guard(map->device);
   cudaError_t e = ohm::launch_export(map, first, count, keys, occupancy, counts, reinterpret_cast<long long*>(ndt),
                                      tsdf, reinterpret_cast<unsigned long long*>(path_sum),
-                                     static_cast<cudaStream_t>(stream));
+                                     reinterpret_cast<unsigned long long*>(mean), static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "export: launch");
   return OHM_OK;
 }

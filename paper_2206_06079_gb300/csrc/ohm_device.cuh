@@ -21,8 +21,7 @@ constexpr int kRegionVoxels = 1 << (3 * kRegionShift);
 constexpr long long kEmptyKey = -1;              // never a packed key (packed keys are < 2^63)
 constexpr long long kTombKey = -2;               // a key removed by a rolled-back call
 
-constexpr uint32_t kLayerOcc = 1, kLayerNdt = 2, kLayerTsdf = 4, kLayerCounts = 8, kLayerDecay = 16;
-constexpr float kDecayUnits = 1048576.0f;  // path lengths are summed in 2^-20 m
+constexpr uint32_t kLayerOcc = 1, kLayerNdt = 2, kLayerTsdf = 4, kLayerCounts = 8, kLayerDecay = 16, kLayerMean = 32;
 constexpr uint8_t kFlagNoReturn = 1;
 
 // Status bits latched in device memory (0 = fine).
@@ -117,7 +116,7 @@ struct CallCounters {
   int32_t seq;                      // sequence number of the current call (LRU stamps, birth marks)
   int32_t free_used_start;          // free-list positions when the call began (rollback point)
   int32_t ndt_free_used_start;
-  int32_t pad;
+  int32_t mean_touched;             // entries of mean_list written by the current call
   unsigned long long restores;      // evicted region keys this call asked to restore
 };
 
@@ -134,6 +133,9 @@ struct DeviceMap {
   float* occ;                    // [max_regions][32768], Morton order inside a region
   unsigned long long* counts;    // [max_regions][32768], hits << 32 | misses
   unsigned long long* decay;     // [max_regions][32768], summed path length, 2^-20 m
+  unsigned long long* vmean;     // [max_regions][32768], count << 32 | z10 << 20 | y10 << 10 | x10
+  unsigned long long* vmean_acc; // [max_regions][32768][2], per-call sums: Sx | Sy << 32, Sz | c << 32
+  int32_t* mean_list;            // [max_rays], voxels given samples by the current call
   int32_t* ndt_slot;             // [max_regions], -1 = no NDT layer yet
   int32_t* ndt_count;
   int32_t max_ndt;

@@ -45,10 +45,11 @@ namespace ohm {
 // Enqueue every kernel of one integrate call on `stream`.
 cudaError_t launch_integrate(ohm_map* map, const CallArgs& args, cudaStream_t stream);
 cudaError_t launch_query(ohm_map* map, const float* points, long long n, float* occupancy, uint8_t* known, float* ndt,
-                         float* tsdf, uint32_t* counts, unsigned long long* path_sum, cudaStream_t stream);
+                         float* tsdf, uint32_t* counts, unsigned long long* path_sum, float* mean,
+                         cudaStream_t stream);
 cudaError_t launch_export(ohm_map* map, long long first, long long count, int32_t* keys, float* occupancy,
                           uint32_t* counts, long long* ndt, float* tsdf, unsigned long long* path_sum,
-                          cudaStream_t stream);
+                          unsigned long long* mean, cudaStream_t stream);
 int walk_blocks_per_sm();
 
 // Region cache (ohm_cache.cu).

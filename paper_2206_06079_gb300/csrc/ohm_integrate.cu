@@ -48,6 +48,13 @@ __global__ void __launch_bounds__(kBlock) k_hits(DeviceMap m, long long n) {
   OHM_GRID_STRIDE(i, n) hit_ray<kOcc, kCounts, kNdt>(m, i);
 }
 
+// Runs for failed calls too: it then only clears the per-call sums.
+__global__ void __launch_bounds__(kBlock) k_mean_apply(DeviceMap m) {
+  const bool apply = !latched(m);
+  const long long nt = mean_touched_count(m);
+  OHM_GRID_STRIDE(t, nt) mean_apply_one(m, t, apply);
+}
+
 __global__ void __launch_bounds__(kBlock) k_prepare_tsdf(DeviceMap m, CallArgs args) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   prepare_tsdf_ray(m, args, i, i < args.n);
@@ -74,7 +81,7 @@ __global__ void k_end(DeviceMap m) {
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kBlock) k_query(DeviceMap m, const float* pts, long long n, float* occupancy,
                                                    uint8_t* known, float* ndt, float* tsdf, uint32_t* counts,
-                                                   unsigned long long* path_sum) {
+                                                   unsigned long long* path_sum, float* mean) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int F = m.frac_bits;
@@ -101,6 +108,16 @@ __global__ void __launch_bounds__(kBlock) k_query(DeviceMap m, const float* pts,
     if (known) known[i] = (l == l) ? 1 : 0;
   }
   if (path_sum) path_sum[i] = (slot >= 0 && (m.layers & kLayerDecay)) ? m.decay[off] : 0ULL;
+  if (mean) {
+    const unsigned long long w = (slot >= 0 && (m.layers & kLayerMean)) ? m.vmean[off] : 0ULL;
+    const unsigned long long cnt = w >> 32;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const double frac = ((double)((w >> (10 * k)) & 1023ULL) + 0.5) / 1024.0;
+      mean[4 * i + k] = cnt ? (float)(m.origin[k] + ((double)v[k] + frac) * m.voxel_size) : __int_as_float(0x7fc00000);
+    }
+    mean[4 * i + 3] = (float)cnt;
+  }
   if (counts) {
     unsigned long long c = 0;
     if (slot >= 0 && (m.layers & kLayerCounts)) c = m.counts[off];
@@ -147,7 +164,7 @@ __global__ void __launch_bounds__(kBlock) k_query(DeviceMap m, const float* pts,
 
 __global__ void __launch_bounds__(kBlock) k_export(DeviceMap m, long long first, long long count, int32_t* keys,
                                                     float* occupancy, uint32_t* counts, long long* ndt, float* tsdf,
-                                                    unsigned long long* path_sum) {
+                                                    unsigned long long* path_sum, unsigned long long* mean) {
   const long long total = count * kRegionVoxels;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
@@ -164,6 +181,7 @@ __global__ void __launch_bounds__(kBlock) k_export(DeviceMap m, long long first,
       counts[2 * t + 1] = (uint32_t)(c & 0xffffffffu);
     }
     if (path_sum) path_sum[t] = (m.layers & kLayerDecay) ? m.decay[off] : 0ULL;
+    if (mean) mean[t] = (m.layers & kLayerMean) ? m.vmean[off] : 0ULL;
     if (tsdf) {
       const float2 dw = (m.layers & kLayerTsdf) ? m.tsdf[off] : make_float2(0.f, 0.f);
       tsdf[2 * t + 0] = dw.x;
@@ -203,7 +221,8 @@ cudaError_t launch_integrate(ohm_map* map, const CallArgs& args, cudaStream_t st
   DeviceMap& m = map->d;
   const bool occ = (m.layers & kLayerOcc) != 0, cnt = (m.layers & kLayerCounts) != 0, ndt = (m.layers & kLayerNdt) != 0;
   const bool tsdf = (m.layers & kLayerTsdf) != 0;
-  const bool occ_like = occ || cnt || ndt || (m.layers & kLayerDecay);
+  const bool mean = (m.layers & kLayerMean) != 0;
+  const bool occ_like = occ || cnt || ndt || mean || (m.layers & kLayerDecay);
   const long long n = args.n;
   const int grid = map->walk_blocks;
   const long long per_ray_blocks = blocks_for(n) > 0 ? blocks_for(n) : 1;
@@ -228,7 +247,7 @@ cudaError_t launch_integrate(ohm_map* map, const CallArgs& args, cudaStream_t st
       default: OHM_LAUNCH(OHM_STAGE_WALK, k_walk_miss<false, false, true><<<grid, kBlock, 0, stream>>>(m)); break;
     }
   }
-  if (occ || cnt || ndt) {
+  if (occ || cnt || ndt || mean) {
     const int sel = (occ ? 4 : 0) | (cnt ? 2 : 0) | (ndt ? 1 : 0);
     switch (sel) {
       case 7: OHM_LAUNCH(OHM_STAGE_HITS, k_hits<true, true, true><<<ray_grid, kBlock, 0, stream>>>(m, n)); break;
@@ -238,8 +257,9 @@ cudaError_t launch_integrate(ohm_map* map, const CallArgs& args, cudaStream_t st
       case 3: OHM_LAUNCH(OHM_STAGE_HITS, k_hits<false, true, true><<<ray_grid, kBlock, 0, stream>>>(m, n)); break;
       case 2: OHM_LAUNCH(OHM_STAGE_HITS, k_hits<false, true, false><<<ray_grid, kBlock, 0, stream>>>(m, n)); break;
       case 1: OHM_LAUNCH(OHM_STAGE_HITS, k_hits<false, false, true><<<ray_grid, kBlock, 0, stream>>>(m, n)); break;
-      default: break;
+      default: OHM_LAUNCH(OHM_STAGE_HITS, k_hits<false, false, false><<<ray_grid, kBlock, 0, stream>>>(m, n)); break;
     }
+    if (mean) OHM_LAUNCH(OHM_STAGE_MEAN_APPLY, k_mean_apply<<<ray_grid, kBlock, 0, stream>>>(m));
   }
   if (tsdf) {
     OHM_LAUNCH(OHM_STAGE_TSDF_WALK, k_tsdf_walk<<<ray_grid, kBlock, 0, stream>>>(m, n));
@@ -250,20 +270,22 @@ cudaError_t launch_integrate(ohm_map* map, const CallArgs& args, cudaStream_t st
 }
 
 cudaError_t launch_query(ohm_map* map, const float* points, long long n, float* occupancy, uint8_t* known, float* ndt,
-                         float* tsdf, uint32_t* counts, unsigned long long* path_sum, cudaStream_t stream) {
+                         float* tsdf, uint32_t* counts, unsigned long long* path_sum, float* mean,
+                         cudaStream_t stream) {
   if (n > 0)
     k_query<<<(unsigned)blocks_for(n), kBlock, 0, stream>>>(map->d, points, n, occupancy, known, ndt, tsdf, counts,
-                                                            path_sum);
+                                                            path_sum, mean);
   return cudaGetLastError();
 }
 
 cudaError_t launch_export(ohm_map* map, long long first, long long count, int32_t* keys, float* occupancy,
                           uint32_t* counts, long long* ndt, float* tsdf, unsigned long long* path_sum,
-                          cudaStream_t stream) {
+                          unsigned long long* mean, cudaStream_t stream) {
   if (count > 0) {
     long long b = blocks_for(count * kRegionVoxels);
     if (b > 65535LL * 16) b = 65535LL * 16;
-    k_export<<<(unsigned)b, kBlock, 0, stream>>>(map->d, first, count, keys, occupancy, counts, ndt, tsdf, path_sum);
+    k_export<<<(unsigned)b, kBlock, 0, stream>>>(map->d, first, count, keys, occupancy, counts, ndt, tsdf, path_sum,
+                                                  mean);
   }
   return cudaGetLastError();
 }

@@ -161,6 +161,7 @@ __device__ __forceinline__ void begin_call(const DeviceMap& m, long long n) {
   m.calls->segments = 0;
   m.calls->visits = 0;
   m.calls->touched = 0;
+  m.calls->mean_touched = 0;
   m.calls->restores = 0;
   m.calls->rays = (unsigned long long)n;
 }
@@ -404,6 +405,12 @@ __device__ __forceinline__ void walk_segment_any(const DeviceMap& m, long long s
   }
 }
 
+// Position of a sample inside its voxel (fixed-point offset 0 .. 2^F - 1) in
+// 1/1024 of the voxel, rounded down: the voxel-mean layer's 10-bit field.
+__device__ __forceinline__ unsigned long long sub_voxel10(long long offset, int F) {
+  return F >= 10 ? (unsigned long long)(offset >> (F - 10)) : (unsigned long long)(offset << (10 - F));
+}
+
 // Sample phase (Sec. III-C phase two) for one ray: the voxel holding its
 // sample takes a hit; with the NDT layer it also accumulates the sample's
 // exact integer moments (count, sum, outer-product sum of the position inside
@@ -426,6 +433,14 @@ __device__ __forceinline__ void hit_ray(const DeviceMap& m, long long i) {
   const long long off = voxel_offset(slot, mo);
   if (kOcc) logodds_update(m, m.occ + off, m.hit);
   if (kCounts) atomicAdd(m.counts + off, 1ULL << 32);
+  if (m.layers & kLayerMean) {
+    // 10-bit position inside the voxel per axis; per-call sums (x | y << 32, z | count << 32)
+    const unsigned long long p[3] = {sub_voxel10(b[0] - (long long)vx * U, F), sub_voxel10(b[1] - (long long)vy * U, F),
+                                     sub_voxel10(b[2] - (long long)vz * U, F)};
+    atomicAdd(m.vmean_acc + 2 * off, p[0] | (p[1] << 32));
+    const unsigned long long prev = atomicAdd(m.vmean_acc + 2 * off + 1, p[2] | (1ULL << 32));
+    if ((prev >> 32) == 0) m.mean_list[atomicAdd(&m.calls->mean_touched, 1)] = (int32_t)off;
+  }
   if (kNdt) {
     const int32_t ns = m.ndt_slot[slot];
     if (ns < 0) {
@@ -554,6 +569,30 @@ __device__ __forceinline__ void tsdf_apply_one(const DeviceMap& m, long long t) 
   const double Dn = (W * D + S) / Wn;
   m.tsdf[off] = make_float2((float)Dn, (float)(Wn < (double)m.wmax ? Wn : (double)m.wmax));
 }
+
+// Voxel-mean update of one voxel given samples by the call: per axis
+// m <- floor((m n + S + floor((n + c) / 2)) / (n + c)), n <- min(n + c, 2^32 - 1);
+// the per-call sums are cleared.  apply = false (a failed call) only clears.
+__device__ __forceinline__ void mean_apply_one(const DeviceMap& m, long long t, bool apply) {
+  const int32_t off = m.mean_list[t];
+  const unsigned long long a0 = m.vmean_acc[2LL * off], a1 = m.vmean_acc[2LL * off + 1];
+  m.vmean_acc[2LL * off] = 0;
+  m.vmean_acc[2LL * off + 1] = 0;
+  if (!apply) return;
+  const unsigned long long S[3] = {a0 & 0xffffffffULL, a0 >> 32, a1 & 0xffffffffULL};
+  const unsigned long long c = a1 >> 32;
+  const unsigned long long w = m.vmean[off];
+  const unsigned long long n0 = w >> 32, nt = n0 + c;
+  unsigned long long packed = 0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const unsigned long long mk = (w >> (10 * k)) & 1023ULL;
+    packed |= ((mk * n0 + S[k] + nt / 2) / nt) << (10 * k);
+  }
+  m.vmean[off] = ((nt < 0xffffffffULL ? nt : 0xffffffffULL) << 32) | packed;
+}
+
+__device__ __forceinline__ long long mean_touched_count(const DeviceMap& m) { return (long long)m.calls->mean_touched; }
 
 __device__ __forceinline__ long long touched_count(const DeviceMap& m) {
   unsigned long long nt = m.calls->touched;

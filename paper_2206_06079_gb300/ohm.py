@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.environ.get("OHM_GB_LIB") or os.path.join(_HERE, "_lib", "libohm_gb.so")
 
 OK, ERR_INVALID, ERR_CAPACITY, ERR_CUDA, ERR_PROBE_LIMIT, ERR_UNSUPPORTED, ERR_EVICTED = range(7)
-LAYER_OCCUPANCY, LAYER_NDT, LAYER_TSDF, LAYER_COUNTS, LAYER_DECAY = 1, 2, 4, 8, 16
+LAYER_OCCUPANCY, LAYER_NDT, LAYER_TSDF, LAYER_COUNTS, LAYER_DECAY, LAYER_MEAN = 1, 2, 4, 8, 16, 32
 DECAY_UNITS = float(1 << 20)   # path_sum units per metre
 FLAG_NO_RETURN = 1
 REGION_VOXELS = 32768
@@ -38,7 +38,8 @@ BATCH_MAX_MAPS = 32
 NOALLOC_MAX_RAYS = 32768
 
 # Kernel stages of an integrate call (ohm_stage).
-STAGES = ["begin", "prepare", "ndt_alloc", "prepare_tsdf", "walk", "hits", "tsdf_walk", "tsdf_apply", "end"]
+STAGES = ["begin", "prepare", "ndt_alloc", "prepare_tsdf", "walk", "hits", "tsdf_walk", "tsdf_apply", "end",
+          "mean_apply"]
 
 
 class OhmError(RuntimeError):
@@ -114,11 +115,11 @@ def load_library(path: str = LIB_PATH):
     lib.ohm_map_sync.restype = st
     lib.ohm_map_sync.argtypes = [vp, vp]
     lib.ohm_query_voxels.restype = st
-    lib.ohm_query_voxels.argtypes = [vp, p, i64, p, p, p, p, p, p, vp]
+    lib.ohm_query_voxels.argtypes = [vp, p, i64, p, p, p, p, p, p, p, vp]
     lib.ohm_map_region_count.restype = st
     lib.ohm_map_region_count.argtypes = [vp, ctypes.POINTER(i64), vp]
     lib.ohm_map_export.restype = st
-    lib.ohm_map_export.argtypes = [vp, i64, i64, p, p, p, p, p, p, vp]
+    lib.ohm_map_export.argtypes = [vp, i64, i64, p, p, p, p, p, p, p, vp]
     lib.ohm_map_stats.restype = st
     lib.ohm_map_stats.argtypes = [vp, ctypes.POINTER(CallStats), vp]
     lib.ohm_map_profile.restype = st
@@ -304,9 +305,10 @@ class Map:
                                                 _stream_handle(stream)))
         return gd, gt
 
-    def query(self, points, stream=None, ndt=False, tsdf=False, counts=False, path_sum=False):
+    def query(self, points, stream=None, ndt=False, tsdf=False, counts=False, path_sum=False, mean=False):
         """Look up world points; returns a dict of CUDA tensors (path_sum:
-        int64 summed path length in 2^-20 m units, the decay layer)."""
+        int64 summed path length in 2^-20 m units, the decay layer; mean:
+        (n, 4) float32 voxel-mean position x y z and sample count)."""
         p = _as_points(points, "points")
         n = int(p.shape[0])
         dev = self.device
@@ -320,9 +322,12 @@ class Map:
             out["counts"] = torch.empty((n, 2), dtype=torch.int32, device=dev)
         if path_sum:
             out["path_sum"] = torch.empty(n, dtype=torch.int64, device=dev)
+        if mean:
+            out["mean"] = torch.empty((n, 4), dtype=torch.float32, device=dev)
         _check(load_library().ohm_query_voxels(self._h, _ptr(p), n, _ptr(out["occupancy"]), _ptr(out["known"]),
                                                _ptr(out.get("ndt")), _ptr(out.get("tsdf")), _ptr(out.get("counts")),
-                                               _ptr(out.get("path_sum")), _stream_handle(stream)))
+                                               _ptr(out.get("path_sum")), _ptr(out.get("mean")),
+                                               _stream_handle(stream)))
         return out
 
     def evict(self, keep_regions: int, stream=None) -> int:
@@ -372,8 +377,8 @@ class Map:
         _check(load_library().ohm_map_profile_read(self._h, STAGES.index(stage), ctypes.byref(ms), ctypes.byref(n)))
         return float(ms.value), int(n.value)
 
-    def export(self, occupancy=True, counts=False, ndt=False, tsdf=False, path_sum=False, first=0, count=None,
-               stream=None):
+    def export(self, occupancy=True, counts=False, ndt=False, tsdf=False, path_sum=False, mean=False, first=0,
+               count=None, stream=None):
         """Regions [first, first + count) in allocation order as CUDA tensors;
         voxels x fastest inside a region."""
         if count is None:
@@ -390,9 +395,12 @@ class Map:
             out["tsdf"] = torch.empty((count, REGION_VOXELS, 2), dtype=torch.float32, device=dev)
         if path_sum:
             out["path_sum"] = torch.empty((count, REGION_VOXELS), dtype=torch.int64, device=dev)
+        if mean:
+            out["mean"] = torch.empty((count, REGION_VOXELS), dtype=torch.int64, device=dev)
         _check(load_library().ohm_map_export(self._h, first, count, _ptr(out["keys"]), _ptr(out.get("occupancy")),
                                              _ptr(out.get("counts")), _ptr(out.get("ndt")), _ptr(out.get("tsdf")),
-                                             _ptr(out.get("path_sum")), _stream_handle(stream)))
+                                             _ptr(out.get("path_sum")), _ptr(out.get("mean")),
+                                             _stream_handle(stream)))
         return out
 
 

@@ -11,7 +11,7 @@ import numpy as np
 
 from . import synth
 
-OCC, NDT, TSDF, COUNTS, DECAY = 1, 2, 4, 8, 16
+OCC, NDT, TSDF, COUNTS, DECAY, MEAN = 1, 2, 4, 8, 16, 32
 
 HIT = float(np.float32(math.log(0.7 / 0.3)))    # p = 0.7 -> +0.847
 MISS = float(np.float32(math.log(0.4 / 0.6)))   # p = 0.4 -> -0.405

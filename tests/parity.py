@@ -15,25 +15,26 @@ def gpu_region_order(gm: ohm.Map):
 
 
 def compare_dense(gm: ohm.Map, om: oracle.OracleMap, occupancy=True, counts=True, tsdf=False,
-                  tsdf_atol=1e-5, batch=1024, path=False):
+                  tsdf_atol=1e-5, batch=1024, path=False, mean=False):
     """Region set equal; occupancy bit-exact; hit/miss counts exact; TSDF D
     within tsdf_atol and W exact; decay-rate path sums exact (both sides
-    round each visit's distance to 2^-20 m in float the same way).  Returns
-    the number of regions compared."""
+    use the same integer definition); voxel-mean words exact.  Returns the
+    number of regions compared."""
     keys, order = gpu_region_order(gm)
     n = len(order)
     assert n == om.region_count(), (n, om.region_count())
     for i0 in range(0, n, batch):
         i1 = min(n, i0 + batch)
         ref = om.export(first=i0, count=i1 - i0, occupancy=occupancy, counts=counts, ndt=False, tsdf=tsdf,
-                        path=path)
+                        path=path, mean=mean)
         assert np.array_equal(keys[order[i0:i1]], ref["keys"]), "region keys differ"
         slots = torch.from_numpy(order[i0:i1]).cuda()
         for s0 in range(0, i1 - i0, 256):
             sl = slots[s0:s0 + 256]
             # export contiguous GPU slots covering this batch, then gather
             lo, hi = int(sl.min()), int(sl.max()) + 1
-            ex = gm.export(occupancy=occupancy, counts=counts, tsdf=tsdf, path_sum=path, first=lo, count=hi - lo)
+            ex = gm.export(occupancy=occupancy, counts=counts, tsdf=tsdf, path_sum=path, mean=mean, first=lo,
+                           count=hi - lo)
             idx = sl - lo
             r = slice(s0, s0 + len(sl))
             if occupancy:
@@ -49,6 +50,11 @@ def compare_dense(gm: ohm.Map, om: oracle.OracleMap, occupancy=True, counts=True
             if path:
                 ps = ex["path_sum"][idx].cpu().numpy().view(np.uint64)
                 assert np.array_equal(ps, ref["path"][r]), "decay path sums differ"
+            if mean:
+                w = ex["mean"][idx].cpu().numpy().view(np.uint64)
+                dec = np.stack([w >> 32, w & 1023, (w >> 10) & 1023, (w >> 20) & 1023], -1).astype(np.uint32)
+                assert np.array_equal(dec, ref["mean"][r]), "voxel means differ"
+                assert not ((w >> 30) & 3).any(), "unused bits of a voxel-mean word set"
             if tsdf:
                 t = ex["tsdf"][idx].cpu().numpy().astype(np.float64)
                 assert np.array_equal(t[..., 1], ref["tsdf"][r][..., 1]), "TSDF weights differ"
@@ -91,10 +97,14 @@ def compare_ndt(gm: ohm.Map, om: oracle.OracleMap):
 
 
 def compare_query(gm: ohm.Map, om: oracle.OracleMap, pts: np.ndarray, ndt=False, tsdf=False, ndt_rtol=1e-4,
-                  tsdf_atol=1e-5, path=False):
+                  tsdf_atol=1e-5, path=False, mean=False):
     g = gm.query(torch.from_numpy(np.ascontiguousarray(pts, dtype=np.float32)).cuda(), ndt=ndt, tsdf=tsdf,
-                 path_sum=path)
+                 path_sum=path, mean=mean)
     r = om.query(pts)
+    if mean:
+        gm4 = g["mean"].cpu().numpy().astype(np.float64)
+        assert np.array_equal(gm4[:, 3], r["mean"][:, 3]), "voxel-mean counts differ"
+        assert np.allclose(gm4[:, :3], r["mean"][:, :3], rtol=1e-6, atol=1e-6, equal_nan=True), "voxel means differ"
     if path:
         assert np.array_equal(g["path_sum"].cpu().numpy().view(np.uint64), r["path"]), "decay path sums differ"
     assert np.array_equal(g["known"].cpu().numpy(), r["known"]), "known flags differ"
@@ -122,7 +132,8 @@ def export_sorted(gm: ohm.Map):
     """Every layer of every region, regions sorted by key (CPU tensors)."""
     L = gm.params["layers"]
     ex = gm.export(occupancy=bool(L & ohm.LAYER_OCCUPANCY), counts=bool(L & ohm.LAYER_COUNTS),
-                   ndt=bool(L & ohm.LAYER_NDT), tsdf=bool(L & ohm.LAYER_TSDF), path_sum=bool(L & ohm.LAYER_DECAY))
+                   ndt=bool(L & ohm.LAYER_NDT), tsdf=bool(L & ohm.LAYER_TSDF), path_sum=bool(L & ohm.LAYER_DECAY),
+                   mean=bool(L & ohm.LAYER_MEAN))
     keys = ex["keys"].cpu().numpy()
     order = torch.from_numpy(np.lexsort((keys[:, 2], keys[:, 1], keys[:, 0]))).to(ex["keys"].device)
     out = {}

@@ -62,3 +62,28 @@ def test_param_structs_match_the_header(tmp_path):
         got = _c_layout(name, fields, tmp_path)
         assert got[:-1] == [getattr(cls, f).offset for f in fields], name
         assert got[-1] == ctypes.sizeof(cls), name
+
+
+def test_create_rejects_bad_parameters_before_touching_a_device():
+    """Parameter validation is host logic: every rejection below returns
+    OHM_ERR_INVALID with a message and needs no GPU."""
+    import pytest
+    from paper_2206_06079_gb300 import workloads as W
+    build_lib.build()
+    cases = [
+        (dict(layers=0), "layer mask"),
+        (dict(layers=64), "layer mask"),
+        (dict(frac_bits=7), "frac_bits"),
+        (dict(frac_bits=21), "frac_bits"),
+        (dict(max_regions=(1 << 16) + 1), "max_regions"),
+        (dict(layers=W.OCC | W.MEAN, max_rays=(1 << 22) + 1), "mean layer"),
+        (dict(max_range=1e5), "2^30"),
+        (dict(l_min=1.0, l_max=0.0), "l_min"),
+        (dict(ndt_clear_below=float("nan")), "NaN"),
+        (dict(layers=W.NDT, max_ndt_regions=0), "max_ndt_regions"),
+    ]
+    for kw, msg in cases:
+        with pytest.raises(ohm.OhmError) as ei:
+            ohm.Map(**W.room_params(**kw))
+        assert ei.value.code == ohm.ERR_INVALID, kw
+        assert msg in str(ei.value), (kw, str(ei.value))

@@ -26,7 +26,7 @@ def _map_specs():
                         max_range=20.0),
         W.room_params(layers=W.DECAY, max_rays=32768),
         W.tsdf_params(layers=W.TSDF, max_rays=160 * 120),
-        W.room_params(layers=W.OCC | W.COUNTS | W.NDT, max_rays=32768, voxel_size=0.05, max_regions=4096),
+        W.room_params(layers=W.OCC | W.COUNTS | W.NDT | W.MEAN, max_rays=32768, voxel_size=0.05, max_regions=4096),
         W.tsdf_params(layers=W.TSDF | W.OCC, max_rays=160 * 120),
     ]
 

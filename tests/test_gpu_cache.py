@@ -21,7 +21,7 @@ def _built():
 
 
 def _params(**kw):
-    p = dict(layers=W.OCC | W.NDT | W.COUNTS | W.DECAY, max_rays=32768, max_range=20.0, max_regions=8192,
+    p = dict(layers=W.OCC | W.NDT | W.COUNTS | W.DECAY | W.MEAN, max_rays=32768, max_range=20.0, max_regions=8192,
              max_ndt_regions=2048)
     p.update(kw)
     return W.tunnel_params(**p)
@@ -59,7 +59,7 @@ def test_integrating_into_evicted_regions_restores_them():
         om.integrate(*[t.cpu().numpy() for t in s])
     a.restore_all()
     assert_maps_identical(a, b)
-    compare_dense(b, om, path=True)
+    compare_dense(b, om, path=True, mean=True)
     compare_ndt(b, om)
 
 

@@ -182,7 +182,7 @@ def test_per_ray_origins_and_async_sync():
 
 
 def test_edge_cases():
-    p = W.room_params(layers=W.OCC | W.COUNTS | W.NDT | W.DECAY, max_rays=64)
+    p = W.room_params(layers=W.OCC | W.COUNTS | W.NDT | W.DECAY | W.MEAN, max_rays=64)
     gm, om = _pair(p)
     gm.integrate(np.zeros((1, 3), np.float32), np.zeros((0, 3), np.float32))  # empty ray set
     assert gm.region_count() == 0
@@ -196,13 +196,13 @@ def test_edge_cases():
                   [0.3, -0.3, 0.3]], np.float32)  # exact diagonal
     f = np.array([0, 0, 0, 0, 0, 0, 1], np.uint8)
     _integrate_both(gm, om, synth.RaySet(torch.from_numpy(o), torch.from_numpy(e), torch.from_numpy(f)))
-    compare_dense(gm, om, path=True)
+    compare_dense(gm, om, path=True, mean=True)
     compare_ndt(gm, om)
     # all rays skipped
     bad = np.full((5, 3), np.inf, np.float32)
     gm.integrate(o, bad)
     om.integrate(o, bad)
-    compare_dense(gm, om, path=True)
+    compare_dense(gm, om, path=True, mean=True)
     with pytest.raises(ohm.OhmError):
         gm.integrate(o, np.zeros((65, 3), np.float32))  # more than max_rays
 
@@ -288,4 +288,28 @@ def test_decay_layer_tunnel_full_size():
     _integrate_both(gm, om, rays)
     compare_query(gm, om, _sample_points(rays, k=50000), ndt=True, path=True)
     compare_dense(gm, om, batch=512, path=True)
+
+
+@pytest.mark.parametrize("layers", ["occ_mean", "mean_only"])
+def test_voxel_mean_layer_matches_oracle(layers):
+    """Voxel mean (Sec. III-C): packed 10-bit means and counts bit-exact
+    over several calls (the per-call update makes them order-independent)."""
+    L = W.OCC | W.COUNTS | W.MEAN if layers == "occ_mean" else W.MEAN
+    p = W.room_params(layers=L, max_regions=4096, max_rays=8192, max_range=2.5)
+    gm, om = _pair(p)
+    for scan in range(4):
+        rays = synth.fuzz_rays(700 + scan, 6000)
+        _integrate_both(gm, om, rays)
+    compare_dense(gm, om, occupancy=bool(L & W.OCC), counts=bool(L & W.COUNTS), mean=True)
+    compare_query(gm, om, _sample_points(rays), mean=True)
+
+
+def test_voxel_mean_tunnel_with_every_layer():
+    p = W.tunnel_params(layers=W.OCC | W.NDT | W.COUNTS | W.DECAY | W.MEAN)
+    gm, om = _pair(p)
+    for i in range(2):
+        rays = W.tunnel_rays(40 + i)
+        _integrate_both(gm, om, rays)
+    compare_query(gm, om, _sample_points(rays, k=50000), ndt=True, path=True, mean=True)
+    compare_dense(gm, om, batch=512, path=True, mean=True)
 
