@@ -100,7 +100,7 @@ __device__ __forceinline__ CallArgs batch_args(const BatchStep* step, int i) {
 
 __global__ void k_batch_begin(const BatchDesc* desc, const BatchStep* step) {
   const int i = threadIdx.x;
-  if (i < desc->n_maps) begin_call(desc->maps[i], step->n[i]);
+  if (i < desc->n_maps) begin_call(desc->maps[i], batch_args(step, i));
 }
 
 __global__ void __launch_bounds__(kBlock) k_batch_prepare(const BatchDesc* desc, const BatchStep* step, int tsdf) {

@@ -237,6 +237,12 @@ ohm_status ohm_map_create(const ohm_map_params* params, ohm_map** out) {
   for (int k = 0; k < 3; ++k) d.origin[k] = p.map_origin[k];
   d.scale = scale;
   d.rmax_q = p.max_range * scale;
+  {
+    // |b - a|^2 <= (rmax_q - 1)^2 gives a double length below rmax_q (its
+    // relative error is a few 2^-53); checked against the double bound
+    const double r_in = d.rmax_q - 1.0;
+    d.rmax_in2 = r_in > 0.0 ? (unsigned long long)std::floor(r_in * r_in) : 0ULL;
+  }
   d.rmin_q = p.min_range * scale;
   d.tau_q = p.tsdf_trunc * scale;
   d.voxel_size = p.voxel_size;

@@ -118,6 +118,9 @@ struct CallCounters {
   int32_t ndt_free_used_start;
   int32_t mean_touched;             // entries of mean_list written by the current call
   unsigned long long restores;      // evicted region keys this call asked to restore
+  long long origin_q[3];            // the call's shared sensor origin, quantised (one origin only)
+  int32_t origin_ok;                // 1 if origin_q is valid
+  int32_t pad2;
 };
 
 // Everything a kernel needs, passed by value.
@@ -167,6 +170,9 @@ struct DeviceMap {
   double origin[3];
   double scale;                  // 2^F / voxel_size
   double rmax_q, rmin_q, tau_q;  // ranges in fixed-point units
+  // a ray with |b - a|^2 <= rmax_in2 (fixed-point units^2) is certainly
+  // within max_range
+  unsigned long long rmax_in2;
   double voxel_size;
   int32_t frac_bits;
   uint32_t layers;
@@ -299,7 +305,8 @@ __device__ inline void insert_region(const DeviceMap& m, int rx, int ry, int rz)
 __device__ __forceinline__ bool quantise(float x, double origin, double scale, long long* q) {
   double d = __dsub_rn((double)x, origin);
   double s = __dmul_rn(d, scale);
-  if (!(fabs(s) < 4503599627370496.0)) return false;  // 2^52, also rejects NaN
+  // |s| < 2^52 (also rejects NaN), tested on the bit pattern
+  if (!((__double_as_longlong(s) & 0x7fffffffffffffffLL) < 0x4330000000000000LL)) return false;
   *q = __double2ll_rn(s);
   return true;
 }

@@ -23,9 +23,9 @@ namespace ohm {
 #define OHM_GRID_STRIDE(i, n) \
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += (long long)gridDim.x * blockDim.x)
 
-__global__ void k_begin(DeviceMap m, long long n) { begin_call(m, n); }
+__global__ void k_begin(DeviceMap m, CallArgs args) { begin_call(m, args); }
 
-__global__ void __launch_bounds__(kBlock) k_prepare_occ(DeviceMap m, CallArgs args) {
+__global__ void __launch_bounds__(kBlock, OHM_PREPARE_MIN_BLOCKS) k_prepare_occ(DeviceMap m, CallArgs args) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   prepare_occ_ray(m, args, i, i < args.n);
 }
@@ -228,7 +228,7 @@ cudaError_t launch_integrate(ohm_map* map, const CallArgs& args, cudaStream_t st
   const long long per_ray_blocks = blocks_for(n) > 0 ? blocks_for(n) : 1;
   const int ray_grid = (int)(per_ray_blocks < grid ? per_ray_blocks : grid);
   const unsigned prb = (unsigned)per_ray_blocks;
-  OHM_LAUNCH(OHM_STAGE_BEGIN, k_begin<<<1, 1, 0, stream>>>(m, n));
+  OHM_LAUNCH(OHM_STAGE_BEGIN, k_begin<<<1, 1, 0, stream>>>(m, args));
   if (occ_like) {
     OHM_LAUNCH(OHM_STAGE_PREPARE, k_prepare_occ<<<prb, kBlock, 0, stream>>>(m, args));
     if (ndt) OHM_LAUNCH(OHM_STAGE_NDT_ALLOC, k_ndt_alloc<<<ray_grid, kBlock, 0, stream>>>(m, n));

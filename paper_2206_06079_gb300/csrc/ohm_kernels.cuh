@@ -150,9 +150,15 @@ static __device__ __noinline__ void logodds_retry(const DeviceMap& m, unsigned i
 #define OHM_WALK_MIN_BLOCKS 4
 #endif
 constexpr int kWalkBatch = OHM_WALK_BATCH;
+// blocks of 256 threads per SM the prepare kernel is compiled for (4: a
+// 131,072-ray scan fits one wave on 152 SMs)
+#ifndef OHM_PREPARE_MIN_BLOCKS
+#define OHM_PREPARE_MIN_BLOCKS 4
+#endif
 
 // Snapshot of the pool counters at the start of a call (the rollback point).
-__device__ __forceinline__ void begin_call(const DeviceMap& m, long long n) {
+__device__ __forceinline__ void begin_call(const DeviceMap& m, const CallArgs& a) {
+  const long long n = a.n;
   m.calls->region_start = *m.region_count;
   m.calls->ndt_start = *m.ndt_count;
   m.calls->free_used_start = m.free_info[1];
@@ -164,6 +170,33 @@ __device__ __forceinline__ void begin_call(const DeviceMap& m, long long n) {
   m.calls->mean_touched = 0;
   m.calls->restores = 0;
   m.calls->rays = (unsigned long long)n;
+  // a shared sensor origin is quantised once for the whole call
+  bool ok = false;
+  if (a.n_origins == 1 && n > 0) {
+    ok = true;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float o = a.origins[k];
+      long long q = 0;
+      ok = ok && isfinite(o) && quantise(o, m.origin[k], m.scale, &q);
+      m.calls->origin_q[k] = q;
+    }
+  }
+  m.calls->origin_ok = ok ? 1 : 0;
+}
+
+// quantise_ray for the rays of the current call: a shared origin comes
+// quantised from begin_call.
+__device__ __forceinline__ bool quantise_call_ray(const DeviceMap& m, const CallArgs& a, const float o[3],
+                                                  const float e[3], long long qo[3], long long qe[3]) {
+  if (a.n_origins != 1) return quantise_ray(m, o, e, qo, qe);
+  bool ok = m.calls->origin_ok != 0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    qo[k] = m.calls->origin_q[k];
+    ok = ok && isfinite(e[k]) && quantise(e[k], m.origin[k], m.scale, &qe[k]);
+  }
+  return ok;
 }
 
 // Per ray: fixed-point quantisation, max-range truncation, region walk with
@@ -183,16 +216,30 @@ __device__ __forceinline__ void prepare_occ_ray(const DeviceMap& m, const CallAr
     uint8_t flag;
     load_ray(args, i, o, e, &flag);
     long long qo[3], qe[3];
-    bool ok = quantise_ray(m, o, e, qo, qe);
+    bool ok = quantise_call_ray(m, args, o, e, qo, qe);
     bool sample = (flag & kFlagNoReturn) == 0;
     if (ok) {
-      double d[3];
-      const double len = ray_length(qo, qe, d);
-      if (len > m.rmax_q) {
-        const double ratio = __ddiv_rn(m.rmax_q, len);
+      // Truncation test len > rmax_q with len the double length: settled by
+      // the exact integer |b - a|^2 unless it lies in a band around rmax_q^2
+      // (or an axis difference is too large for it), where the double
+      // evaluation decides.
+      bool in_range = false;
+      const long long dx = qe[0] - qo[0], dy = qe[1] - qo[1], dz = qe[2] - qo[2];
+      const long long lim = 1LL << 30;
+      if (dx > -lim && dx < lim && dy > -lim && dy < lim && dz > -lim && dz < lim) {
+        const unsigned long long l2 = (unsigned long long)(dx * dx) + (unsigned long long)(dy * dy) +
+                                      (unsigned long long)(dz * dz);
+        in_range = l2 <= m.rmax_in2;
+      }
+      if (!in_range) {
+        double d[3];
+        const double len = ray_length(qo, qe, d);
+        if (len > m.rmax_q) {
+          const double ratio = __ddiv_rn(m.rmax_q, len);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) qe[k] = qo[k] + __double2ll_rn(__dmul_rn(d[k], ratio));
-        sample = false;
+          for (int k = 0; k < 3; ++k) qe[k] = qo[k] + __double2ll_rn(__dmul_rn(d[k], ratio));
+          sample = false;
+        }
       }
       ok = in_extent(qo, F) && in_extent(qe, F);
     }
@@ -470,7 +517,7 @@ __device__ __forceinline__ void prepare_tsdf_ray(const DeviceMap& m, const CallA
     uint8_t flag;
     load_ray(args, i, o, e, &flag);
     long long qo[3], qe[3];
-    bool ok = quantise_ray(m, o, e, qo, qe) && (flag & kFlagNoReturn) == 0;
+    bool ok = quantise_call_ray(m, args, o, e, qo, qe) && (flag & kFlagNoReturn) == 0;
     double d[3], len = 0.0;
     if (ok) {
       len = ray_length(qo, qe, d);
