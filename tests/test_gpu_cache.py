@@ -141,3 +141,22 @@ def test_without_eviction_a_full_pool_is_an_error():
         a.integrate(*_scan(0))
     assert ei.value.code == ohm.ERR_CAPACITY
     assert a.residency() == (0, 0)
+
+
+def test_occupancy_ndt_map_through_repeated_eviction():
+    """An occupancy + NDT map evicted down to 40 regions before each of five
+    scans ends identical to one never evicted, and to the oracle."""
+    p = _params(layers=W.OCC | W.NDT)
+    a, b = ohm.Map(**p), ohm.Map(**p)
+    om = oracle.OracleMap(**W.oracle_params(p))
+    for i in range(8):
+        s = _scan(i // 2)
+        if i >= 3:
+            a.evict(40)
+        a.integrate(*s)
+        b.integrate(*s)
+        om.integrate(*[t.cpu().numpy() for t in s])
+    a.restore_all()
+    assert_maps_identical(a, b)
+    compare_dense(a, om, counts=False)
+

@@ -313,3 +313,32 @@ def test_voxel_mean_tunnel_with_every_layer():
     compare_query(gm, om, _sample_points(rays, k=50000), ndt=True, path=True, mean=True)
     compare_dense(gm, om, batch=512, path=True, mean=True)
 
+
+
+@pytest.mark.parametrize("steps", [1, 4, 100000])
+def test_many_scans_over_saturated_space(steps):
+    """Ten scans over the same stretch of tunnel drive most free voxels to the
+    clamp l_min (misses then change nothing, hits still do); occupancy + NDT
+    stay bit-identical to the oracle at every segment split."""
+    p = W.tunnel_params(layers=W.OCC | W.NDT, segment_steps=steps, max_rays=32768, max_range=20.0,
+                        max_regions=8192, max_ndt_regions=2048)
+    gm, om = _pair(p)
+    for i in range(10):
+        rays = synth.tunnel_scan(i // 2, beams=32, azimuths=1024, max_range=20.0)
+        _integrate_both(gm, om, rays)
+    compare_dense(gm, om, counts=False)
+    compare_ndt(gm, om)
+
+
+def test_repeated_room_scans_from_moving_origins():
+    """Repeated room scans from moving origins: free voxels reach l_min, then
+    samples land on some of them again; occupancy only."""
+    p = W.room_params(layers=W.OCC, max_rays=32768)
+    gm, om = _pair(p)
+    rng = np.random.default_rng(11)
+    for i in range(12):
+        rays = synth.room_scan(seed=900 + i, n=20000)
+        o, e, f = rays.numpy()
+        shift = rng.uniform(-0.5, 0.5, size=3).astype(np.float32)
+        _integrate_both(gm, om, synth.RaySet(torch.from_numpy(o + shift), torch.from_numpy(e), torch.from_numpy(f)))
+    compare_dense(gm, om, counts=False)
