@@ -155,6 +155,15 @@ ohm_status ohm_integrate_rays_async(ohm_map* map, const float* origins, int64_t 
 /* Wait for `stream` and return (then clear) the latched device status. */
 ohm_status ohm_map_sync(ohm_map* map, void* stream);
 
+/* Enqueue on `stream` a copy of the map's latched device status bits into
+ * *status (host memory; pinned memory keeps the copy asynchronous) and return
+ * at once.  After the stream has passed this point, *status == 0 means every
+ * call enqueued before it succeeded so far; nonzero bits mean one failed (call
+ * ohm_map_sync to get the error and clear it).  Lets a caller read each
+ * call's result without waiting between calls.  The paper has no counterpart
+ * (its API is synchronous). */
+ohm_status ohm_map_status_async(ohm_map* map, int32_t* status, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Region cache (Sec. III-A: regions move between the GPU and host memory).
  * Every pool region carries the sequence number of the last integrate call

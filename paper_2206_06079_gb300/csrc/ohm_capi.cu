@@ -292,6 +292,16 @@ ohm_status ohm_map_sync(ohm_map* map, void* stream) {
   return status_from_bits(bits);
 }
 
+ohm_status ohm_map_status_async(ohm_map* map, int32_t* status, void* stream) {
+  if (!map || !status) return fail(OHM_ERR_INVALID, "status_async: NULL argument");
+  if (is_device_pointer(status)) return fail(OHM_ERR_INVALID, "status_async: status must be host memory");
+  DeviceGuard guard(map->device);
+  cudaError_t e = cudaMemcpyAsync(status, map->d.status, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                  static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "status_async");
+  return OHM_OK;
+}
+
 ohm_status ohm_integrate_rays(ohm_map* map, const float* origins, int64_t n_origins, const float* endpoints,
                               const uint8_t* flags, int64_t n, void* stream) {
   // A call that reaches evicted regions changes nothing; bring them back and

@@ -26,7 +26,7 @@ _STATUS_NAMES = {ERR_INVALID: "invalid argument", ERR_CAPACITY: "capacity", ERR_
                  ERR_PROBE_LIMIT: "hash probe limit", ERR_UNSUPPORTED: "unsupported", ERR_EVICTED: "evicted"}
 
 # Every symbol include/ohm_gb.h declares.
-EXPORTED = ["ohm_map_create", "ohm_map_destroy", "ohm_integrate_rays", "ohm_integrate_rays_async", "ohm_map_sync",
+EXPORTED = ["ohm_map_create", "ohm_map_destroy", "ohm_integrate_rays", "ohm_integrate_rays_async", "ohm_map_sync", "ohm_map_status_async",
             "ohm_query_voxels", "ohm_map_region_count", "ohm_map_export", "ohm_map_stats", "ohm_map_profile",
             "ohm_map_profile_read", "ohm_last_error", "ohm_count_rays_noalloc", "ohm_batch_create",
             "ohm_batch_destroy", "ohm_batch_tune", "ohm_batch_integrate", "ohm_batch_sync", "ohm_batch_stats",
@@ -114,6 +114,8 @@ def load_library(path: str = LIB_PATH):
         f.argtypes = [vp, p, i64, p, p, i64, vp]
     lib.ohm_map_sync.restype = st
     lib.ohm_map_sync.argtypes = [vp, vp]
+    lib.ohm_map_status_async.restype = st
+    lib.ohm_map_status_async.argtypes = [vp, p, vp]
     lib.ohm_query_voxels.restype = st
     lib.ohm_query_voxels.argtypes = [vp, p, i64, p, p, p, p, p, p, p, vp]
     lib.ohm_map_region_count.restype = st
@@ -268,6 +270,14 @@ class Map:
 
     def sync(self, stream=None):
         _check(load_library().ohm_map_sync(self._h, _stream_handle(stream)))
+
+    def status_async(self, out, stream=None):
+        """Enqueue a copy of the latched status bits into `out` (an int32 CPU
+        tensor element, pinned for an asynchronous copy); nonzero after the
+        stream passes it means an earlier call failed (see sync)."""
+        if out.device.type != "cpu" or out.dtype != torch.int32:
+            raise ValueError("status_async: out must be an int32 CPU tensor")
+        _check(load_library().ohm_map_status_async(self._h, _ptr(out), _stream_handle(stream)))
 
     @staticmethod
     def _frame_args(K, pose):

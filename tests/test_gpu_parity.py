@@ -342,3 +342,25 @@ def test_repeated_room_scans_from_moving_origins():
         shift = rng.uniform(-0.5, 0.5, size=3).astype(np.float32)
         _integrate_both(gm, om, synth.RaySet(torch.from_numpy(o + shift), torch.from_numpy(e), torch.from_numpy(f)))
     compare_dense(gm, om, counts=False)
+
+
+def test_status_async_reports_each_step_without_waiting():
+    p = W.room_params(layers=W.OCC | W.COUNTS, max_regions=40, max_ndt_regions=40)
+    gm, om = _pair(p)
+    st = torch.full((3,), -7, dtype=torch.int32).pin_memory()
+    small = synth.room_scan(n=2000, room_min=(-1, -1, 0), room_max=(1, 1, 2))
+    gm.integrate(small.origins.cuda(), small.endpoints.cuda(), small.flags.cuda(), sync=False)
+    gm.status_async(st[0:1])
+    big = W.room_rays(0)  # needs 48 regions: the call fails and changes nothing
+    gm.integrate(big.origins.cuda(), big.endpoints.cuda(), big.flags.cuda(), sync=False)
+    gm.status_async(st[1:2])
+    torch.cuda.synchronize()
+    assert int(st[0]) == 0 and int(st[1]) != 0
+    with pytest.raises(ohm.OhmError) as ei:
+        gm.sync()
+    assert ei.value.code == ohm.ERR_CAPACITY
+    gm.status_async(st[2:3])
+    torch.cuda.synchronize()
+    assert int(st[2]) == 0  # cleared by the sync
+    om.integrate(*small.numpy())
+    compare_dense(gm, om)
