@@ -87,8 +87,11 @@ typedef struct {
   int64_t max_regions;     /* capacity of the region pool, 1..65536 (8 GB of occupancy) */
   int64_t max_ndt_regions; /* capacity of the NDT layer pool (regions holding samples) */
   int64_t max_rays;        /* largest ray count accepted by one integrate call */
-  int32_t segment_steps;   /* rays are split every this many voxel steps along their
-                              dominant axis (Sec. III-B ray segments); 0 = 4 */
+  int32_t segment_steps;   /* target voxel steps per ray segment (Sec. III-B ray segments):
+                              a ray whose walk takes N voxel steps, n of them along its dominant
+                              axis, is split every max(1, round(segment_steps n / N)) (at most
+                              65535) dominant-axis steps, so segments of rays in any direction
+                              are about equally long; 0 = 10 */
   int32_t device;          /* CUDA device ordinal */
   int32_t evict_when_full; /* nonzero: when ohm_integrate_rays finds the region or NDT pool full it
                               moves least recently used regions to host memory and repeats the call
@@ -148,7 +151,10 @@ ohm_status ohm_integrate_rays(ohm_map* map, const float* origins, int64_t n_orig
 /* As ohm_integrate_rays, but returns once the work is enqueued.  Device-side
  * failures are latched in the map and returned (and cleared) by the next
  * ohm_map_sync; a failed call still leaves the map unchanged.  Input buffers
- * must stay valid until the stream has passed the call. */
+ * must stay valid until the stream has passed the call.  Host inputs are
+ * copied on a stream of the map's own into one of two staging slots (the
+ * `stream` waits for the copy), so the copy of one call overlaps the kernels
+ * of the previous one; pinned host memory keeps the copies asynchronous. */
 ohm_status ohm_integrate_rays_async(ohm_map* map, const float* origins, int64_t n_origins, const float* endpoints,
                                     const uint8_t* flags, int64_t n, void* stream);
 
@@ -330,8 +336,8 @@ ohm_status ohm_batch_create(ohm_map* const* maps, int32_t n_maps, ohm_batch** ou
 /* Free the batch (not its maps).  NULL is ignored. */
 void ohm_batch_destroy(ohm_batch* batch);
 
-/* Tile parameters of later steps: segment_steps (ray segment length in
- * dominant-axis steps, applied to every map; 0 = unchanged) and the walk
+/* Tile parameters of later steps: segment_steps (target voxel steps per ray
+ * segment, as in ohm_map_params, applied to every map; 0 = unchanged) and the walk
  * kernel's blocks per SM (0 = unchanged).  Results do not depend on them.
  * Drops the captured graph.  Synchronises the device. */
 ohm_status ohm_batch_tune(ohm_batch* batch, int32_t segment_steps, int32_t walk_blocks_per_sm);

@@ -13,6 +13,7 @@
 // device-resident table copied before each graph launch, so the graph itself
 // never changes between steps; the tile parameters (segment length, walk grid)
 // are fixed into it and changed by ohm_batch_tune, which re-captures.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -373,7 +374,7 @@ ohm_status ohm_batch_tune(ohm_batch* b, int32_t segment_steps, int32_t walk_bloc
     for (int i = 0; i < b->n_maps; ++i) {
       ohm_map* m = b->maps[i];
       const long long vox_steps = (long long)std::ceil(m->p.max_range / m->p.voxel_size) + 2;
-      const long long need = m->p.max_rays * (vox_steps / segment_steps + 1);
+      const long long need = m->p.max_rays * (vox_steps / std::max(1, segment_steps / 3) + 1);
       if (need > m->d.max_segs) {
         int2* segs = nullptr;
         e = cudaMalloc(reinterpret_cast<void**>(&segs), sizeof(int2) * need);

@@ -1,5 +1,6 @@
 // C ABI of the ray-integration library: map lifetime, argument checks, host
 // staging and status reporting.  Declared in include/ohm_gb.h.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -65,7 +66,14 @@ void free_map(ohm_map* m) {
   void* ptrs[] = {d.htab, d.region_count, d.region_coords, d.occ, d.counts, d.decay, d.vmean, d.vmean_acc, d.mean_list, d.ndt_slot, d.ndt_count,
                   d.ndt, d.tsdf, d.tsdf_cnt, d.tsdf_sum, d.grad, d.status, d.calls, d.rays, d.decay_rays, d.trays, d.segs, d.touched,
                   d.stamp, d.born, d.ndt_born, d.free_slots, d.ndt_free, d.free_info, d.restore_keys,
-                  m->stage_origins, m->stage_endpoints, m->stage_flags};
+                  m->stage_origins, m->stage_endpoints, m->stage_flags, m->hin_origins[0], m->hin_origins[1],
+                  m->hin_endpoints[0], m->hin_endpoints[1], m->hin_flags[0], m->hin_flags[1]};
+  if (m->copy_stream) cudaStreamSynchronize(m->copy_stream);
+  for (int s = 0; s < 2; ++s) {
+    if (m->hin_copied[s]) cudaEventDestroy(m->hin_copied[s]);
+    if (m->hin_free[s]) cudaEventDestroy(m->hin_free[s]);
+  }
+  if (m->copy_stream) cudaStreamDestroy(m->copy_stream);
   ohm::destroy_host_store(m);
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -109,24 +117,39 @@ ohm_status enqueue_integrate(ohm_map* map, const float* origins, int64_t n_origi
   a.origins = origins;
   a.endpoints = endpoints;
   a.flags = flags;
-  cudaError_t e;
-  if (!is_device_pointer(origins)) {
-    e = cudaMemcpyAsync(map->stage_origins, origins, sizeof(float) * 3 * n_origins, cudaMemcpyHostToDevice, stream);
-    if (e != cudaSuccess) return cuda_fail(e, "integrate: copy origins");
-    a.origins = map->stage_origins;
-  }
-  if (!is_device_pointer(endpoints)) {
-    e = cudaMemcpyAsync(map->stage_endpoints, endpoints, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, stream);
-    if (e != cudaSuccess) return cuda_fail(e, "integrate: copy endpoints");
-    a.endpoints = map->stage_endpoints;
-  }
-  if (flags && !is_device_pointer(flags)) {
-    e = cudaMemcpyAsync(map->stage_flags, flags, (size_t)n, cudaMemcpyHostToDevice, stream);
-    if (e != cudaSuccess) return cuda_fail(e, "integrate: copy flags");
-    a.flags = map->stage_flags;
+  const bool host_o = !is_device_pointer(origins), host_e = !is_device_pointer(endpoints);
+  const bool host_f = flags && !is_device_pointer(flags);
+  cudaError_t e = cudaSuccess;
+  int slot = -1;
+  if (host_o || host_e || host_f) {
+    // copy into the staging slot not used by the previous call, on the copy
+    // stream, once the kernels of the slot's last call are done with it
+    slot = map->hin_next;
+    map->hin_next ^= 1;
+    cudaStream_t cs = map->copy_stream;
+    e = cudaStreamWaitEvent(cs, map->hin_free[slot], 0);
+    if (e == cudaSuccess && host_o) {
+      e = cudaMemcpyAsync(map->hin_origins[slot], origins, sizeof(float) * 3 * n_origins, cudaMemcpyHostToDevice, cs);
+      a.origins = map->hin_origins[slot];
+    }
+    if (e == cudaSuccess && host_e) {
+      e = cudaMemcpyAsync(map->hin_endpoints[slot], endpoints, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, cs);
+      a.endpoints = map->hin_endpoints[slot];
+    }
+    if (e == cudaSuccess && host_f) {
+      e = cudaMemcpyAsync(map->hin_flags[slot], flags, (size_t)n, cudaMemcpyHostToDevice, cs);
+      a.flags = map->hin_flags[slot];
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(map->hin_copied[slot], cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, map->hin_copied[slot], 0);
+    if (e != cudaSuccess) return cuda_fail(e, "integrate: copy host inputs");
   }
   e = ohm::launch_integrate(map, a, stream);
   if (e != cudaSuccess) return cuda_fail(e, "integrate: launch");
+  if (slot >= 0) {
+    e = cudaEventRecord(map->hin_free[slot], stream);
+    if (e != cudaSuccess) return cuda_fail(e, "integrate: record");
+  }
   return OHM_OK;
 }
 
@@ -140,7 +163,7 @@ ohm_status ohm_map_create(const ohm_map_params* params, ohm_map** out) {
   if (!params || !out) return fail(OHM_ERR_INVALID, "create: NULL argument");
   *out = nullptr;
   ohm_map_params p = *params;
-  if (p.segment_steps == 0) p.segment_steps = 4;
+  if (p.segment_steps == 0) p.segment_steps = 10;
   if (!(p.voxel_size > 0.0) || !std::isfinite(p.voxel_size)) return fail(OHM_ERR_INVALID, "create: voxel_size must be > 0");
   if (p.frac_bits < 8 || p.frac_bits > 20) return fail(OHM_ERR_INVALID, "create: frac_bits must be in [8, 20]");
   const uint32_t all = OHM_LAYER_OCCUPANCY | OHM_LAYER_NDT | OHM_LAYER_TSDF | OHM_LAYER_COUNTS | OHM_LAYER_DECAY | OHM_LAYER_MEAN;
@@ -178,7 +201,8 @@ ohm_status ohm_map_create(const ohm_map_params* params, ohm_map** out) {
   d.max_regions = (int32_t)R;
   d.max_ndt = (p.layers & OHM_LAYER_NDT) ? (int32_t)p.max_ndt_regions : 0;
   const long long vox_steps = (long long)std::ceil(p.max_range / p.voxel_size) + 2;
-  d.max_segs = p.max_rays * (vox_steps / p.segment_steps + 1);
+  // a ray's segments take at least max(1, segment_steps / 3) dominant-axis steps
+  d.max_segs = p.max_rays * (vox_steps / std::max(1, p.segment_steps / 3) + 1);
   const long long band = (long long)std::ceil(2.0 * p.tsdf_trunc / p.voxel_size) + 2;
   d.max_touched = (p.layers & OHM_LAYER_TSDF) ? p.max_rays * (1 + 3 * band) : 0;
   if (d.max_touched > R * V) d.max_touched = R * V;
@@ -226,6 +250,14 @@ ohm_status ohm_map_create(const ohm_map_params* params, ohm_map** out) {
   chk(alloc(&m->stage_origins, 3 * p.max_rays, 0));
   chk(alloc(&m->stage_endpoints, 3 * p.max_rays, 0));
   chk(alloc(&m->stage_flags, p.max_rays, 0));
+  for (int s = 0; s < 2; ++s) {
+    chk(alloc(&m->hin_origins[s], 3 * p.max_rays, 0));
+    chk(alloc(&m->hin_endpoints[s], 3 * p.max_rays, 0));
+    chk(alloc(&m->hin_flags[s], p.max_rays, 0));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->hin_copied[s], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->hin_free[s], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&m->copy_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&m->h_status), sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&m->h_calls), sizeof(ohm::CallCounters));
   if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&m->h_count), 2 * sizeof(int32_t));

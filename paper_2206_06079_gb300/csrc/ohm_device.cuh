@@ -592,6 +592,17 @@ __host__ __device__ __forceinline__ uint32_t morton_mask(int axis) {
 // Number of segments of a walk whose dominant axis takes nmaj steps.
 __host__ __device__ __forceinline__ int32_t segment_count(int32_t nmaj, int32_t S) { return nmaj / S + 1; }
 
+// Dominant-axis steps per segment of a walk that takes nsteps voxel steps,
+// nmaj of them along its dominant axis, so that a segment covers about
+// `target` voxel steps whatever the ray's direction: round(target nmaj /
+// nsteps), within [1, 65535].  Never below target / 3 (nsteps <= 3 nmaj).
+__host__ __device__ __forceinline__ int32_t ray_segment_steps(int32_t nmaj, long long nsteps, int32_t target) {
+  if (nsteps <= 0) return 1;
+  const long long s = ((long long)target * nmaj * 2 + nsteps) / (2 * nsteps);
+  return s < 1 ? 1 : (s > 65535 ? 65535 : (int32_t)s);
+}
+constexpr int kRaySegShift = 16;  // RayRec flags bits 16..31: the ray's dominant-axis steps per segment
+
 // ---------------------------------------------------------------------------
 // Warp-aggregated reservation: every lane of a full warp calls this together
 // with its own count (possibly 0); returns this lane's first index.

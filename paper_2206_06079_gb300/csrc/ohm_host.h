@@ -22,10 +22,19 @@ struct ohm_map {
   int num_sms;
   int walk_blocks;          // persistent grid for the walk kernels
   long long hash_capacity;
-  // device staging for host inputs
+  // device staging for inputs generated on the device (depth frames)
   float* stage_origins;
   float* stage_endpoints;
   uint8_t* stage_flags;
+  // host inputs: two staging slots filled on copy_stream, so that the copy of
+  // one call overlaps the kernels of the previous one
+  float* hin_origins[2];
+  float* hin_endpoints[2];
+  uint8_t* hin_flags[2];
+  cudaStream_t copy_stream;
+  cudaEvent_t hin_copied[2];  // slot filled
+  cudaEvent_t hin_free[2];    // kernels of the slot's last call done
+  int hin_next;
   // pinned host mirrors for status / counters
   int32_t* h_status;
   ohm::CallCounters* h_calls;

@@ -246,10 +246,17 @@ __device__ __forceinline__ void prepare_occ_ray(const DeviceMap& m, const CallAr
     if (ok) {
       int32_t nmaj;
       const int M = dominant_axis(qo, qe, F, &nmaj);
-      nseg = (unsigned int)segment_count(nmaj, m.seg_steps);
+      long long l1 = 0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        long long dv = (qe[k] >> F) - (qo[k] >> F);
+        l1 += dv < 0 ? -dv : dv;
+      }
+      const int32_t S = ray_segment_steps(nmaj, l1, m.seg_steps);
+      nseg = (unsigned int)segment_count(nmaj, S);
       const long long am = sel3(M, qe[0] - qo[0], qe[1] - qo[1], qe[2] - qo[2]);
       r.inv = reciprocal64((unsigned long long)(am < 0 ? -am : am));
-      r.flags = kRayValid | (sample ? kRaySample : 0) | (M << kRayAxisShift);
+      r.flags = kRayValid | (sample ? kRaySample : 0) | (M << kRayAxisShift) | (int32_t)((uint32_t)S << kRaySegShift);
       ray_constants(qo, qe, F, &r);
       r.nseg = (int32_t)nseg;
       if (m.layers & kLayerDecay) {
@@ -258,12 +265,6 @@ __device__ __forceinline__ void prepare_occ_ray(const DeviceMap& m, const CallAr
         for (int k = 0; k < 3; ++k) dr.inv[k] = reciprocal64((unsigned long long)r.A[k]);
         dr.length = walk_length_units(qo, qe, m.voxel_size, F);
         m.decay_rays[i] = dr;
-      }
-      long long l1 = 0;
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        long long dv = (qe[k] >> F) - (qo[k] >> F);
-        l1 += dv < 0 ? -dv : dv;
       }
       nvisit = (unsigned int)(1 + l1);
       insert_ray_regions(m, qo, qe);
@@ -331,10 +332,10 @@ __device__ __forceinline__ unsigned long long decay_position(long long dist, int
 template <bool kOcc, bool kCounts, bool kDecay>
 __device__ __forceinline__ void walk_segment(const DeviceMap& m, long long si) {
   const int F = m.frac_bits;
-  const int32_t S = m.seg_steps;
   const float miss = m.miss;
   const int2 sg = m.segs[si];
   const RayRec r = m.rays[sg.x];
+  const int32_t S = (int32_t)((uint32_t)r.flags >> kRaySegShift);  // this ray's dominant-axis steps per segment
   const int M = (r.flags >> kRayAxisShift) & 3;
   const bool last = sg.y == r.nseg - 1;
   const bool sample = (r.flags & kRaySample) != 0;

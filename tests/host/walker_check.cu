@@ -21,7 +21,14 @@ int main(int argc, char** argv) {
     if (scanf("%lld %lld %lld %lld %lld %lld", &a[0], &a[1], &a[2], &b[0], &b[1], &b[2]) != 6) return 1;
     int32_t nmaj;
     const int M = ohm::dominant_axis(a, b, F, &nmaj);
-    const int nseg = ohm::segment_count(nmaj, S);
+    long long nsteps = 0;
+    for (int k = 0; k < 3; ++k) {
+      const long long dv = (b[k] >> F) - (a[k] >> F);
+      nsteps += dv < 0 ? -dv : dv;
+    }
+    // the kernels' per-ray segment length (S is the target voxel steps per segment)
+    const int Sr = use_inv ? ohm::ray_segment_steps(nmaj, nsteps, S) : S;
+    const int nseg = ohm::segment_count(nmaj, Sr);
     long long c = 0;
     for (int j = 0; j < nseg; ++j) {
       ohm::Walker w;
@@ -36,12 +43,12 @@ int main(int argc, char** argv) {
         long long bb[3];
         ohm::ray_end(rec, F, bb);
         if (bb[0] != b[0] || bb[1] != b[1] || bb[2] != b[2]) return 3;
-        ohm::walker_init_rec(w, rec, F, M, (long long)j * S);
+        ohm::walker_init_rec(w, rec, F, M, (long long)j * Sr);
       } else {
-        ohm::walker_init(w, a, b, F, M, (long long)j * S, inv);
+        ohm::walker_init(w, a, b, F, M, (long long)j * Sr, inv);
       }
       const bool last = j == nseg - 1;
-      int mrem = last ? INT_MAX : S - 1;
+      int mrem = last ? INT_MAX : Sr - 1;
       uint32_t mo = ohm::morton((uint32_t)(w.vx & 31), (uint32_t)(w.vy & 31), (uint32_t)(w.vz & 31));
       for (;;) {
         // the incrementally stepped Morton index must equal the recomputed one

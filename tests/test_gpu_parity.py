@@ -12,7 +12,7 @@ import torch
 import oracle
 from paper_2206_06079_gb300 import ohm, synth, workloads as W
 
-from .parity import compare_dense, compare_ndt, compare_query
+from .parity import assert_maps_identical, compare_dense, compare_ndt, compare_query
 
 pytestmark = pytest.mark.gpu
 
@@ -364,3 +364,25 @@ def test_status_async_reports_each_step_without_waiting():
     assert int(st[2]) == 0  # cleared by the sync
     om.integrate(*small.numpy())
     compare_dense(gm, om)
+
+
+def test_async_host_inputs_back_to_back():
+    """Scans submitted from pinned host memory without waiting (two staging
+    slots filled on the map's copy stream) give the map built from device
+    inputs, bit for bit; pageable inputs too."""
+    p = W.tunnel_params(layers=W.OCC | W.NDT | W.COUNTS, max_rays=32768, max_range=20.0, max_regions=8192,
+                        max_ndt_regions=2048)
+    a, b = ohm.Map(**p), ohm.Map(**p)
+    scans = [synth.tunnel_scan(i, beams=32, azimuths=1024, max_range=20.0) for i in range(6)]
+    stream = torch.cuda.Stream()
+    for i, r in enumerate(scans):
+        o, e, f = r.origins, r.endpoints, r.flags
+        if i % 3 != 2:
+            o, e, f = o.pin_memory(), e.pin_memory(), f.pin_memory()
+        with torch.cuda.stream(stream):
+            a.integrate(o, e, f, stream=stream, sync=False)
+    a.sync(stream)
+    for r in scans:
+        b.integrate(r.origins.cuda(), r.endpoints.cuda(), r.flags.cuda())
+    assert_maps_identical(a, b)
+
