@@ -124,24 +124,33 @@ def _traffic_per_launch(rays_per_scan):
     return per_ray * rays_per_scan
 
 
-def _max_over_ranks(x, ws):
+def _reduce_over_ranks(x, ws, op):
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def _max_over_ranks(x, ws):
+    import torch.distributed as dist
+    return _reduce_over_ranks(x, ws, dist.ReduceOp.MAX)
 
 
 def _sum_over_ranks(x, ws):
-    if ws == 1:
-        return x
-    import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _reduce_over_ranks(x, ws, dist.ReduceOp.SUM)
+
+
+def whole_job(units, elapsed_ms, ws):
+    """Whole-job throughput of replicas: the units every rank processed over
+    the slowest rank's time.  Returns (total units, max ms, units per second)."""
+    max_ms = _max_over_ranks(elapsed_ms, ws)
+    total = _sum_over_ranks(float(units), ws)
+    return total, max_ms, total / (max_ms / 1e3)
 
 
 def _barrier(ws):
@@ -250,10 +259,8 @@ def run_ours(args):
                 stage_ms[name] = ms / nl
         gm.profile([])
 
-    max_ms = _max_over_ranks(elapsed_ms, ws)
-    total_rays = _sum_over_ranks(float(rays_per_scan * args.steps), ws)
+    total_rays, max_ms, value = whole_job(rays_per_scan * args.steps, elapsed_ms, ws)
     total_visits = _sum_over_ranks(float(visits), ws)
-    value = total_rays / (max_ms / 1e3)
 
     if args.profile_case:
         if rank == 0:
