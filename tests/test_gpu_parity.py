@@ -375,10 +375,12 @@ def test_async_host_inputs_back_to_back():
     a, b = ohm.Map(**p), ohm.Map(**p)
     scans = [synth.tunnel_scan(i, beams=32, azimuths=1024, max_range=20.0) for i in range(6)]
     stream = torch.cuda.Stream()
+    held = []  # inputs must stay valid until the stream has passed their call
     for i, r in enumerate(scans):
         o, e, f = r.origins, r.endpoints, r.flags
         if i % 3 != 2:
             o, e, f = o.pin_memory(), e.pin_memory(), f.pin_memory()
+        held.append((o, e, f))
         with torch.cuda.stream(stream):
             a.integrate(o, e, f, stream=stream, sync=False)
     a.sync(stream)
