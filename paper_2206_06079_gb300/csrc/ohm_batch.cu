@@ -104,7 +104,7 @@ __global__ void k_batch_begin(const BatchDesc* desc, const BatchStep* step) {
   if (i < desc->n_maps) begin_call(desc->maps[i], batch_args(step, i));
 }
 
-__global__ void __launch_bounds__(kBlock) k_batch_prepare(const BatchDesc* desc, const BatchStep* step, int tsdf) {
+__global__ void __launch_bounds__(kBlock, OHM_PREPARE_MIN_BLOCKS) k_batch_prepare(const BatchDesc* desc, const BatchStep* step, int tsdf) {
   __shared__ BatchShared sh;
   batch_stage(sh, desc, step, kRaysPadded);
   const long long total = sh.pref[sh.n_maps];  // a multiple of 32: whole warps iterate together
