@@ -388,3 +388,23 @@ def test_async_host_inputs_back_to_back():
         b.integrate(r.origins.cuda(), r.endpoints.cuda(), r.flags.cuda())
     assert_maps_identical(a, b)
 
+
+
+@pytest.mark.parametrize("vs, F, origin", [(0.05, 8, (0.0, 0.0, 0.0)), (0.37, 12, (-3.1, 2.7, 0.55)),
+                                           (0.1, 20, (101.3, -57.9, 12.01)), (0.2, 16, (0.013, -0.007, 0.0))])
+def test_grid_parameters_and_map_origin(vs, F, origin):
+    """Other voxel sizes, fixed-point fractions and map origins (rays placed
+    around the origin, with face/edge/corner hits at the voxel pitch): every
+    layer bit-exact, NDT and query values within tolerance."""
+    p = W.room_params(layers=W.OCC | W.COUNTS | W.NDT | W.DECAY | W.MEAN, voxel_size=vs, frac_bits=F,
+                      map_origin=origin, max_regions=512, max_ndt_regions=512, max_rays=4096,
+                      max_range=30.0 * vs)
+    gm, om = _pair(p)
+    shift = torch.tensor(origin, dtype=torch.float32)
+    for scan in range(3):
+        r = synth.fuzz_rays(900 + scan + int(F), 3000, voxel=vs, extent=12 * vs)
+        rays = synth.RaySet(r.origins + shift, r.endpoints + shift, r.flags)
+        _integrate_both(gm, om, rays)
+    compare_dense(gm, om, path=True, mean=True)
+    compare_ndt(gm, om)
+    compare_query(gm, om, _sample_points(rays), ndt=True, path=True, mean=True)
