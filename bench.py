@@ -312,6 +312,11 @@ def run_ours(args):
     algo_bytes = 8.0 * visits_per_scan + 64.0 * rays_per_scan + 8.0 * segs_per_scan
     achieved = algo_bytes / walk_avg_s / 1e9
     traffic = _traffic_per_launch(rays_per_scan)
+    # the walk's second ceiling: L2 compare-and-swap throughput on random words
+    # (measured here with the library's probe, outside the timed region)
+    cas_per_scan = float(st1["atomics"])
+    cas_peak = ohm.probe_cas_rate(local, words=1 << 28, ops=1 << 26)
+    cas_achieved = cas_per_scan / walk_avg_s
 
     # ---- CPU baseline: the oracle, single thread, on a bounded sample of scans
     cpu = None
@@ -343,7 +348,11 @@ def run_ours(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic, "kernel": "k_walk_miss",
                          "algorithmic_bytes_per_launch": algo_bytes, "avg_launch_ms": walk_avg_s * 1e3,
-                         "peak_source": peak_src},
+                         "peak_source": peak_src,
+                         "atomics": {"achieved": cas_achieved, "peak": cas_peak, "unit": "CAS/s",
+                                     "frac": cas_achieved / cas_peak, "per_launch": cas_per_scan,
+                                     "peak_source": "ohm_probe_cas_rate: load + CAS of random 4-byte words of a "
+                                                    "1 GiB buffer, 4 in flight per thread, measured in this run"}},
             "clocks": clocks,
             "cpu_baseline": cpu,
         }

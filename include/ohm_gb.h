@@ -246,10 +246,22 @@ typedef struct {
   int64_t touched;       /* TSDF voxels updated by the last call */
   int64_t total_visits;  /* voxel visits of every call since the map was created */
   int64_t launches;      /* kernels this map has launched since it was created */
+  int64_t atomics;       /* log-odds compare-and-swap operations the miss walk of the last
+                            single-map call issued on first attempt (retries after a lost
+                            race are not counted; 0 after a batched step) */
 } ohm_call_stats;
 
 /* Statistics of the last completed integrate call (synchronises `stream`). */
 ohm_status ohm_map_stats(ohm_map* map, ohm_call_stats* out, void* stream);
+
+/* Throughput of 32-bit compare-and-swap on random words of a `words`-word
+ * device buffer (words a power of two, 2^10..2^32), the pattern of the miss
+ * walk's log-odds updates: per operation a load of the word, then a CAS of it,
+ * four operations in flight per thread, 4 blocks of 256 threads per SM.
+ * Runs about `ops` operations on `device` (allocating and freeing the buffer)
+ * and writes operations per second; the ceiling the walk's atomic rate is
+ * reported against.  The paper has no counterpart.  Synchronous. */
+ohm_status ohm_probe_cas_rate(int32_t device, int64_t words, int64_t ops, double* ops_per_second);
 
 /* Kernel stages of an integrate call, for per-stage GPU timing. */
 typedef enum {

@@ -141,7 +141,8 @@ __global__ void __launch_bounds__(kBlock, OHM_WALK_MIN_BLOCKS) k_batch_walk(cons
     const int mi = batch_find(sh, g);
     const DeviceMap& m = sh.maps[mi];
     const long long si = g - sh.pref[mi];
-    walk_segment_any(m, si);
+    unsigned int cas = 0;  // not attributed per map in a batched step
+    walk_segment_any(m, si, cas);
   }
 }
 

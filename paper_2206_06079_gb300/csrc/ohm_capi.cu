@@ -324,6 +324,18 @@ ohm_status ohm_map_sync(ohm_map* map, void* stream) {
   return status_from_bits(bits);
 }
 
+ohm_status ohm_probe_cas_rate(int32_t device, int64_t words, int64_t ops, double* ops_per_second) {
+  if (!ops_per_second) return fail(OHM_ERR_INVALID, "probe_cas_rate: NULL output");
+  if (words < 1024 || words > (1LL << 32) || (words & (words - 1)))
+    return fail(OHM_ERR_INVALID, "probe_cas_rate: words must be a power of two in [2^10, 2^32]");
+  if (ops < 1) return fail(OHM_ERR_INVALID, "probe_cas_rate: ops < 1");
+  DeviceGuard guard(device);
+  if (!guard.ok) return fail(OHM_ERR_CUDA, "probe_cas_rate: cannot select device");
+  cudaError_t e = ohm::probe_cas_rate(device, words, ops, ops_per_second);
+  if (e != cudaSuccess) return cuda_fail(e, "probe_cas_rate");
+  return OHM_OK;
+}
+
 ohm_status ohm_map_status_async(ohm_map* map, int32_t* status, void* stream) {
   if (!map || !status) return fail(OHM_ERR_INVALID, "status_async: NULL argument");
   if (is_device_pointer(status)) return fail(OHM_ERR_INVALID, "status_async: status must be host memory");
@@ -504,6 +516,7 @@ ohm_status ohm_map_stats(ohm_map* map, ohm_call_stats* out, void* stream) {
   out->ndt_regions = map->h_count[1];
   out->total_visits = (int64_t)map->h_calls->total_visits;
   out->launches = map->launches;
+  out->atomics = (int64_t)map->h_calls->atomics;
   return OHM_OK;
 }
 

@@ -121,6 +121,7 @@ struct CallCounters {
   long long origin_q[3];            // the call's shared sensor origin, quantised (one origin only)
   int32_t origin_ok;                // 1 if origin_q is valid
   int32_t pad2;
+  unsigned long long atomics;       // log-odds CAS operations the miss walk issued (single-map calls)
 };
 
 // Everything a kernel needs, passed by value.

@@ -53,6 +53,7 @@ namespace ohm {
 
 // Enqueue every kernel of one integrate call on `stream`.
 cudaError_t launch_integrate(ohm_map* map, const CallArgs& args, cudaStream_t stream);
+cudaError_t probe_cas_rate(int device, long long words, long long ops, double* rate);
 cudaError_t launch_query(ohm_map* map, const float* points, long long n, float* occupancy, uint8_t* known, float* ndt,
                          float* tsdf, uint32_t* counts, unsigned long long* path_sum, float* mean,
                          cudaStream_t stream);

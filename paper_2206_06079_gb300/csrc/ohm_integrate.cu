@@ -39,7 +39,11 @@ template <bool kOcc, bool kCounts, bool kDecay>
 __global__ void __launch_bounds__(kBlock, OHM_WALK_MIN_BLOCKS) k_walk_miss(DeviceMap m) {
   if (latched(m)) return;
   const long long nseg = (long long)m.calls->segments;
-  OHM_GRID_STRIDE(si, nseg) walk_segment<kOcc, kCounts, kDecay>(m, si);
+  unsigned int cas = 0;
+  OHM_GRID_STRIDE(si, nseg) walk_segment<kOcc, kCounts, kDecay>(m, si, cas);
+  // every thread gets here: one atomic per warp for the call's CAS count
+  cas = __reduce_add_sync(0xffffffffu, cas);
+  if ((threadIdx.x & 31) == 0 && cas) atomicAdd(&m.calls->atomics, (unsigned long long)cas);
 }
 
 template <bool kOcc, bool kCounts, bool kNdt>
@@ -267,6 +271,60 @@ cudaError_t launch_integrate(ohm_map* map, const CallArgs& args, cudaStream_t st
   }
   OHM_LAUNCH(OHM_STAGE_END, k_end<<<grid, kBlock, 0, stream>>>(m));
   return cudaGetLastError();
+}
+
+// 64-bit finaliser of SplitMix64 (Steele, Lea, Flood 2014), a published mixer.
+__device__ __forceinline__ unsigned long long splitmix64_mix(unsigned long long z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+  return z ^ (z >> 31);
+}
+
+// Throughput probe: per round, four random words are loaded, then each is
+// compare-and-swapped to its value + 1.
+__global__ void __launch_bounds__(kBlock, 4) k_probe_cas(unsigned int* buf, unsigned long long mask, int rounds) {
+  const unsigned long long threads = (unsigned long long)gridDim.x * blockDim.x;
+  const unsigned long long t = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (int r = 0; r < rounds; ++r) {
+    unsigned long long a[4];
+    unsigned int old[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) a[j] = splitmix64_mix((unsigned long long)r * threads * 4 + t * 4 + j) & mask;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) old[j] = buf[a[j]];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) atomicCAS(buf + a[j], old[j], old[j] + 1u);
+  }
+}
+
+cudaError_t probe_cas_rate(int device, long long words, long long ops, double* rate) {
+  int sms = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  if (e != cudaSuccess) return e;
+  const unsigned long long threads = (unsigned long long)sms * 4 * kBlock;
+  int rounds = (int)(ops / (long long)(threads * 4));
+  if (rounds < 1) rounds = 1;
+  unsigned int* buf = nullptr;
+  e = cudaMalloc(reinterpret_cast<void**>(&buf), sizeof(unsigned int) * (size_t)words);
+  if (e != cudaSuccess) return e;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  e = cudaMemset(buf, 0, sizeof(unsigned int) * (size_t)words);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) {
+    k_probe_cas<<<sms * 4, kBlock>>>(buf, (unsigned long long)words - 1, rounds);  // warm-up
+    cudaEventRecord(e0);
+    k_probe_cas<<<sms * 4, kBlock>>>(buf, (unsigned long long)words - 1, rounds);
+    cudaEventRecord(e1);
+    e = cudaEventSynchronize(e1);
+  }
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (e == cudaSuccess) *rate = (double)threads * 4.0 * rounds / (ms * 1e-3);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(buf);
+  return e;
 }
 
 cudaError_t launch_query(ohm_map* map, const float* points, long long n, float* occupancy, uint8_t* known, float* ndt,

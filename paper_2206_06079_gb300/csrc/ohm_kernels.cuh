@@ -169,6 +169,7 @@ __device__ __forceinline__ void begin_call(const DeviceMap& m, const CallArgs& a
   m.calls->touched = 0;
   m.calls->mean_touched = 0;
   m.calls->restores = 0;
+  m.calls->atomics = 0;
   m.calls->rays = (unsigned long long)n;
   // a shared sensor origin is quantised once for the whole call
   bool ok = false;
@@ -330,7 +331,7 @@ __device__ __forceinline__ unsigned long long decay_position(long long dist, int
 }
 
 template <bool kOcc, bool kCounts, bool kDecay>
-__device__ __forceinline__ void walk_segment(const DeviceMap& m, long long si) {
+__device__ __forceinline__ void walk_segment(const DeviceMap& m, long long si, unsigned int& cas) {
   const int F = m.frac_bits;
   const float miss = m.miss;
   const int2 sg = m.segs[si];
@@ -421,6 +422,7 @@ __device__ __forceinline__ void walk_segment(const DeviceMap& m, long long si) {
         const unsigned int nb = __float_as_uint(fminf(fmaxf(__fadd_rn(l0, miss), m.l_min), m.l_max));
         if (nb == old[j]) continue;
         prev[j] = atomicCAS(base + off[j], old[j], nb);
+        ++cas;
       }
 #pragma unroll
       for (int j = 0; j < kWalkBatch; ++j) {
@@ -439,16 +441,16 @@ __device__ __forceinline__ void walk_segment(const DeviceMap& m, long long si) {
 }
 
 // Miss-phase walk of one segment with the map's layers chosen at run time.
-__device__ __forceinline__ void walk_segment_any(const DeviceMap& m, long long si) {
+__device__ __forceinline__ void walk_segment_any(const DeviceMap& m, long long si, unsigned int& cas) {
   const int sel = ((m.layers & kLayerOcc) ? 4 : 0) | ((m.layers & kLayerCounts) ? 2 : 0) | ((m.layers & kLayerDecay) ? 1 : 0);
   switch (sel) {
-    case 7: walk_segment<true, true, true>(m, si); break;
-    case 6: walk_segment<true, true, false>(m, si); break;
-    case 5: walk_segment<true, false, true>(m, si); break;
-    case 4: walk_segment<true, false, false>(m, si); break;
-    case 3: walk_segment<false, true, true>(m, si); break;
-    case 2: walk_segment<false, true, false>(m, si); break;
-    case 1: walk_segment<false, false, true>(m, si); break;
+    case 7: walk_segment<true, true, true>(m, si, cas); break;
+    case 6: walk_segment<true, true, false>(m, si, cas); break;
+    case 5: walk_segment<true, false, true>(m, si, cas); break;
+    case 4: walk_segment<true, false, false>(m, si, cas); break;
+    case 3: walk_segment<false, true, true>(m, si, cas); break;
+    case 2: walk_segment<false, true, false>(m, si, cas); break;
+    case 1: walk_segment<false, false, true>(m, si, cas); break;
     default: break;
   }
 }

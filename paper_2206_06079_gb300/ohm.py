@@ -26,7 +26,7 @@ _STATUS_NAMES = {ERR_INVALID: "invalid argument", ERR_CAPACITY: "capacity", ERR_
                  ERR_PROBE_LIMIT: "hash probe limit", ERR_UNSUPPORTED: "unsupported", ERR_EVICTED: "evicted"}
 
 # Every symbol include/ohm_gb.h declares.
-EXPORTED = ["ohm_map_create", "ohm_map_destroy", "ohm_integrate_rays", "ohm_integrate_rays_async", "ohm_map_sync", "ohm_map_status_async",
+EXPORTED = ["ohm_map_create", "ohm_map_destroy", "ohm_integrate_rays", "ohm_integrate_rays_async", "ohm_map_sync", "ohm_map_status_async", "ohm_probe_cas_rate",
             "ohm_query_voxels", "ohm_map_region_count", "ohm_map_export", "ohm_map_stats", "ohm_map_profile",
             "ohm_map_profile_read", "ohm_last_error", "ohm_count_rays_noalloc", "ohm_batch_create",
             "ohm_batch_destroy", "ohm_batch_tune", "ohm_batch_integrate", "ohm_batch_sync", "ohm_batch_stats",
@@ -75,7 +75,7 @@ class MapParams(ctypes.Structure):
 
 class CallStats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in ("rays", "segments", "visits", "regions", "ndt_regions", "touched",
-                                              "total_visits", "launches")]
+                                              "total_visits", "launches", "atomics")]
 
 
 class CountGrid(ctypes.Structure):
@@ -116,6 +116,8 @@ def load_library(path: str = LIB_PATH):
     lib.ohm_map_sync.argtypes = [vp, vp]
     lib.ohm_map_status_async.restype = st
     lib.ohm_map_status_async.argtypes = [vp, p, vp]
+    lib.ohm_probe_cas_rate.restype = st
+    lib.ohm_probe_cas_rate.argtypes = [ctypes.c_int32, i64, i64, ctypes.POINTER(ctypes.c_double)]
     lib.ohm_query_voxels.restype = st
     lib.ohm_query_voxels.argtypes = [vp, p, i64, p, p, p, p, p, p, p, vp]
     lib.ohm_map_region_count.restype = st
@@ -412,6 +414,14 @@ class Map:
                                              _ptr(out.get("path_sum")), _ptr(out.get("mean")),
                                              _stream_handle(stream)))
         return out
+
+
+def probe_cas_rate(device=0, words=1 << 28, ops=1 << 26) -> float:
+    """Random-word compare-and-swap operations per second on `device` (the
+    miss walk's access pattern; see ohm_probe_cas_rate)."""
+    r = ctypes.c_double()
+    _check(load_library().ohm_probe_cas_rate(int(device), int(words), int(ops), ctypes.byref(r)))
+    return float(r.value)
 
 
 def count_rays_noalloc(grid: dict, origins, endpoints, flags, hits, misses, stream=None):

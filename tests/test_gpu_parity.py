@@ -408,3 +408,20 @@ def test_grid_parameters_and_map_origin(vs, F, origin):
     compare_dense(gm, om, path=True, mean=True)
     compare_ndt(gm, om)
     compare_query(gm, om, _sample_points(rays), ndt=True, path=True, mean=True)
+
+
+def test_cas_count_and_probe():
+    """The walk reports the log-odds CAS operations it issued: at least one
+    per voxel whose value a call changed, none for a repeated saturated ray;
+    the CAS-rate probe returns a positive rate."""
+    p = W.room_params(layers=W.OCC | W.COUNTS, max_rays=64)
+    gm = ohm.Map(**p)
+    o = np.array([[0.05, 0.05, 0.05]], np.float32)
+    e = np.array([[0.95, 0.05, 0.05]], np.float32)
+    gm.integrate(o, e)
+    assert gm.stats()["atomics"] >= 9  # nine voxels take their first miss
+    for _ in range(6):
+        gm.integrate(o, e)
+    assert gm.stats()["atomics"] == 0  # misses now leave l_min unchanged: no CAS
+    assert ohm.probe_cas_rate(0, words=1 << 20, ops=1 << 20) > 0
+
