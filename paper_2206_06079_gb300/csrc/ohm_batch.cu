@@ -279,7 +279,7 @@ cudaError_t enqueue_step(ohm_batch* b, cudaStream_t s, int* count) {
     ++n;
   }
   if (b->any_occ) {
-    k_batch_walk<<<grid, kBlock, 0, s>>>(b->d_desc, b->d_step);
+    k_batch_walk<<<grid * OHM_WALK_OVERSUBSCRIBE, kBlock, 0, s>>>(b->d_desc, b->d_step);  // oversubscribed like k_walk_miss
     ++n;
   }
   if (b->any_occ || b->any_ndt || b->any_mean) {

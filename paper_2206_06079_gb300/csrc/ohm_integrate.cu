@@ -229,6 +229,10 @@ cudaError_t launch_integrate(ohm_map* map, const CallArgs& args, cudaStream_t st
   const bool occ_like = occ || cnt || ndt || mean || (m.layers & kLayerDecay);
   const long long n = args.n;
   const int grid = map->walk_blocks;
+  // the walk's grid-stride loop runs on OHM_WALK_OVERSUBSCRIBE times the
+  // resident blocks: a block whose segments took longer holds its SM while
+  // blocks that finished early are replaced by new ones (no long tail)
+  const int wgrid = grid * OHM_WALK_OVERSUBSCRIBE;
   const long long per_ray_blocks = blocks_for(n) > 0 ? blocks_for(n) : 1;
   const int ray_grid = (int)(per_ray_blocks < grid ? per_ray_blocks : grid);
   const unsigned prb = (unsigned)per_ray_blocks;
@@ -242,13 +246,13 @@ cudaError_t launch_integrate(ohm_map* map, const CallArgs& args, cudaStream_t st
   if (occ || cnt || dec) {
     const int sel = (occ ? 4 : 0) | (cnt ? 2 : 0) | (dec ? 1 : 0);
     switch (sel) {
-      case 7: OHM_LAUNCH(OHM_STAGE_WALK, k_walk_miss<true, true, true><<<grid, kBlock, 0, stream>>>(m)); break;
-      case 6: OHM_LAUNCH(OHM_STAGE_WALK, k_walk_miss<true, true, false><<<grid, kBlock, 0, stream>>>(m)); break;
-      case 5: OHM_LAUNCH(OHM_STAGE_WALK, k_walk_miss<true, false, true><<<grid, kBlock, 0, stream>>>(m)); break;
-      case 4: OHM_LAUNCH(OHM_STAGE_WALK, k_walk_miss<true, false, false><<<grid, kBlock, 0, stream>>>(m)); break;
-      case 3: OHM_LAUNCH(OHM_STAGE_WALK, k_walk_miss<false, true, true><<<grid, kBlock, 0, stream>>>(m)); break;
-      case 2: OHM_LAUNCH(OHM_STAGE_WALK, k_walk_miss<false, true, false><<<grid, kBlock, 0, stream>>>(m)); break;
-      default: OHM_LAUNCH(OHM_STAGE_WALK, k_walk_miss<false, false, true><<<grid, kBlock, 0, stream>>>(m)); break;
+      case 7: OHM_LAUNCH(OHM_STAGE_WALK, k_walk_miss<true, true, true><<<wgrid, kBlock, 0, stream>>>(m)); break;
+      case 6: OHM_LAUNCH(OHM_STAGE_WALK, k_walk_miss<true, true, false><<<wgrid, kBlock, 0, stream>>>(m)); break;
+      case 5: OHM_LAUNCH(OHM_STAGE_WALK, k_walk_miss<true, false, true><<<wgrid, kBlock, 0, stream>>>(m)); break;
+      case 4: OHM_LAUNCH(OHM_STAGE_WALK, k_walk_miss<true, false, false><<<wgrid, kBlock, 0, stream>>>(m)); break;
+      case 3: OHM_LAUNCH(OHM_STAGE_WALK, k_walk_miss<false, true, true><<<wgrid, kBlock, 0, stream>>>(m)); break;
+      case 2: OHM_LAUNCH(OHM_STAGE_WALK, k_walk_miss<false, true, false><<<wgrid, kBlock, 0, stream>>>(m)); break;
+      default: OHM_LAUNCH(OHM_STAGE_WALK, k_walk_miss<false, false, true><<<wgrid, kBlock, 0, stream>>>(m)); break;
     }
   }
   if (occ || cnt || ndt || mean) {

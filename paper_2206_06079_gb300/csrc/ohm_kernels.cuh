@@ -152,6 +152,9 @@ static __device__ __noinline__ void logodds_retry(const DeviceMap& m, unsigned i
 constexpr int kWalkBatch = OHM_WALK_BATCH;
 // blocks of 256 threads per SM the prepare kernel is compiled for (4: a
 // 131,072-ray scan fits one wave on 152 SMs)
+#ifndef OHM_WALK_OVERSUBSCRIBE
+#define OHM_WALK_OVERSUBSCRIBE 8
+#endif
 #ifndef OHM_PREPARE_MIN_BLOCKS
 #define OHM_PREPARE_MIN_BLOCKS 4
 #endif
