@@ -143,15 +143,21 @@ static __device__ __noinline__ void logodds_retry(const DeviceMap& m, unsigned i
   atomicOr(m.status, kStatusCasLimit);
 }
 
+// Launch shapes (measured on GB300, tunnel scans of 131,072 rays):
+//  OHM_WALK_BATCH          voxels in flight per thread in the miss walk
+//  OHM_WALK_MIN_BLOCKS     blocks of 256 threads per SM the walk is compiled for
+//                          (5: 48 registers; 4 and 6 were slower)
+//  OHM_WALK_OVERSUBSCRIBE  the walk's grid-stride launch covers this many
+//                          times the resident blocks
+//  OHM_PREPARE_MIN_BLOCKS  blocks per SM of the prepare kernels (4: a
+//                          131,072-ray scan fits one wave on 152 SMs)
 #ifndef OHM_WALK_BATCH
 #define OHM_WALK_BATCH 4
 #endif
 #ifndef OHM_WALK_MIN_BLOCKS
-#define OHM_WALK_MIN_BLOCKS 4
+#define OHM_WALK_MIN_BLOCKS 5
 #endif
 constexpr int kWalkBatch = OHM_WALK_BATCH;
-// blocks of 256 threads per SM the prepare kernel is compiled for (4: a
-// 131,072-ray scan fits one wave on 152 SMs)
 #ifndef OHM_WALK_OVERSUBSCRIBE
 #define OHM_WALK_OVERSUBSCRIBE 8
 #endif
