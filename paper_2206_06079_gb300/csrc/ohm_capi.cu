@@ -45,6 +45,18 @@ bool is_device_pointer(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Device memory of another GPU than `dev` (the map's): rejected rather than
+// reached through peer access.
+bool on_other_device(const void* p, int dev) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice && a.device != dev;
+}
+
 template <typename T>
 cudaError_t alloc(T** p, size_t count, int fill) {
   *p = nullptr;
@@ -117,6 +129,9 @@ ohm_status enqueue_integrate(ohm_map* map, const float* origins, int64_t n_origi
   a.origins = origins;
   a.endpoints = endpoints;
   a.flags = flags;
+  if (on_other_device(origins, map->device) || on_other_device(endpoints, map->device) ||
+      on_other_device(flags, map->device))
+    return fail(OHM_ERR_INVALID, "integrate: inputs are on another device than the map");
   const bool host_o = !is_device_pointer(origins), host_e = !is_device_pointer(endpoints);
   const bool host_f = flags && !is_device_pointer(flags);
   cudaError_t e = cudaSuccess;
@@ -439,7 +454,8 @@ ohm_status ohm_query_voxels(ohm_map* map, const float* points, int64_t n, float*
   if (!points) return fail(OHM_ERR_INVALID, "query: points is NULL");
   void* outs[] = {occupancy, known, ndt, tsdf, counts, path_sum, mean};
   for (void* o : outs)
-    if (o && !is_device_pointer(o)) return fail(OHM_ERR_INVALID, "query: outputs must be device memory");
+    if (o && (!is_device_pointer(o) || on_other_device(o, map->device)))
+      return fail(OHM_ERR_INVALID, "query: outputs must be device memory of the map's device");
   if (path_sum && !(map->p.layers & OHM_LAYER_DECAY)) return fail(OHM_ERR_UNSUPPORTED, "query: map has no decay layer");
   if (mean && !(map->p.layers & OHM_LAYER_MEAN)) return fail(OHM_ERR_UNSUPPORTED, "query: map has no mean layer");
   if (ndt && !(map->p.layers & OHM_LAYER_NDT)) return fail(OHM_ERR_UNSUPPORTED, "query: map has no NDT layer");
@@ -449,6 +465,7 @@ ohm_status ohm_query_voxels(ohm_map* map, const float* points, int64_t n, float*
   const float* pts = points;
   float* staged = nullptr;
   cudaError_t e;
+  if (on_other_device(points, map->device)) return fail(OHM_ERR_INVALID, "query: points on another device than the map");
   if (!is_device_pointer(points)) {
     e = cudaMallocAsync(reinterpret_cast<void**>(&staged), sizeof(float) * 3 * n, s);
     if (e != cudaSuccess) return cuda_fail(e, "query: staging");
@@ -483,7 +500,8 @@ ohm_status ohm_map_export(ohm_map* map, int64_t first, int64_t count, int32_t* k
     return fail(OHM_ERR_INVALID, "export: region range outside the pool");
   void* outs[] = {keys, occupancy, counts, ndt, tsdf, path_sum, mean};
   for (void* o : outs)
-    if (o && !is_device_pointer(o)) return fail(OHM_ERR_INVALID, "export: outputs must be device memory");
+    if (o && (!is_device_pointer(o) || on_other_device(o, map->device)))
+      return fail(OHM_ERR_INVALID, "export: outputs must be device memory of the map's device");
   if (path_sum && !(map->p.layers & OHM_LAYER_DECAY)) return fail(OHM_ERR_UNSUPPORTED, "export: no decay layer");
   if (mean && !(map->p.layers & OHM_LAYER_MEAN)) return fail(OHM_ERR_UNSUPPORTED, "export: no mean layer");
   if (occupancy && !(map->p.layers & OHM_LAYER_OCCUPANCY)) return fail(OHM_ERR_UNSUPPORTED, "export: no occupancy layer");
