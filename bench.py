@@ -336,7 +336,7 @@ def run_ours(args):
             "data": "synthetic (seeded tunnel lidar scans generated on the device)",
             "config": {"workload": WORKLOAD, "rays_per_scan": rays_per_scan, "scans": SCANS,
                        "layers": "occupancy+ndt", "voxel_size_m": 0.1, "max_range_m": 50.0,
-                       "segment_target_voxel_steps": args.segment_steps or 10, "parallelism": "replicas" if ws > 1 else "single GPU",
+                       "segment_target_voxel_steps": args.segment_steps or 24, "parallelism": "replicas" if ws > 1 else "single GPU",
                        "l2": "map working set per scan (~7.7k 128 KB regions) exceeds the 129 MB L2; "
                              "each step integrates a different scan"},
             "voxel_updates_per_s": total_visits / (max_ms / 1e3),

@@ -91,7 +91,7 @@ typedef struct {
                               a ray whose walk takes N voxel steps, n of them along its dominant
                               axis, is split every max(1, round(segment_steps n / N)) (at most
                               65535) dominant-axis steps, so segments of rays in any direction
-                              are about equally long; 0 = 10 */
+                              are about equally long; 0 = 24 */
   int32_t device;          /* CUDA device ordinal */
   int32_t evict_when_full; /* nonzero: when ohm_integrate_rays finds the region or NDT pool full it
                               moves least recently used regions to host memory and repeats the call

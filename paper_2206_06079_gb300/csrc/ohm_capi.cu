@@ -178,7 +178,7 @@ ohm_status ohm_map_create(const ohm_map_params* params, ohm_map** out) {
   if (!params || !out) return fail(OHM_ERR_INVALID, "create: NULL argument");
   *out = nullptr;
   ohm_map_params p = *params;
-  if (p.segment_steps == 0) p.segment_steps = 10;
+  if (p.segment_steps == 0) p.segment_steps = 24;
   if (!(p.voxel_size > 0.0) || !std::isfinite(p.voxel_size)) return fail(OHM_ERR_INVALID, "create: voxel_size must be > 0");
   if (p.frac_bits < 8 || p.frac_bits > 20) return fail(OHM_ERR_INVALID, "create: frac_bits must be in [8, 20]");
   const uint32_t all = OHM_LAYER_OCCUPANCY | OHM_LAYER_NDT | OHM_LAYER_TSDF | OHM_LAYER_COUNTS | OHM_LAYER_DECAY | OHM_LAYER_MEAN;

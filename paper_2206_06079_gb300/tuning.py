@@ -13,7 +13,7 @@ import torch
 
 from . import ohm
 
-DEFAULT_SEGMENT_STEPS = (4, 6, 10, 16)
+DEFAULT_SEGMENT_STEPS = (6, 10, 16, 24)
 DEFAULT_WALK_BLOCKS = (2, 3, 4)
 
 
