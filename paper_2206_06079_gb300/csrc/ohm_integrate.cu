@@ -26,17 +26,20 @@ namespace ohm {
 __global__ void k_begin(DeviceMap m, CallArgs args) { begin_call(m, args); }
 
 __global__ void __launch_bounds__(kBlock, OHM_PREPARE_MIN_BLOCKS) k_prepare_occ(DeviceMap m, CallArgs args) {
+  chain_enter();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   prepare_occ_ray(m, args, i, i < args.n);
 }
 
 __global__ void __launch_bounds__(kBlock) k_ndt_alloc(DeviceMap m, long long n) {
+  chain_enter();
   if (latched(m)) return;
   OHM_GRID_STRIDE(i, n) ndt_alloc_ray(m, i);
 }
 
 template <bool kOcc, bool kCounts, bool kDecay>
 __global__ void __launch_bounds__(kBlock, OHM_WALK_MIN_BLOCKS) k_walk_miss(DeviceMap m) {
+  chain_enter();
   if (latched(m)) return;
   const long long nseg = (long long)m.calls->segments;
   unsigned int cas = 0;
@@ -48,34 +51,40 @@ __global__ void __launch_bounds__(kBlock, OHM_WALK_MIN_BLOCKS) k_walk_miss(Devic
 
 template <bool kOcc, bool kCounts, bool kNdt>
 __global__ void __launch_bounds__(kBlock) k_hits(DeviceMap m, long long n) {
+  chain_enter();
   if (latched(m)) return;
   OHM_GRID_STRIDE(i, n) hit_ray<kOcc, kCounts, kNdt>(m, i);
 }
 
 // Runs for failed calls too: it then only clears the per-call sums.
 __global__ void __launch_bounds__(kBlock) k_mean_apply(DeviceMap m) {
+  chain_enter();
   const bool apply = !latched(m);
   const long long nt = mean_touched_count(m);
   OHM_GRID_STRIDE(t, nt) mean_apply_one(m, t, apply);
 }
 
 __global__ void __launch_bounds__(kBlock) k_prepare_tsdf(DeviceMap m, CallArgs args) {
+  chain_enter();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   prepare_tsdf_ray(m, args, i, i < args.n);
 }
 
 __global__ void __launch_bounds__(kBlock) k_tsdf_walk(DeviceMap m, long long n) {
+  chain_enter();
   if (latched(m)) return;
   OHM_GRID_STRIDE(i, n) tsdf_walk_ray(m, i);
 }
 
 __global__ void __launch_bounds__(kBlock) k_tsdf_apply(DeviceMap m) {
+  chain_enter();
   if (latched(m)) return;
   const long long nt = touched_count(m);
   OHM_GRID_STRIDE(t, nt) tsdf_apply_one(m, t);
 }
 
 __global__ void k_end(DeviceMap m) {
+  chain_enter();
   if (!latched(m)) return;
   rollback_call(m, (long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
 }
@@ -211,6 +220,29 @@ int walk_blocks_per_sm() {
 
 static long long blocks_for(long long n) { return (n + kBlock - 1) / kBlock; }
 
+// Launch one kernel of the integrate chain with programmatic stream
+// serialisation: its blocks may be scheduled while the previous kernel of the
+// stream drains, and wait in chain_enter() until that kernel has completed.
+// Where the attribute is refused the kernel is launched the ordinary way.
+template <typename... K, typename... A>
+static void chained(void (*kernel)(K...), unsigned grid, cudaStream_t stream, A... args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kBlock);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = stream;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, kernel, args...) != cudaSuccess) {
+    (void)cudaGetLastError();
+    cfg.numAttrs = 0;
+    (void)cudaLaunchKernelEx(&cfg, kernel, args...);
+  }
+}
+
 // Launch one kernel as stage `stage`, with event timing when it is profiled.
 #define OHM_LAUNCH(stage, ...)                  \
   do {                                          \
@@ -238,42 +270,42 @@ cudaError_t launch_integrate(ohm_map* map, const CallArgs& args, cudaStream_t st
   const unsigned prb = (unsigned)per_ray_blocks;
   OHM_LAUNCH(OHM_STAGE_BEGIN, k_begin<<<1, 1, 0, stream>>>(m, args));
   if (occ_like) {
-    OHM_LAUNCH(OHM_STAGE_PREPARE, k_prepare_occ<<<prb, kBlock, 0, stream>>>(m, args));
-    if (ndt) OHM_LAUNCH(OHM_STAGE_NDT_ALLOC, k_ndt_alloc<<<ray_grid, kBlock, 0, stream>>>(m, n));
+    OHM_LAUNCH(OHM_STAGE_PREPARE, chained(k_prepare_occ, prb, stream, m, args));
+    if (ndt) OHM_LAUNCH(OHM_STAGE_NDT_ALLOC, chained(k_ndt_alloc, ray_grid, stream, m, n));
   }
-  if (tsdf) OHM_LAUNCH(OHM_STAGE_PREPARE_TSDF, k_prepare_tsdf<<<prb, kBlock, 0, stream>>>(m, args));
+  if (tsdf) OHM_LAUNCH(OHM_STAGE_PREPARE_TSDF, chained(k_prepare_tsdf, prb, stream, m, args));
   const bool dec = (m.layers & kLayerDecay) != 0;
   if (occ || cnt || dec) {
     const int sel = (occ ? 4 : 0) | (cnt ? 2 : 0) | (dec ? 1 : 0);
     switch (sel) {
-      case 7: OHM_LAUNCH(OHM_STAGE_WALK, k_walk_miss<true, true, true><<<wgrid, kBlock, 0, stream>>>(m)); break;
-      case 6: OHM_LAUNCH(OHM_STAGE_WALK, k_walk_miss<true, true, false><<<wgrid, kBlock, 0, stream>>>(m)); break;
-      case 5: OHM_LAUNCH(OHM_STAGE_WALK, k_walk_miss<true, false, true><<<wgrid, kBlock, 0, stream>>>(m)); break;
-      case 4: OHM_LAUNCH(OHM_STAGE_WALK, k_walk_miss<true, false, false><<<wgrid, kBlock, 0, stream>>>(m)); break;
-      case 3: OHM_LAUNCH(OHM_STAGE_WALK, k_walk_miss<false, true, true><<<wgrid, kBlock, 0, stream>>>(m)); break;
-      case 2: OHM_LAUNCH(OHM_STAGE_WALK, k_walk_miss<false, true, false><<<wgrid, kBlock, 0, stream>>>(m)); break;
-      default: OHM_LAUNCH(OHM_STAGE_WALK, k_walk_miss<false, false, true><<<wgrid, kBlock, 0, stream>>>(m)); break;
+      case 7: OHM_LAUNCH(OHM_STAGE_WALK, chained(k_walk_miss<true, true, true>, wgrid, stream, m)); break;
+      case 6: OHM_LAUNCH(OHM_STAGE_WALK, chained(k_walk_miss<true, true, false>, wgrid, stream, m)); break;
+      case 5: OHM_LAUNCH(OHM_STAGE_WALK, chained(k_walk_miss<true, false, true>, wgrid, stream, m)); break;
+      case 4: OHM_LAUNCH(OHM_STAGE_WALK, chained(k_walk_miss<true, false, false>, wgrid, stream, m)); break;
+      case 3: OHM_LAUNCH(OHM_STAGE_WALK, chained(k_walk_miss<false, true, true>, wgrid, stream, m)); break;
+      case 2: OHM_LAUNCH(OHM_STAGE_WALK, chained(k_walk_miss<false, true, false>, wgrid, stream, m)); break;
+      default: OHM_LAUNCH(OHM_STAGE_WALK, chained(k_walk_miss<false, false, true>, wgrid, stream, m)); break;
     }
   }
   if (occ || cnt || ndt || mean) {
     const int sel = (occ ? 4 : 0) | (cnt ? 2 : 0) | (ndt ? 1 : 0);
     switch (sel) {
-      case 7: OHM_LAUNCH(OHM_STAGE_HITS, k_hits<true, true, true><<<ray_grid, kBlock, 0, stream>>>(m, n)); break;
-      case 6: OHM_LAUNCH(OHM_STAGE_HITS, k_hits<true, true, false><<<ray_grid, kBlock, 0, stream>>>(m, n)); break;
-      case 5: OHM_LAUNCH(OHM_STAGE_HITS, k_hits<true, false, true><<<ray_grid, kBlock, 0, stream>>>(m, n)); break;
-      case 4: OHM_LAUNCH(OHM_STAGE_HITS, k_hits<true, false, false><<<ray_grid, kBlock, 0, stream>>>(m, n)); break;
-      case 3: OHM_LAUNCH(OHM_STAGE_HITS, k_hits<false, true, true><<<ray_grid, kBlock, 0, stream>>>(m, n)); break;
-      case 2: OHM_LAUNCH(OHM_STAGE_HITS, k_hits<false, true, false><<<ray_grid, kBlock, 0, stream>>>(m, n)); break;
-      case 1: OHM_LAUNCH(OHM_STAGE_HITS, k_hits<false, false, true><<<ray_grid, kBlock, 0, stream>>>(m, n)); break;
-      default: OHM_LAUNCH(OHM_STAGE_HITS, k_hits<false, false, false><<<ray_grid, kBlock, 0, stream>>>(m, n)); break;
+      case 7: OHM_LAUNCH(OHM_STAGE_HITS, chained(k_hits<true, true, true>, ray_grid, stream, m, n)); break;
+      case 6: OHM_LAUNCH(OHM_STAGE_HITS, chained(k_hits<true, true, false>, ray_grid, stream, m, n)); break;
+      case 5: OHM_LAUNCH(OHM_STAGE_HITS, chained(k_hits<true, false, true>, ray_grid, stream, m, n)); break;
+      case 4: OHM_LAUNCH(OHM_STAGE_HITS, chained(k_hits<true, false, false>, ray_grid, stream, m, n)); break;
+      case 3: OHM_LAUNCH(OHM_STAGE_HITS, chained(k_hits<false, true, true>, ray_grid, stream, m, n)); break;
+      case 2: OHM_LAUNCH(OHM_STAGE_HITS, chained(k_hits<false, true, false>, ray_grid, stream, m, n)); break;
+      case 1: OHM_LAUNCH(OHM_STAGE_HITS, chained(k_hits<false, false, true>, ray_grid, stream, m, n)); break;
+      default: OHM_LAUNCH(OHM_STAGE_HITS, chained(k_hits<false, false, false>, ray_grid, stream, m, n)); break;
     }
-    if (mean) OHM_LAUNCH(OHM_STAGE_MEAN_APPLY, k_mean_apply<<<ray_grid, kBlock, 0, stream>>>(m));
+    if (mean) OHM_LAUNCH(OHM_STAGE_MEAN_APPLY, chained(k_mean_apply, ray_grid, stream, m));
   }
   if (tsdf) {
-    OHM_LAUNCH(OHM_STAGE_TSDF_WALK, k_tsdf_walk<<<ray_grid, kBlock, 0, stream>>>(m, n));
-    OHM_LAUNCH(OHM_STAGE_TSDF_APPLY, k_tsdf_apply<<<grid, kBlock, 0, stream>>>(m));
+    OHM_LAUNCH(OHM_STAGE_TSDF_WALK, chained(k_tsdf_walk, ray_grid, stream, m, n));
+    OHM_LAUNCH(OHM_STAGE_TSDF_APPLY, chained(k_tsdf_apply, grid, stream, m));
   }
-  OHM_LAUNCH(OHM_STAGE_END, k_end<<<grid, kBlock, 0, stream>>>(m));
+  OHM_LAUNCH(OHM_STAGE_END, chained(k_end, grid, stream, m));
   return cudaGetLastError();
 }
 

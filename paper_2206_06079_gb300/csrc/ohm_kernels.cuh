@@ -14,6 +14,19 @@ constexpr int kBlock = 256;
 
 __device__ __forceinline__ bool latched(const DeviceMap& m) { return *(volatile int32_t*)m.status != 0; }
 
+// Programmatic dependent launch (sm_90 and later).  A kernel launched with
+// programmatic stream serialisation may be scheduled while the kernel before
+// it in the stream is still draining.  chain_enter() first waits until that
+// kernel has completed and its writes are visible (griddepcontrol.wait; a
+// no-op for an ordinary launch), then allows the next kernel of the stream to
+// be scheduled.  Called first thing by every kernel of the integrate chain, so
+// each body still runs strictly after its predecessor; only the launch
+// latency and the block scheduling overlap.
+__device__ __forceinline__ void chain_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Clamped log-odds update of one voxel (Eq. 2 with the clamp of Sec. II-B):
 // l <- min(max(l0 + delta, l_min), l_max), l0 = 0 for an unknown (NaN) voxel.
 // Concurrent updates of one voxel are serialised by compare-and-swap; within
