@@ -105,6 +105,7 @@ __global__ void k_batch_begin(const BatchDesc* desc, const BatchStep* step) {
 }
 
 __global__ void __launch_bounds__(kBlock, OHM_PREPARE_MIN_BLOCKS) k_batch_prepare(const BatchDesc* desc, const BatchStep* step, int tsdf) {
+  chain_enter();
   __shared__ BatchShared sh;
   batch_stage(sh, desc, step, kRaysPadded);
   const long long total = sh.pref[sh.n_maps];  // a multiple of 32: whole warps iterate together
@@ -123,6 +124,7 @@ __global__ void __launch_bounds__(kBlock, OHM_PREPARE_MIN_BLOCKS) k_batch_prepar
 }
 
 __global__ void __launch_bounds__(kBlock) k_batch_ndt_alloc(const BatchDesc* desc, const BatchStep* step) {
+  chain_enter();
   __shared__ BatchShared sh;
   batch_stage(sh, desc, step, kRays);
   const long long total = sh.pref[sh.n_maps];
@@ -134,6 +136,7 @@ __global__ void __launch_bounds__(kBlock) k_batch_ndt_alloc(const BatchDesc* des
 }
 
 __global__ void __launch_bounds__(kBlock, OHM_WALK_MIN_BLOCKS) k_batch_walk(const BatchDesc* desc, const BatchStep* step) {
+  chain_enter();
   __shared__ BatchShared sh;
   batch_stage(sh, desc, step, kSegments);
   const long long total = sh.pref[sh.n_maps];
@@ -147,6 +150,7 @@ __global__ void __launch_bounds__(kBlock, OHM_WALK_MIN_BLOCKS) k_batch_walk(cons
 }
 
 __global__ void __launch_bounds__(kBlock) k_batch_hits(const BatchDesc* desc, const BatchStep* step) {
+  chain_enter();
   __shared__ BatchShared sh;
   batch_stage(sh, desc, step, kRays);
   const long long total = sh.pref[sh.n_maps];
@@ -171,6 +175,7 @@ __global__ void __launch_bounds__(kBlock) k_batch_hits(const BatchDesc* desc, co
 }
 
 __global__ void __launch_bounds__(kBlock) k_batch_mean_apply(const BatchDesc* desc, const BatchStep* step) {
+  chain_enter();
   __shared__ BatchShared sh;
   batch_stage(sh, desc, step, kMeanTouched);
   const long long total = sh.pref[sh.n_maps];
@@ -182,6 +187,7 @@ __global__ void __launch_bounds__(kBlock) k_batch_mean_apply(const BatchDesc* de
 }
 
 __global__ void __launch_bounds__(kBlock) k_batch_tsdf_walk(const BatchDesc* desc, const BatchStep* step) {
+  chain_enter();
   __shared__ BatchShared sh;
   batch_stage(sh, desc, step, kRays);
   const long long total = sh.pref[sh.n_maps];
@@ -193,6 +199,7 @@ __global__ void __launch_bounds__(kBlock) k_batch_tsdf_walk(const BatchDesc* des
 }
 
 __global__ void __launch_bounds__(kBlock) k_batch_tsdf_apply(const BatchDesc* desc, const BatchStep* step) {
+  chain_enter();
   __shared__ BatchShared sh;
   batch_stage(sh, desc, step, kTouched);
   const long long total = sh.pref[sh.n_maps];
@@ -205,6 +212,7 @@ __global__ void __launch_bounds__(kBlock) k_batch_tsdf_apply(const BatchDesc* de
 
 // One group of blocks per map rolls back that map if its call failed.
 __global__ void k_batch_end(const BatchDesc* desc) {
+  chain_enter();
   const int per_map = gridDim.x / kMaxBatchMaps;
   const int mi = blockIdx.x / per_map;
   if (mi >= desc->n_maps) return;
@@ -267,35 +275,35 @@ cudaError_t enqueue_step(ohm_batch* b, cudaStream_t s, int* count) {
   k_batch_begin<<<1, kMaxBatchMaps, 0, s>>>(b->d_desc, b->d_step);
   int n = 1;
   if (b->any_occ || b->any_ndt || b->any_mean) {
-    k_batch_prepare<<<ray_grid, kBlock, 0, s>>>(b->d_desc, b->d_step, 0);
+    launch_chained(k_batch_prepare, ray_grid, s, b->d_desc, b->d_step, 0);
     ++n;
     if (b->any_ndt) {
-      k_batch_ndt_alloc<<<ray_grid, kBlock, 0, s>>>(b->d_desc, b->d_step);
+      launch_chained(k_batch_ndt_alloc, ray_grid, s, b->d_desc, b->d_step);
       ++n;
     }
   }
   if (b->any_tsdf) {
-    k_batch_prepare<<<ray_grid, kBlock, 0, s>>>(b->d_desc, b->d_step, 1);
+    launch_chained(k_batch_prepare, ray_grid, s, b->d_desc, b->d_step, 1);
     ++n;
   }
   if (b->any_occ) {
-    k_batch_walk<<<grid * OHM_WALK_OVERSUBSCRIBE, kBlock, 0, s>>>(b->d_desc, b->d_step);  // oversubscribed like k_walk_miss
+    launch_chained(k_batch_walk, grid * OHM_WALK_OVERSUBSCRIBE, s, b->d_desc, b->d_step);  // oversubscribed like k_walk_miss
     ++n;
   }
   if (b->any_occ || b->any_ndt || b->any_mean) {
-    k_batch_hits<<<ray_grid, kBlock, 0, s>>>(b->d_desc, b->d_step);
+    launch_chained(k_batch_hits, ray_grid, s, b->d_desc, b->d_step);
     ++n;
   }
   if (b->any_mean) {
-    k_batch_mean_apply<<<ray_grid, kBlock, 0, s>>>(b->d_desc, b->d_step);
+    launch_chained(k_batch_mean_apply, ray_grid, s, b->d_desc, b->d_step);
     ++n;
   }
   if (b->any_tsdf) {
-    k_batch_tsdf_walk<<<ray_grid, kBlock, 0, s>>>(b->d_desc, b->d_step);
-    k_batch_tsdf_apply<<<ray_grid, kBlock, 0, s>>>(b->d_desc, b->d_step);
+    launch_chained(k_batch_tsdf_walk, ray_grid, s, b->d_desc, b->d_step);
+    launch_chained(k_batch_tsdf_apply, ray_grid, s, b->d_desc, b->d_step);
     n += 2;
   }
-  k_batch_end<<<kMaxBatchMaps * 8, kBlock, 0, s>>>(b->d_desc);
+  launch_chained(k_batch_end, kMaxBatchMaps * 8, s, b->d_desc);
   ++n;
   *count = n;
   return cudaGetLastError();

@@ -220,28 +220,6 @@ int walk_blocks_per_sm() {
 
 static long long blocks_for(long long n) { return (n + kBlock - 1) / kBlock; }
 
-// Launch one kernel of the integrate chain with programmatic stream
-// serialisation: its blocks may be scheduled while the previous kernel of the
-// stream drains, and wait in chain_enter() until that kernel has completed.
-// Where the attribute is refused the kernel is launched the ordinary way.
-template <typename... K, typename... A>
-static void chained(void (*kernel)(K...), unsigned grid, cudaStream_t stream, A... args) {
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(kBlock);
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = stream;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  if (cudaLaunchKernelEx(&cfg, kernel, args...) != cudaSuccess) {
-    (void)cudaGetLastError();
-    cfg.numAttrs = 0;
-    (void)cudaLaunchKernelEx(&cfg, kernel, args...);
-  }
-}
 
 // Launch one kernel as stage `stage`, with event timing when it is profiled.
 #define OHM_LAUNCH(stage, ...)                  \
@@ -270,42 +248,42 @@ cudaError_t launch_integrate(ohm_map* map, const CallArgs& args, cudaStream_t st
   const unsigned prb = (unsigned)per_ray_blocks;
   OHM_LAUNCH(OHM_STAGE_BEGIN, k_begin<<<1, 1, 0, stream>>>(m, args));
   if (occ_like) {
-    OHM_LAUNCH(OHM_STAGE_PREPARE, chained(k_prepare_occ, prb, stream, m, args));
-    if (ndt) OHM_LAUNCH(OHM_STAGE_NDT_ALLOC, chained(k_ndt_alloc, ray_grid, stream, m, n));
+    OHM_LAUNCH(OHM_STAGE_PREPARE, launch_chained(k_prepare_occ, prb, stream, m, args));
+    if (ndt) OHM_LAUNCH(OHM_STAGE_NDT_ALLOC, launch_chained(k_ndt_alloc, ray_grid, stream, m, n));
   }
-  if (tsdf) OHM_LAUNCH(OHM_STAGE_PREPARE_TSDF, chained(k_prepare_tsdf, prb, stream, m, args));
+  if (tsdf) OHM_LAUNCH(OHM_STAGE_PREPARE_TSDF, launch_chained(k_prepare_tsdf, prb, stream, m, args));
   const bool dec = (m.layers & kLayerDecay) != 0;
   if (occ || cnt || dec) {
     const int sel = (occ ? 4 : 0) | (cnt ? 2 : 0) | (dec ? 1 : 0);
     switch (sel) {
-      case 7: OHM_LAUNCH(OHM_STAGE_WALK, chained(k_walk_miss<true, true, true>, wgrid, stream, m)); break;
-      case 6: OHM_LAUNCH(OHM_STAGE_WALK, chained(k_walk_miss<true, true, false>, wgrid, stream, m)); break;
-      case 5: OHM_LAUNCH(OHM_STAGE_WALK, chained(k_walk_miss<true, false, true>, wgrid, stream, m)); break;
-      case 4: OHM_LAUNCH(OHM_STAGE_WALK, chained(k_walk_miss<true, false, false>, wgrid, stream, m)); break;
-      case 3: OHM_LAUNCH(OHM_STAGE_WALK, chained(k_walk_miss<false, true, true>, wgrid, stream, m)); break;
-      case 2: OHM_LAUNCH(OHM_STAGE_WALK, chained(k_walk_miss<false, true, false>, wgrid, stream, m)); break;
-      default: OHM_LAUNCH(OHM_STAGE_WALK, chained(k_walk_miss<false, false, true>, wgrid, stream, m)); break;
+      case 7: OHM_LAUNCH(OHM_STAGE_WALK, launch_chained(k_walk_miss<true, true, true>, wgrid, stream, m)); break;
+      case 6: OHM_LAUNCH(OHM_STAGE_WALK, launch_chained(k_walk_miss<true, true, false>, wgrid, stream, m)); break;
+      case 5: OHM_LAUNCH(OHM_STAGE_WALK, launch_chained(k_walk_miss<true, false, true>, wgrid, stream, m)); break;
+      case 4: OHM_LAUNCH(OHM_STAGE_WALK, launch_chained(k_walk_miss<true, false, false>, wgrid, stream, m)); break;
+      case 3: OHM_LAUNCH(OHM_STAGE_WALK, launch_chained(k_walk_miss<false, true, true>, wgrid, stream, m)); break;
+      case 2: OHM_LAUNCH(OHM_STAGE_WALK, launch_chained(k_walk_miss<false, true, false>, wgrid, stream, m)); break;
+      default: OHM_LAUNCH(OHM_STAGE_WALK, launch_chained(k_walk_miss<false, false, true>, wgrid, stream, m)); break;
     }
   }
   if (occ || cnt || ndt || mean) {
     const int sel = (occ ? 4 : 0) | (cnt ? 2 : 0) | (ndt ? 1 : 0);
     switch (sel) {
-      case 7: OHM_LAUNCH(OHM_STAGE_HITS, chained(k_hits<true, true, true>, ray_grid, stream, m, n)); break;
-      case 6: OHM_LAUNCH(OHM_STAGE_HITS, chained(k_hits<true, true, false>, ray_grid, stream, m, n)); break;
-      case 5: OHM_LAUNCH(OHM_STAGE_HITS, chained(k_hits<true, false, true>, ray_grid, stream, m, n)); break;
-      case 4: OHM_LAUNCH(OHM_STAGE_HITS, chained(k_hits<true, false, false>, ray_grid, stream, m, n)); break;
-      case 3: OHM_LAUNCH(OHM_STAGE_HITS, chained(k_hits<false, true, true>, ray_grid, stream, m, n)); break;
-      case 2: OHM_LAUNCH(OHM_STAGE_HITS, chained(k_hits<false, true, false>, ray_grid, stream, m, n)); break;
-      case 1: OHM_LAUNCH(OHM_STAGE_HITS, chained(k_hits<false, false, true>, ray_grid, stream, m, n)); break;
-      default: OHM_LAUNCH(OHM_STAGE_HITS, chained(k_hits<false, false, false>, ray_grid, stream, m, n)); break;
+      case 7: OHM_LAUNCH(OHM_STAGE_HITS, launch_chained(k_hits<true, true, true>, ray_grid, stream, m, n)); break;
+      case 6: OHM_LAUNCH(OHM_STAGE_HITS, launch_chained(k_hits<true, true, false>, ray_grid, stream, m, n)); break;
+      case 5: OHM_LAUNCH(OHM_STAGE_HITS, launch_chained(k_hits<true, false, true>, ray_grid, stream, m, n)); break;
+      case 4: OHM_LAUNCH(OHM_STAGE_HITS, launch_chained(k_hits<true, false, false>, ray_grid, stream, m, n)); break;
+      case 3: OHM_LAUNCH(OHM_STAGE_HITS, launch_chained(k_hits<false, true, true>, ray_grid, stream, m, n)); break;
+      case 2: OHM_LAUNCH(OHM_STAGE_HITS, launch_chained(k_hits<false, true, false>, ray_grid, stream, m, n)); break;
+      case 1: OHM_LAUNCH(OHM_STAGE_HITS, launch_chained(k_hits<false, false, true>, ray_grid, stream, m, n)); break;
+      default: OHM_LAUNCH(OHM_STAGE_HITS, launch_chained(k_hits<false, false, false>, ray_grid, stream, m, n)); break;
     }
-    if (mean) OHM_LAUNCH(OHM_STAGE_MEAN_APPLY, chained(k_mean_apply, ray_grid, stream, m));
+    if (mean) OHM_LAUNCH(OHM_STAGE_MEAN_APPLY, launch_chained(k_mean_apply, ray_grid, stream, m));
   }
   if (tsdf) {
-    OHM_LAUNCH(OHM_STAGE_TSDF_WALK, chained(k_tsdf_walk, ray_grid, stream, m, n));
-    OHM_LAUNCH(OHM_STAGE_TSDF_APPLY, chained(k_tsdf_apply, grid, stream, m));
+    OHM_LAUNCH(OHM_STAGE_TSDF_WALK, launch_chained(k_tsdf_walk, ray_grid, stream, m, n));
+    OHM_LAUNCH(OHM_STAGE_TSDF_APPLY, launch_chained(k_tsdf_apply, grid, stream, m));
   }
-  OHM_LAUNCH(OHM_STAGE_END, chained(k_end, grid, stream, m));
+  OHM_LAUNCH(OHM_STAGE_END, launch_chained(k_end, grid, stream, m));
   return cudaGetLastError();
 }
 

@@ -19,12 +19,35 @@ __device__ __forceinline__ bool latched(const DeviceMap& m) { return *(volatile 
 // it in the stream is still draining.  chain_enter() first waits until that
 // kernel has completed and its writes are visible (griddepcontrol.wait; a
 // no-op for an ordinary launch), then allows the next kernel of the stream to
-// be scheduled.  Called first thing by every kernel of the integrate chain, so
-// each body still runs strictly after its predecessor; only the launch
-// latency and the block scheduling overlap.
+// be scheduled.  Called first thing by every kernel of an integrate chain
+// (single map or batched), so each body still runs strictly after its
+// predecessor; only the launch latency and the block scheduling overlap.
 __device__ __forceinline__ void chain_enter() {
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Host side: launch one kernel of a chain with programmatic stream
+// serialisation: its blocks may be scheduled while the previous kernel of the
+// stream drains, and wait in chain_enter() until that kernel has completed.
+// Where the attribute is refused the kernel is launched the ordinary way.
+template <typename... K, typename... A>
+inline void launch_chained(void (*kernel)(K...), unsigned grid, cudaStream_t stream, A... args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kBlock);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = stream;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, kernel, args...) != cudaSuccess) {
+    (void)cudaGetLastError();
+    cfg.numAttrs = 0;
+    (void)cudaLaunchKernelEx(&cfg, kernel, args...);
+  }
 }
 
 // Clamped log-odds update of one voxel (Eq. 2 with the clamp of Sec. II-B):
