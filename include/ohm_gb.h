@@ -284,6 +284,13 @@ typedef enum {
  * stream, so the times are device durations of those launches. */
 ohm_status ohm_map_profile(ohm_map* map, uint32_t stage_mask);
 
+/* As ohm_map_profile, but only every `every`-th later integrate call (the
+ * 1st, the every+1-th, ...) records its events; the others run without any.
+ * An event between two kernels ends the programmatic-launch overlap of the
+ * call's kernel chain there, so sampling keeps the other calls unperturbed.
+ * every >= 1, else OHM_ERR_INVALID. */
+ohm_status ohm_map_profile_every(ohm_map* map, uint32_t stage_mask, int32_t every);
+
 /* Wait for the recorded launches of `stage` and return their summed device
  * time in milliseconds and their number. */
 ohm_status ohm_map_profile_read(ohm_map* map, int32_t stage, double* total_ms, int64_t* launches);

@@ -549,11 +549,21 @@ ohm_status ohm_map_profile(ohm_map* map, uint32_t stage_mask) {
   }
   map->pending.clear();
   map->profile_mask = stage_mask;
+  map->profile_every = 1;
+  map->profile_call = 0;
   for (int k = 0; k < OHM_STAGE_COUNT; ++k) {
     map->stage_ms[k] = 0.0;
     map->stage_launches[k] = 0;
   }
   return OHM_OK;
+}
+
+ohm_status ohm_map_profile_every(ohm_map* map, uint32_t stage_mask, int32_t every) {
+  if (!map) return fail(OHM_ERR_INVALID, "profile_every: map is NULL");
+  if (every < 1) return fail(OHM_ERR_INVALID, "profile_every: every must be >= 1");
+  const ohm_status st = ohm_map_profile(map, stage_mask);
+  if (st == OHM_OK) map->profile_every = every;
+  return st;
 }
 
 ohm_status ohm_map_profile_read(ohm_map* map, int32_t stage, double* total_ms, int64_t* launches) {
@@ -596,6 +606,7 @@ static cudaEvent_t pooled_event(ohm_map* map) {
 void stage_begin(ohm_map* map, int stage, cudaStream_t stream, cudaEvent_t* ev) {
   *ev = nullptr;
   if (!(map->profile_mask & (1u << stage))) return;
+  if (map->profile_every > 1 && (map->profile_call - 1) % map->profile_every != 0) return;
   *ev = pooled_event(map);
   cudaEventRecord(*ev, stream);
 }

@@ -42,6 +42,8 @@ struct ohm_map {
   long long launches;       // kernels launched by this map
   // per-stage event timing
   uint32_t profile_mask;
+  int32_t profile_every;    // record only every profile_every-th call (0 or 1: every call)
+  long long profile_call;   // integrate calls since the mask was set
   std::vector<cudaEvent_t> event_pool;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
   double stage_ms[OHM_STAGE_COUNT];

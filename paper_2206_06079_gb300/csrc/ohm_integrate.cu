@@ -233,6 +233,7 @@ static long long blocks_for(long long n) { return (n + kBlock - 1) / kBlock; }
 
 cudaError_t launch_integrate(ohm_map* map, const CallArgs& args, cudaStream_t stream) {
   DeviceMap& m = map->d;
+  map->profile_call += 1;  // the call's index for sampled stage timing
   const bool occ = (m.layers & kLayerOcc) != 0, cnt = (m.layers & kLayerCounts) != 0, ndt = (m.layers & kLayerNdt) != 0;
   const bool tsdf = (m.layers & kLayerTsdf) != 0;
   const bool mean = (m.layers & kLayerMean) != 0;

@@ -27,7 +27,7 @@ _STATUS_NAMES = {ERR_INVALID: "invalid argument", ERR_CAPACITY: "capacity", ERR_
 
 # Every symbol include/ohm_gb.h declares.
 EXPORTED = ["ohm_map_create", "ohm_map_destroy", "ohm_integrate_rays", "ohm_integrate_rays_async", "ohm_map_sync", "ohm_map_status_async", "ohm_probe_cas_rate",
-            "ohm_query_voxels", "ohm_map_region_count", "ohm_map_export", "ohm_map_stats", "ohm_map_profile",
+            "ohm_query_voxels", "ohm_map_region_count", "ohm_map_export", "ohm_map_stats", "ohm_map_profile", "ohm_map_profile_every",
             "ohm_map_profile_read", "ohm_last_error", "ohm_count_rays_noalloc", "ohm_batch_create",
             "ohm_batch_destroy", "ohm_batch_tune", "ohm_batch_integrate", "ohm_batch_sync", "ohm_batch_stats",
             "ohm_integrate_depth", "ohm_tsdf_backward", "ohm_map_evict", "ohm_map_restore_pending",
@@ -128,6 +128,8 @@ def load_library(path: str = LIB_PATH):
     lib.ohm_map_stats.argtypes = [vp, ctypes.POINTER(CallStats), vp]
     lib.ohm_map_profile.restype = st
     lib.ohm_map_profile.argtypes = [vp, ctypes.c_uint32]
+    lib.ohm_map_profile_every.restype = st
+    lib.ohm_map_profile_every.argtypes = [vp, ctypes.c_uint32, ctypes.c_int32]
     lib.ohm_map_profile_read.restype = st
     lib.ohm_map_profile_read.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
     lib.ohm_count_rays_noalloc.restype = st
@@ -375,12 +377,17 @@ class Map:
         _check(load_library().ohm_map_stats(self._h, ctypes.byref(s), _stream_handle(stream)))
         return {k: int(getattr(s, k)) for k, _ in CallStats._fields_}
 
-    def profile(self, stages=()):
-        """Time the kernels of the named stages (see STAGES) in later calls."""
+    def profile(self, stages=(), every=1):
+        """Time the kernels of the named stages (see STAGES) in later calls;
+        with every > 1 only in every every-th call (the others run without
+        events, keeping the programmatic-launch overlap of their kernels)."""
         mask = 0
         for name in stages:
             mask |= 1 << STAGES.index(name)
-        _check(load_library().ohm_map_profile(self._h, mask))
+        if every == 1:
+            _check(load_library().ohm_map_profile(self._h, mask))
+        else:
+            _check(load_library().ohm_map_profile_every(self._h, mask, int(every)))
 
     def profile_read(self, stage: str):
         """(total device ms, launches) of a profiled stage; waits for them."""

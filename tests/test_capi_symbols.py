@@ -87,3 +87,10 @@ def test_create_rejects_bad_parameters_before_touching_a_device():
             ohm.Map(**W.room_params(**kw))
         assert ei.value.code == ohm.ERR_INVALID, kw
         assert msg in str(ei.value), (kw, str(ei.value))
+
+
+def test_sampled_profiling_rejects_bad_arguments_without_a_device():
+    build_lib.build()
+    lib = ohm.load_library()
+    assert lib.ohm_map_profile_every(None, 0, 2) == ohm.ERR_INVALID
+    assert b"NULL" in lib.ohm_last_error()

@@ -366,6 +366,25 @@ def test_status_async_reports_each_step_without_waiting():
     compare_dense(gm, om)
 
 
+def test_sampled_stage_timing_changes_nothing():
+    """Stage events in every third call only (ohm_map_profile_every): the
+    sampled calls are the ones counted, and the map equals one built without
+    any events, bit for bit."""
+    p = W.room_params(layers=W.OCC | W.NDT | W.COUNTS)
+    a, b = ohm.Map(**p), ohm.Map(**p)
+    a.profile(["walk", "hits"], every=3)
+    for i in range(10):
+        r = W.room_rays(i, n=4096)
+        a.integrate(r.origins.cuda(), r.endpoints.cuda(), r.flags.cuda(), sync=False)
+        b.integrate(r.origins.cuda(), r.endpoints.cuda(), r.flags.cuda(), sync=False)
+    a.sync()
+    b.sync()
+    ms, n = a.profile_read("walk")
+    assert n == 4 and ms > 0.0  # calls 1, 4, 7 and 10
+    assert a.profile_read("hits")[1] == 4 and a.profile_read("prepare")[1] == 0
+    assert_maps_identical(a, b)
+
+
 def test_async_host_inputs_back_to_back():
     """Scans submitted from pinned host memory without waiting (two staging
     slots filled on the map's copy stream) give the map built from device
