@@ -87,19 +87,25 @@ typedef struct {
   int64_t max_regions;     /* capacity of the region pool, 1..65536 (8 GB of occupancy) */
   int64_t max_ndt_regions; /* capacity of the NDT layer pool (regions holding samples) */
   int64_t max_rays;        /* largest ray count accepted by one integrate call */
-  int32_t segment_steps;   /* target voxel steps per ray segment (Sec. III-B ray segments):
-                              a ray whose walk takes N voxel steps, n of them along its dominant
-                              axis, is split every max(1, round(segment_steps n / N)) (at most
-                              65535) dominant-axis steps, so segments of rays in any direction
-                              are about equally long; 0 = 24 */
+  int32_t segment_steps;   /* target voxels per ray segment (Sec. III-B ray segments): a ray
+                              whose walk visits N voxels is cut into ceil(N / segment_steps)
+                              segments (more where needed to keep each within 65535 steps of its
+                              dominant axis), its dominant-axis steps dealt out to them as evenly
+                              as possible, so segments of rays in any direction are about equally
+                              long; 0 = 24 */
   int32_t device;          /* CUDA device ordinal */
   int32_t evict_when_full; /* nonzero: when ohm_integrate_rays finds the region or NDT pool full it
                               moves least recently used regions to host memory and repeats the call
                               (see the region cache below); 0: the call fails with OHM_ERR_CAPACITY */
-  int32_t reserved;        /* must be 0 */
+  int32_t max_probe;       /* hash probe bound: a region key lookup or insertion gives up after this
+                              many table entries (Sec. III-A region lookup) and the call fails with
+                              OHM_ERR_PROBE_LIMIT, changing nothing; 0 = min(table capacity, 4096),
+                              larger values are clamped to that */
 } ohm_map_params;
 
-/* Create a map.  Fills `*out` on success.  Allocates the region pool, the
+/* Create a map (Sec. III-A: a map is a sparse set of regions of 32^3 voxels,
+ * each region holding one contiguous block per layer, found from its region
+ * key in O(1)).  Fills `*out` on success.  Allocates the region pool, the
  * region hash table (capacity: the next power of two >= 2 * max_regions), the
  * enabled layers and per-call scratch sized for max_rays, on `device`.
  * Errors: OHM_ERR_INVALID for out-of-range parameters (including
@@ -107,8 +113,10 @@ typedef struct {
  * integer walk), OHM_ERR_CUDA if allocation fails. */
 ohm_status ohm_map_create(const ohm_map_params* params, ohm_map** out);
 
-/* Free the map and everything it owns.  NULL is ignored.  The caller must not
- * destroy a map while work on it is still pending on some stream. */
+/* Free the map and everything it owns (the region storage of Sec. III-A).
+ * NULL is ignored.  Waits for the last work an entry point enqueued on the map
+ * (and the map's own copy stream), not for the whole device; the caller must
+ * not destroy a map while it still has other work on it pending. */
 void ohm_map_destroy(ohm_map* map);
 
 /* Integrate one ray set (Sec. III-B; one call is one "scan").
@@ -221,7 +229,9 @@ ohm_status ohm_query_voxels(ohm_map* map, const float* points, int64_t n, float*
 ohm_status ohm_map_region_count(ohm_map* map, int64_t* out, void* stream);
 
 /* Copy regions [first, first + count) in allocation order into device buffers
- * (any may be NULL).  Voxel order inside a region: x fastest, then y, then z.
+ * (any may be NULL): the map's regions and their layers (Sec. III-A), the way
+ * the paper's GPU cache synchronises regions back to the CPU-side map.  Voxel
+ * order inside a region: x fastest, then y, then z.
  *   keys       count x 3 int32 region coordinates (voxel index >> 5)
  *   occupancy  count x 32768 float
  *   counts     count x 32768 x 2 uint32 (hits, misses)
@@ -262,6 +272,26 @@ ohm_status ohm_map_stats(ohm_map* map, ohm_call_stats* out, void* stream);
  * and writes operations per second; the ceiling the walk's atomic rate is
  * reported against.  The paper has no counterpart.  Synchronous. */
 ohm_status ohm_probe_cas_rate(int32_t device, int64_t words, int64_t ops, double* ops_per_second);
+
+/* Measured ceilings for the miss walk's memory work (no counterpart in the
+ * paper): throughput of the library's probe kernels on `device`, 8 blocks of
+ * 256 threads per SM, 8 random locations in flight per thread, best of three
+ * timed launches after a warm-up launch (which also fills L2).  Allocates
+ * and frees its buffer.  Synchronous.
+ *   OHM_PROBE_L2_ADD      fire-and-forget float atomic add of 1 to a random
+ *                         word of a `units`-word buffer (the walk's miss
+ *                         update): L2 atomic throughput when the buffer fits in
+ *                         L2, over distinct words when it is large and over
+ *                         few (contended) words when `units` is small
+ *   OHM_PROBE_L2_CAS      load, then compare-and-swap of a random word
+ *   OHM_PROBE_SECTOR_RMW  load of a word of a random 32-byte sector of a
+ *                         `units`-sector buffer, then a store of it plus one:
+ *                         with a buffer larger than L2 every operation reads a
+ *                         sector from memory and writes it back
+ * `units` is a power of two (at most 2^32 words, 2^29 sectors); `ops` the
+ * operations per timed launch.  Writes operations per second. */
+enum { OHM_PROBE_L2_ADD = 0, OHM_PROBE_L2_CAS = 1, OHM_PROBE_SECTOR_RMW = 2 };
+ohm_status ohm_probe_rate(int32_t device, int32_t kind, int64_t units, int64_t ops, double* ops_per_second);
 
 /* Kernel stages of an integrate call, for per-stage GPU timing. */
 typedef enum {
@@ -331,6 +361,15 @@ ohm_status ohm_tsdf_backward(ohm_map* map, const float* depth, int32_t width, in
                              const float* query_points, const float* grad_query, int64_t n_query, float* grad_depth,
                              double* grad_twist, void* stream);
 
+/* The pose exp(xi) pose0 of the adjoint's pose parametrisation: the left
+ * twist xi = (rho, phi) (6 doubles) as a rigid motion (rotation by Rodrigues'
+ * formula, translation V rho with V the left Jacobian of SO(3); to first
+ * order below |phi| = 1e-12) applied to the 3 x 4 row-major camera-to-world
+ * pose0, written to pose (12 doubles).  Host memory, host arithmetic (double);
+ * ohm_tsdf_backward's grad_twist is the gradient with respect to xi at 0 of
+ * the frame seen from this pose.  The paper has no counterpart. */
+ohm_status ohm_twist_pose(const double* xi, const double* pose0, double* pose);
+
 /* ---------------------------------------------------------------------------
  * Batched integration of many maps (no counterpart in the paper, which
  * integrates one ray set into one map at a time).
@@ -399,7 +438,10 @@ ohm_status ohm_batch_stats(ohm_batch* batch, int64_t* kernel_launches, int64_t* 
  * any stream capture.  Every call uses the calling thread's current device and
  * shares the array: calls whose work may overlap on the GPU (unordered streams)
  * race on it and must not be issued.  Each call clears the part that must start
- * at zero.  All pointers must be device memory.
+ * at zero.  All pointers must be device memory of the current device; hits and
+ * misses must each hold dims[0] * dims[1] * dims[2] uint32 elements and flags
+ * (if not NULL) n bytes -- the library cannot check the sizes of caller
+ * buffers, and a short one is written or read out of bounds.
  * Errors: OHM_ERR_INVALID when n > OHM_NOALLOC_MAX_RAYS, when n times the
  * segments a ray can have (max_range / voxel_size + 2) / segment_steps + 1
  * exceeds 4 * OHM_NOALLOC_MAX_RAYS, for bad grid parameters or host pointers;
@@ -421,7 +463,11 @@ ohm_status ohm_count_rays_noalloc(const ohm_count_grid* grid, const float* origi
                                   const float* endpoints, const uint8_t* flags, int64_t n, uint32_t* hits,
                                   uint32_t* misses, void* stream);
 
-/* Thread-local message describing the last failure on this thread. */
+/* Thread-local message describing the last failure on this thread.  The
+ * paper has no error interface; the failures reported are those of its steps:
+ * the region allocation before the walk (Sec. III-B: a ray set's regions must
+ * all be present before its voxels are updated), the hash probe bound of the
+ * region lookup (Sec. III-A) and the argument checks of each entry point. */
 const char* ohm_last_error(void);
 
 #ifdef __cplusplus

@@ -72,6 +72,24 @@ def frame_eval(omap, o_nom, e_nom, flags, o_eval, e_eval, qvox, g):
     return loss.value, ge, go
 
 
+def band_margin(omap, o_nom, e_nom, flags, o_eval, e_eval):
+    """Per ray, min over its frozen band voxels of | |s| - tau | at the
+    continuous geometry (oracle_tsdf_band_margin); +inf without a band."""
+    o_nom = np.ascontiguousarray(o_nom, np.float32).reshape(3)
+    e_nom = np.ascontiguousarray(e_nom, np.float32).reshape(-1, 3)
+    f = np.ascontiguousarray(flags, np.uint8)
+    o_eval = np.ascontiguousarray(o_eval, np.float64).reshape(3)
+    e_eval = np.ascontiguousarray(e_eval, np.float64).reshape(-1, 3)
+    n = e_nom.shape[0]
+    out = np.zeros(n, np.float64)
+    lib = _load()
+    lib.oracle_tsdf_band_margin.restype = ctypes.c_int
+    lib.oracle_tsdf_band_margin.argtypes = [ctypes.c_void_p] * 4 + [ctypes.c_int64] + [ctypes.c_void_p] * 3
+    if lib.oracle_tsdf_band_margin(omap._h, _ptr(o_nom), _ptr(e_nom), _ptr(f), n, _ptr(o_eval), _ptr(e_eval), _ptr(out)):
+        raise ValueError("oracle_tsdf_band_margin failed")
+    return out
+
+
 def chain_to_depth_and_twist(ge, go, e_world, o_world, R, pt):
     """Per-pixel dL/dz = dL/de . (R p~) and the twist gradient (6,)."""
     de_dz = pt @ np.asarray(R, np.float64).T

@@ -709,18 +709,15 @@ void oracle_query(void* h, const float* pts, int64_t n, float* occupancy, uint8_
 //   r_perp = r - (r.u) u,  dD_new/ds = 1 / (W + c).
 // qvox: m voxel indices (x, y, z) with weights g.  grad_e: n x 3, grad_o: 3
 // (either may be null).  Returns 0, or -1 on bad arguments.
-int oracle_tsdf_frame_eval(void* h, const float* o_nom, const float* e_nom, const uint8_t* flags, int64_t n,
-                           const double* o_eval, const double* e_eval, const int64_t* qvox, const double* g,
-                           int64_t m_q, double* loss, double* grad_e, double* grad_o) {
-  Map& m = *static_cast<Map*>(h);
-  if (!(m.p.layers & kLayerTsdf)) return -1;
-  typedef std::tuple<int64_t, int64_t, int64_t> Key;
-  // gradient weight per voxel
-  std::map<Key, double> G;
-  for (int64_t q = 0; q < m_q; ++q) G[std::make_tuple(qvox[3 * q], qvox[3 * q + 1], qvox[3 * q + 2])] += g[q];
-  // frozen band voxel lists from the nominal rays, and counts c(v)
+}  // extern "C"
+
+namespace {
+
+// The voxels each ray of a frame updates (the quantised band walk of
+// oracle_integrate), from the nominal float rays.
+std::vector<std::vector<Voxel>> frozen_bands(Map& m, const float* o_nom, const float* e_nom, const uint8_t* flags,
+                                             int64_t n) {
   std::vector<std::vector<Voxel>> bands((size_t)n);
-  std::map<Key, int64_t> count;
   const double rmin = m.p.min_range * m.scale, rmax = m.p.max_range * m.scale;
   for (int64_t j = 0; j < n; ++j) {
     PreparedRay r;
@@ -738,8 +735,28 @@ int oracle_tsdf_frame_eval(void* h, const float* o_nom, const float* e_nom, cons
       a1[a] = r.qo[a] + (int64_t)std::llrint(d[a] * f1);
     }
     bands[(size_t)j] = walk(a0, a1, m.unit);
-    for (const Voxel& v : bands[(size_t)j]) count[std::make_tuple(v.v[0], v.v[1], v.v[2])] += 1;
   }
+  return bands;
+}
+
+}  // namespace
+
+extern "C" {
+
+int oracle_tsdf_frame_eval(void* h, const float* o_nom, const float* e_nom, const uint8_t* flags, int64_t n,
+                           const double* o_eval, const double* e_eval, const int64_t* qvox, const double* g,
+                           int64_t m_q, double* loss, double* grad_e, double* grad_o) {
+  Map& m = *static_cast<Map*>(h);
+  if (!(m.p.layers & kLayerTsdf)) return -1;
+  typedef std::tuple<int64_t, int64_t, int64_t> Key;
+  // gradient weight per voxel
+  std::map<Key, double> G;
+  for (int64_t q = 0; q < m_q; ++q) G[std::make_tuple(qvox[3 * q], qvox[3 * q + 1], qvox[3 * q + 2])] += g[q];
+  // frozen band voxel lists from the nominal rays, and counts c(v)
+  const std::vector<std::vector<Voxel>> bands = frozen_bands(m, o_nom, e_nom, flags, n);
+  std::map<Key, int64_t> count;
+  for (int64_t j = 0; j < n; ++j)
+    for (const Voxel& v : bands[(size_t)j]) count[std::make_tuple(v.v[0], v.v[1], v.v[2])] += 1;
   // loss: unchanged voxels contribute g D, changed ones g D_new
   double L = 0.0;
   std::map<Key, double> sum_s;
@@ -804,6 +821,42 @@ int oracle_tsdf_frame_eval(void* h, const float* o_nom, const float* e_nom, cons
       L += kv.second * (W * D + sum_s[kv.first]) / (W + (double)c->second);
   }
   *loss = L;
+  return 0;
+}
+
+// For each ray of a frame (band voxels frozen as in oracle_tsdf_frame_eval),
+// the distance of the clamp from the nearest unclamped value among its band
+// voxels: min over the band of | |s_j(v)| - tau | with s_j(v) = (e - centre).u
+// at the continuous geometry (o_eval, e_eval), double; +inf for a ray that
+// updates no voxel.  Where it is tiny, evaluations of s that differ by
+// rounding or quantisation can disagree on whether s is clamped, and with it
+// on that voxel's gradient.  Returns 0, or -1 on bad arguments.
+int oracle_tsdf_band_margin(void* h, const float* o_nom, const float* e_nom, const uint8_t* flags, int64_t n,
+                            const double* o_eval, const double* e_eval, double* margin) {
+  Map& m = *static_cast<Map*>(h);
+  if (!(m.p.layers & kLayerTsdf)) return -1;
+  const std::vector<std::vector<Voxel>> bands = frozen_bands(m, o_nom, e_nom, flags, n);
+  const double tau = m.p.tsdf_trunc;
+  for (int64_t j = 0; j < n; ++j) {
+    double best = INFINITY;
+    if (!bands[(size_t)j].empty()) {
+      const double* e = e_eval + 3 * j;
+      double u[3], dist = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        u[a] = e[a] - o_eval[a];
+        dist += u[a] * u[a];
+      }
+      dist = std::sqrt(dist);
+      for (int a = 0; a < 3; ++a) u[a] /= dist;
+      for (const Voxel& v : bands[(size_t)j]) {
+        double s = 0.0;
+        for (int a = 0; a < 3; ++a) s += (e[a] - (m.p.map_origin[a] + ((double)v.v[a] + 0.5) * m.p.voxel_size)) * u[a];
+        const double gap = std::fabs(std::fabs(s) - tau);
+        if (gap < best) best = gap;
+      }
+    }
+    margin[j] = best;
+  }
   return 0;
 }
 

@@ -271,6 +271,7 @@ ohm_status ohm_integrate_depth(ohm_map* map, const float* depth, int32_t width, 
   a.n_origins = 1;
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = launch_integrate(map, a, s);
+  if (e == cudaSuccess) note_work(map, s);
   if (prev >= 0 && prev != map->device) cudaSetDevice(prev);
   if (e != cudaSuccess) return afail(OHM_ERR_CUDA, std::string("integrate_depth: ") + cudaGetErrorString(e));
   return OHM_OK;
@@ -320,8 +321,40 @@ ohm_status ohm_tsdf_backward(ohm_map* map, const float* depth, int32_t width, in
     map->launches += 1;
   }
   if (e == cudaSuccess) e = cudaGetLastError();
+  if (e == cudaSuccess) note_work(map, s);
   if (prev >= 0 && prev != map->device) cudaSetDevice(prev);
   if (e != cudaSuccess) return afail(OHM_ERR_CUDA, std::string("tsdf_backward: ") + cudaGetErrorString(e));
+  return OHM_OK;
+}
+
+ohm_status ohm_twist_pose(const double* xi, const double* pose0, double* pose) {
+  if (!xi || !pose0 || !pose) return ohm::afail(OHM_ERR_INVALID, "twist_pose: NULL argument");
+  // T = exp(xi) as a rigid motion (Rodrigues' formula for the rotation R and
+  // V rho for the translation, V the left Jacobian of SO(3)); pose = T pose0.
+  const double rho[3] = {xi[0], xi[1], xi[2]}, phi[3] = {xi[3], xi[4], xi[5]};
+  const double th = std::sqrt(phi[0] * phi[0] + phi[1] * phi[1] + phi[2] * phi[2]);
+  const double Kx[3][3] = {{0.0, -phi[2], phi[1]}, {phi[2], 0.0, -phi[0]}, {-phi[1], phi[0], 0.0}};
+  double K2[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) K2[i][j] = Kx[i][0] * Kx[0][j] + Kx[i][1] * Kx[1][j] + Kx[i][2] * Kx[2][j];
+  // small angles: the series to first order, as an exact rotation is not needed there
+  const double a = th < 1e-12 ? 1.0 : std::sin(th) / th;
+  const double b = th < 1e-12 ? 0.0 : (1.0 - std::cos(th)) / (th * th);
+  const double bv = th < 1e-12 ? 0.5 : b;
+  const double cv = th < 1e-12 ? 0.0 : (th - std::sin(th)) / (th * th * th);
+  double R[3][3], V[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      const double I = i == j ? 1.0 : 0.0;
+      R[i][j] = I + a * Kx[i][j] + b * K2[i][j];
+      V[i][j] = I + bv * Kx[i][j] + cv * K2[i][j];
+    }
+  for (int i = 0; i < 3; ++i) {
+    for (int j = 0; j < 3; ++j)
+      pose[4 * i + j] = R[i][0] * pose0[0 + j] + R[i][1] * pose0[4 + j] + R[i][2] * pose0[8 + j];
+    pose[4 * i + 3] = R[i][0] * pose0[3] + R[i][1] * pose0[7] + R[i][2] * pose0[11] +
+                      (V[i][0] * rho[0] + V[i][1] * rho[1] + V[i][2] * rho[2]);
+  }
   return OHM_OK;
 }
 

@@ -449,6 +449,7 @@ ohm_status ohm_batch_integrate(ohm_batch* b, const float* const* origins, const 
     }
   }
   if (e != cudaSuccess) return bfail(OHM_ERR_CUDA, std::string("batch_integrate: ") + cudaGetErrorString(e));
+  for (int i = 0; i < b->n_maps; ++i) ohm::note_work(b->maps[i], s);
   return OHM_OK;
 }
 

@@ -81,6 +81,7 @@ void free_map(ohm_map* m) {
                   m->stage_origins, m->stage_endpoints, m->stage_flags, m->hin_origins[0], m->hin_origins[1],
                   m->hin_endpoints[0], m->hin_endpoints[1], m->hin_flags[0], m->hin_flags[1]};
   if (m->copy_stream) cudaStreamSynchronize(m->copy_stream);
+  if (m->work_done) cudaEventDestroy(m->work_done);
   for (int s = 0; s < 2; ++s) {
     if (m->hin_copied[s]) cudaEventDestroy(m->hin_copied[s]);
     if (m->hin_free[s]) cudaEventDestroy(m->hin_free[s]);
@@ -165,6 +166,7 @@ ohm_status enqueue_integrate(ohm_map* map, const float* origins, int64_t n_origi
     e = cudaEventRecord(map->hin_free[slot], stream);
     if (e != cudaSuccess) return cuda_fail(e, "integrate: record");
   }
+  ohm::note_work(map, stream);
   return OHM_OK;
 }
 
@@ -185,12 +187,23 @@ ohm_status ohm_map_create(const ohm_map_params* params, ohm_map** out) {
   if (p.layers == 0 || (p.layers & ~all)) return fail(OHM_ERR_INVALID, "create: bad layer mask");
   if (!(p.l_min <= p.l_max)) return fail(OHM_ERR_INVALID, "create: l_min > l_max");
   if (std::isnan(p.ndt_clear_below)) return fail(OHM_ERR_INVALID, "create: ndt_clear_below is NaN");
+  {
+    // log-odds values are sums of these and the clamp bounds: with every one 0
+    // or at least 2^-100 in magnitude no value is a float subnormal, which the
+    // miss walk's float atomic add would flush to zero
+    const float tiny = std::ldexp(1.0f, -100);
+    const float vals[4] = {p.hit, p.miss, p.l_min, p.l_max};
+    for (float v : vals)
+      if (std::isnan(v) || (v != 0.0f && std::fabs(v) < tiny))
+        return fail(OHM_ERR_INVALID, "create: hit, miss, l_min and l_max must be 0 or at least 2^-100 in magnitude");
+  }
   if (!(p.max_range > 0.0)) return fail(OHM_ERR_INVALID, "create: max_range must be > 0");
   if (!(p.min_range >= 0.0)) return fail(OHM_ERR_INVALID, "create: min_range must be >= 0");
   if (!(p.tsdf_trunc >= 0.0) || !(p.tsdf_wmax > 0.0)) return fail(OHM_ERR_INVALID, "create: bad TSDF parameters");
   if (p.max_regions < 1 || p.max_regions > (1LL << 16)) return fail(OHM_ERR_INVALID, "create: max_regions must be in [1, 65536]");
   if (p.max_rays < 1 || p.max_rays > (1LL << 30)) return fail(OHM_ERR_INVALID, "create: max_rays out of range");
   if (p.segment_steps < 1) return fail(OHM_ERR_INVALID, "create: segment_steps must be >= 1");
+  if (p.max_probe < 0) return fail(OHM_ERR_INVALID, "create: max_probe must be >= 0");
   if ((p.layers & OHM_LAYER_MEAN) && p.max_rays > (1LL << 22))
     return fail(OHM_ERR_INVALID, "create: the mean layer needs max_rays <= 2^22 (per-call 32-bit sums)");
   if ((p.layers & OHM_LAYER_NDT) && (p.max_ndt_regions < 1 || p.max_ndt_regions > p.max_regions))
@@ -212,12 +225,14 @@ ohm_status ohm_map_create(const ohm_map_params* params, ohm_map** out) {
   const long long H = next_pow2(2 * R > 1024 ? 2 * R : 1024);
   m->hash_capacity = H;
   d.hmask = (uint32_t)(H - 1);
-  d.max_probe = (int32_t)(H < 4096 ? H : 4096);
+  const int32_t probe_cap = (int32_t)(H < 4096 ? H : 4096);
+  d.max_probe = (p.max_probe <= 0 || p.max_probe > probe_cap) ? probe_cap : p.max_probe;
   d.max_regions = (int32_t)R;
   d.max_ndt = (p.layers & OHM_LAYER_NDT) ? (int32_t)p.max_ndt_regions : 0;
   const long long vox_steps = (long long)std::ceil(p.max_range / p.voxel_size) + 2;
-  // a ray's segments take at least max(1, segment_steps / 3) dominant-axis steps
-  d.max_segs = p.max_rays * (vox_steps / std::max(1, p.segment_steps / 3) + 1);
+  // a ray takes at most 3 vox_steps voxel steps, so it has at most
+  // ceil(3 vox_steps / segment_steps) segments (ray_segment_split)
+  d.max_segs = p.max_rays * ((3 * vox_steps + p.segment_steps - 1) / p.segment_steps + 1);
   const long long band = (long long)std::ceil(2.0 * p.tsdf_trunc / p.voxel_size) + 2;
   d.max_touched = (p.layers & OHM_LAYER_TSDF) ? p.max_rays * (1 + 3 * band) : 0;
   if (d.max_touched > R * V) d.max_touched = R * V;
@@ -273,6 +288,7 @@ ohm_status ohm_map_create(const ohm_map_params* params, ohm_map** out) {
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->hin_free[s], cudaEventDisableTiming);
   }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&m->copy_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->work_done, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&m->h_status), sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&m->h_calls), sizeof(ohm::CallCounters));
   if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&m->h_count), 2 * sizeof(int32_t));
@@ -312,7 +328,9 @@ ohm_status ohm_map_create(const ohm_map_params* params, ohm_map** out) {
 void ohm_map_destroy(ohm_map* map) {
   if (!map) return;
   DeviceGuard guard(map->device);
-  cudaDeviceSynchronize();
+  // wait only for the map's own work (the last work any entry point enqueued
+  // on it, and its copy stream), not for every stream of the device
+  if (map->work_done) cudaEventSynchronize(map->work_done);
   free_map(map);
 }
 
@@ -348,6 +366,20 @@ ohm_status ohm_probe_cas_rate(int32_t device, int64_t words, int64_t ops, double
   if (!guard.ok) return fail(OHM_ERR_CUDA, "probe_cas_rate: cannot select device");
   cudaError_t e = ohm::probe_cas_rate(device, words, ops, ops_per_second);
   if (e != cudaSuccess) return cuda_fail(e, "probe_cas_rate");
+  return OHM_OK;
+}
+
+ohm_status ohm_probe_rate(int32_t device, int32_t kind, int64_t units, int64_t ops, double* ops_per_second) {
+  if (!ops_per_second) return fail(OHM_ERR_INVALID, "probe_rate: NULL output");
+  if (kind < OHM_PROBE_L2_ADD || kind > OHM_PROBE_SECTOR_RMW) return fail(OHM_ERR_INVALID, "probe_rate: unknown kind");
+  const int64_t max_units = kind == OHM_PROBE_SECTOR_RMW ? (1LL << 29) : (1LL << 32);
+  if (units < 1 || units > max_units || (units & (units - 1)))
+    return fail(OHM_ERR_INVALID, "probe_rate: units must be a power of two in [1, 2^32] (2^29 sectors)");
+  if (ops < 1) return fail(OHM_ERR_INVALID, "probe_rate: ops < 1");
+  DeviceGuard guard(device);
+  if (!guard.ok) return fail(OHM_ERR_CUDA, "probe_rate: cannot select device");
+  cudaError_t e = ohm::probe_rate(device, kind, units, ops, ops_per_second);
+  if (e != cudaSuccess) return cuda_fail(e, "probe_rate");
   return OHM_OK;
 }
 
@@ -477,6 +509,7 @@ ohm_status ohm_query_voxels(ohm_map* map, const float* points, int64_t n, float*
                         reinterpret_cast<unsigned long long*>(path_sum), mean, s);
   if (staged) cudaFreeAsync(staged, s);
   if (e != cudaSuccess) return cuda_fail(e, "query: launch");
+  ohm::note_work(map, s);
   return OHM_OK;
 }
 
@@ -513,6 +546,7 @@ ohm_status ohm_map_export(ohm_map* map, int64_t first, int64_t count, int32_t* k
                                      tsdf, reinterpret_cast<unsigned long long*>(path_sum),
                                      reinterpret_cast<unsigned long long*>(mean), static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "export: launch");
+  ohm::note_work(map, static_cast<cudaStream_t>(stream));
   return OHM_OK;
 }
 
@@ -591,6 +625,10 @@ ohm_status ohm_map_profile_read(ohm_map* map, int32_t stage, double* total_ms, i
 namespace ohm {
 
 void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+void note_work(ohm_map* map, cudaStream_t stream) {
+  if (map->work_done) cudaEventRecord(map->work_done, stream);
+}
 
 static cudaEvent_t pooled_event(ohm_map* map) {
   if (!map->event_pool.empty()) {

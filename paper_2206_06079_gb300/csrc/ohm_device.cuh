@@ -324,6 +324,12 @@ __host__ __device__ __forceinline__ uint32_t morton(uint32_t x, uint32_t y, uint
   return spread5(x) | (spread5(y) << 1) | (spread5(z) << 2);
 }
 
+// Morton index of a voxel inside its region.
+__host__ __device__ __forceinline__ uint32_t region_morton(int32_t vx, int32_t vy, int32_t vz) {
+  const int32_t mask = (1 << kRegionShift) - 1;
+  return morton((uint32_t)(vx & mask), (uint32_t)(vy & mask), (uint32_t)(vz & mask));
+}
+
 // Step one axis of a Morton index by +-1, wrapping inside the 5 bits of that axis.
 __host__ __device__ __forceinline__ uint32_t morton_step(uint32_t m, uint32_t mask, int sign) {
   uint32_t moved = sign > 0 ? ((m | ~mask) + 1u) : ((m & mask) - 1u);
@@ -590,19 +596,220 @@ __host__ __device__ __forceinline__ uint32_t morton_mask(int axis) {
   return axis == 0 ? 0x1249u : (axis == 1 ? 0x2492u : 0x4924u);
 }
 
-// Number of segments of a walk whose dominant axis takes nmaj steps.
+// ---------------------------------------------------------------------------
+// Filtered exact walk: the integrate kernels' voxel walk.  It visits exactly
+// the voxels of Walker, in the same order, with cheaper steps.
+//
+// Along every axis k it keeps c_k, the boundary crossings taken so far, and
+// an FP32 estimate of the exact crossing parameter of the next boundary,
+//     t_k = (d0_k + c_k U) / A_k,
+//     t^_k = fma(c_k, dU_k, t0_k),  r_k = rcp(float(A_k)),  dU_k = U r_k,  t0_k = d0_k r_k.
+// float(A_k), the reciprocal, d0_k r_k and the fma each round once (U is a
+// power of two and d0_k <= 2^20, c_k < 2^24 are exact in float), so
+// t^_k = t_k (1 + e) with |e| <= (1 + u)^3 / (1 - u) - 1 < 4.01 u, u = 2^-24.
+// A step is decided on the estimates when exactly one axis a has
+// t^_a <= thr = fl(g min_k t^_k), g = 1 + 2^-20 = 1 + 16 u.  Then for every
+// other axis j, t^_j > thr >= g (1 - u) t^_a, so
+//     t_j >= t^_j / (1 + 4.01 u) > t^_a g (1 - u) / (1 + 4.01 u) >= t^_a / (1 - 4.01 u) >= t_a
+// (g (1 - u)(1 - 4.01 u) >= 1 + 4.01 u holds since 16 - 1 - 4.01 > 4.01):
+// a is the strict minimum of the exact parameters, which is the axis the
+// exact rule steps.  It is never an axis without steps left (those have
+// t >= 1, and an axis with steps left has t <= 1).  When the estimates do not
+// single out one axis (a near-tie), the exact 64-bit comparison of Walker
+// decides, from c_k (exact_pick).  An axis with A_k = 0 never steps:
+// dU_k = 0, t0_k = +inf, so t^_k = +inf.
+//
+// Morton indices are stepped in a sign-normalised form: the bits of an axis
+// walked in the negative direction are stored inverted, so that every step is
+// +1 on its axis and leaving the region is the wrap from 31 to 0 in both
+// directions.  The voxel's real Morton index is mo ^ neg.
+// ---------------------------------------------------------------------------
+struct FWalker {
+  float tx, ty, tz;  // t^ per axis
+  float cx, cy, cz;  // crossings taken per axis (exact integers)
+  float ux, uy, uz;  // dU
+  float ox, oy, oz;  // t0
+};
+
+__host__ __device__ __forceinline__ float rcp_rn(float x) {
+#ifdef __CUDA_ARCH__
+  return __frcp_rn(x);
+#else
+  return 1.0f / x;
+#endif
+}
+__host__ __device__ __forceinline__ float fmul_rn(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fmul_rn(a, b);
+#else
+  return a * b;
+#endif
+}
+__host__ __device__ __forceinline__ float fma_rn(float a, float b, float c) {
+#ifdef __CUDA_ARCH__
+  return __fmaf_rn(a, b, c);
+#else
+  return std::fmaf(a, b, c);
+#endif
+}
+
+// FP32 constants of one axis.
+__host__ __device__ __forceinline__ void fwalker_axis(int32_t A, int32_t d0, int F, float c, float* u, float* o, float* t) {
+  if (A == 0) {
+    *u = 0.0f;
+    *o = INFINITY;
+  } else {
+    const float r = rcp_rn((float)A);
+    *u = fmul_rn(r, (float)(1 << F));  // exact: a power of two
+    *o = fmul_rn((float)d0, r);
+  }
+  *t = fma_rn(c, *u, *o);
+}
+
+// Filtered state after c[k] crossings along each axis.
+__host__ __device__ __forceinline__ void fwalker_init(FWalker& f, const RayRec& r, int F, const long long c[3]) {
+  f.cx = (float)c[0];
+  f.cy = (float)c[1];
+  f.cz = (float)c[2];
+  fwalker_axis(r.A[0], r.d0[0], F, f.cx, &f.ux, &f.ox, &f.tx);
+  fwalker_axis(r.A[1], r.d0[1], F, f.cy, &f.uy, &f.oy, &f.ty);
+  fwalker_axis(r.A[2], r.d0[2], F, f.cz, &f.uz, &f.oz, &f.tz);
+}
+
+// The axis the estimates single out, or -1 (near-tie: decide exactly).
+__host__ __device__ __forceinline__ int fwalker_pick(const FWalker& f) {
+  const float tm = fminf(f.tx, fminf(f.ty, f.tz));
+  const float thr = fmul_rn(tm, 1.00000095367431640625f);  // 1 + 2^-20
+  const bool nx = f.tx <= thr, ny = f.ty <= thr, nz = f.tz <= thr;
+  if ((int)nx + (int)ny + (int)nz != 1) return -1;
+  return nx ? 0 : (ny ? 1 : 2);
+}
+
+// The exact rule of Walker (walker_init / walker_choose) from the crossing
+// counts: the axis with the smallest t_k (ties: z, then y, then x), and on a
+// tie at t = 1 never an axis without steps left.
+__host__ __device__ inline int exact_pick(const RayRec& r, int F, int32_t c0, int32_t c1, int32_t c2) {
+  const long long U = 1LL << F;
+  const long long dx = r.d0[0] + (long long)c0 * U, dy = r.d0[1] + (long long)c1 * U, dz = r.d0[2] + (long long)c2 * U;
+  const long long cxy = dx * r.A[1] - dy * r.A[0];
+  const long long cxz = dx * r.A[2] - dz * r.A[0];
+  const long long cyz = dy * r.A[2] - dz * r.A[1];
+  int axis = (cxy < 0 && cxz < 0) ? 0 : ((cxy >= 0 && cyz < 0) ? 1 : 2);
+  const int32_t left = axis == 0 ? r.n[0] - c0 : (axis == 1 ? r.n[1] - c1 : r.n[2] - c2);
+  if (left == 0) axis = r.n[2] - c2 > 0 ? 2 : (r.n[1] - c1 > 0 ? 1 : 0);
+  return axis;
+}
+
+// One crossing along `axis`.
+__host__ __device__ __forceinline__ void fwalker_advance(FWalker& f, int axis) {
+  if (axis == 0) {
+    f.cx += 1.0f;
+    f.tx = fma_rn(f.cx, f.ux, f.ox);
+  } else if (axis == 1) {
+    f.cy += 1.0f;
+    f.ty = fma_rn(f.cy, f.uy, f.oy);
+  } else {
+    f.cz += 1.0f;
+    f.tz = fma_rn(f.cz, f.uz, f.oz);
+  }
+}
+
+// Morton bits of the axes a ray walks in the negative direction.
+__host__ __device__ __forceinline__ uint32_t morton_neg(int32_t flags) {
+  uint32_t m = 0;
+  if ((flags >> kRaySignShift) & 1) m |= 0x1249u;
+  if ((flags >> (kRaySignShift + 1)) & 1) m |= 0x2492u;
+  if ((flags >> (kRaySignShift + 2)) & 1) m |= 0x4924u;
+  return m;
+}
+
+// +1 along the axis of `mask` in a sign-normalised Morton index; true when
+// the step left the region (the axis wrapped from 31 to 0).
+__host__ __device__ __forceinline__ bool morton_advance(uint32_t& mo, uint32_t mask) {
+  const bool wrap = (mo & mask) == mask;
+  mo = (((mo | ~mask) + 1u) & mask) | (mo & ~mask);
+  return wrap;
+}
+
+
+// Number of segments of a walk whose dominant axis takes nmaj steps, cut
+// every S dominant-axis steps (the allocation-free entry point's split).
 __host__ __device__ __forceinline__ int32_t segment_count(int32_t nmaj, int32_t S) { return nmaj / S + 1; }
 
-// Dominant-axis steps per segment of a walk that takes nsteps voxel steps,
-// nmaj of them along its dominant axis, so that a segment covers about
-// `target` voxel steps whatever the ray's direction: round(target nmaj /
-// nsteps), within [1, 65535].  Never below target / 3 (nsteps <= 3 nmaj).
-__host__ __device__ __forceinline__ int32_t ray_segment_steps(int32_t nmaj, long long nsteps, int32_t target) {
-  if (nsteps <= 0) return 1;
-  const long long s = ((long long)target * nmaj * 2 + nsteps) / (2 * nsteps);
-  return s < 1 ? 1 : (s > 65535 ? 65535 : (int32_t)s);
+// Ray segments of the integrate kernels (Sec. III-B "breaking long rays into
+// several segments").  A walk whose dominant axis takes nmaj steps has
+// nmaj + 1 dominant-axis "slots": slot 0 is the start voxel, slot k the voxel
+// entered by the k-th dominant-axis step; every other voxel belongs to the
+// slot of the dominant-axis step before it.  The slots are dealt out to nseg
+// segments as evenly as integers allow, q = (nmaj + 1) / nseg each and one
+// more to the first (nmaj + 1) % nseg, so all segments of a ray are about
+// equally long.  nseg = ceil((nsteps + 1) / target) for a walk of nsteps voxel
+// steps, so a segment holds about `target` voxels whatever the ray's
+// direction; nseg is raised where needed to keep q <= 65535.
+struct SegSplit {
+  int32_t nseg;
+  int32_t q;  // slots per segment (the first r segments take q + 1)
+};
+
+__host__ __device__ __forceinline__ SegSplit ray_segment_split(int32_t nmaj, long long nsteps, int32_t target) {
+  const long long slots = (long long)nmaj + 1;
+  long long nseg = (nsteps + target) / target;  // ceil((nsteps + 1) / target)
+  if (nseg > slots) nseg = slots;
+  const long long min_seg = (slots + 65534) / 65535;
+  if (nseg < min_seg) nseg = min_seg;
+  SegSplit s;
+  s.nseg = (int32_t)nseg;
+  s.q = (int32_t)(slots / nseg);
+  return s;
 }
-constexpr int kRaySegShift = 16;  // RayRec flags bits 16..31: the ray's dominant-axis steps per segment
+
+// Dominant-axis steps before segment j starts (K0) and before the segment
+// after it starts (K1), for a ray with nmaj dominant-axis steps split into
+// nseg segments of q or q + 1 slots.  The segment visits the voxels from the
+// one entered by the K0-th dominant-axis step (the start voxel when K0 = 0) up
+// to, not including, the one entered by the K1-th; the last segment runs to
+// the end of the ray.
+__host__ __device__ __forceinline__ void segment_bounds(int32_t nmaj, int32_t nseg, int32_t q, int32_t j, long long* K0,
+                                                        long long* K1) {
+  const long long r = (long long)nmaj + 1 - (long long)nseg * q;
+  *K0 = (long long)j * q + (j < r ? j : r);
+  *K1 = *K0 + q + (j < r ? 1 : 0);
+}
+constexpr int kRaySegShift = 16;  // RayRec flags bits 16..31: q, the ray's dominant-axis slots per segment
+
+// Where segment j of a ray starts and ends, for the filtered walk.
+struct SegStart {
+  long long c[3];    // crossings taken along each axis before the segment's first voxel
+  int32_t v[3];      // the segment's first voxel
+  int32_t ve[3];     // the segment's last voxel
+  long long visits;  // voxels the segment visits
+};
+
+__host__ __device__ inline void segment_start(const RayRec& r, int F, int32_t j, SegStart* s) {
+  const int M = (r.flags >> kRayAxisShift) & 3;
+  const int32_t q = (int32_t)((uint32_t)r.flags >> kRaySegShift);
+  const int32_t nmaj = M == 0 ? r.n[0] : (M == 1 ? r.n[1] : r.n[2]);
+  const long long d0M = M == 0 ? r.d0[0] : (M == 1 ? r.d0[1] : r.d0[2]);
+  const long long AM = M == 0 ? r.A[0] : (M == 1 ? r.A[1] : r.A[2]);
+  long long K0, K1;
+  segment_bounds(nmaj, r.nseg, q, j, &K0, &K1);
+  const bool last = j == r.nseg - 1;
+  long long c1[3];
+  long long steps = 0;
+OHM_UNROLL
+  for (int k = 0; k < 3; ++k) {
+    s->c[k] = K0 == 0 ? 0 : (k == M ? K0 : crossings_before(r.d0[k], r.A[k], d0M, AM, F, K0, k > M, r.n[k], r.inv));
+    if (last)
+      c1[k] = r.n[k];
+    else
+      c1[k] = k == M ? K1 - 1 : crossings_before(r.d0[k], r.A[k], d0M, AM, F, K1, k > M, r.n[k], r.inv);
+    steps += c1[k] - s->c[k];
+    const int32_t sg = ((r.flags >> (kRaySignShift + k)) & 1) ? -1 : 1;
+    s->v[k] = r.v0[k] + sg * (int32_t)s->c[k];
+    s->ve[k] = r.v0[k] + sg * (int32_t)c1[k];
+  }
+  s->visits = steps + 1;
+}
 
 // ---------------------------------------------------------------------------
 // Warp-aggregated reservation: every lane of a full warp calls this together

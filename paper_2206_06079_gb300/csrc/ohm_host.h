@@ -49,6 +49,7 @@ struct ohm_map {
   double stage_ms[OHM_STAGE_COUNT];
   long long stage_launches[OHM_STAGE_COUNT];
   ohm::HostStore* store;    // evicted regions in pinned host memory
+  cudaEvent_t work_done;    // recorded behind the last work any entry point enqueued on the map
 };
 
 namespace ohm {
@@ -56,6 +57,7 @@ namespace ohm {
 // Enqueue every kernel of one integrate call on `stream`.
 cudaError_t launch_integrate(ohm_map* map, const CallArgs& args, cudaStream_t stream);
 cudaError_t probe_cas_rate(int device, long long words, long long ops, double* rate);
+cudaError_t probe_rate(int device, int kind, long long units, long long ops, double* rate);
 cudaError_t launch_query(ohm_map* map, const float* points, long long n, float* occupancy, uint8_t* known, float* ndt,
                          float* tsdf, uint32_t* counts, unsigned long long* path_sum, float* mean,
                          cudaStream_t stream);
@@ -75,6 +77,10 @@ void destroy_host_store(ohm_map* m);
 
 // Set the message ohm_last_error() returns on this thread.
 void set_last_error(const std::string& msg);
+
+// Record, on `stream`, that the map has work enqueued up to here (waited for
+// by ohm_map_destroy).
+void note_work(ohm_map* map, cudaStream_t stream);
 
 // Stage timing helpers (no-ops unless the stage is being profiled).
 void stage_begin(ohm_map* map, int stage, cudaStream_t stream, cudaEvent_t* ev);

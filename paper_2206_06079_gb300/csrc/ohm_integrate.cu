@@ -9,7 +9,8 @@
 //                    segment table (Sec. III-B ray segments)
 //   k_ndt_alloc      per sample: give its region an NDT layer
 //   k_prepare_tsdf   per ray: TSDF band end points and their regions
-//   k_walk_miss      per segment: exact voxel walk, miss update per voxel
+//   k_walk_fast      per segment: exact voxel walk, miss update per voxel
+//                    (k_walk_miss for maps with the decay layer)
 //   k_hits           per sample: hit update, hit count, NDT moments
 //   k_tsdf_walk      per ray: band walk, fixed-point s sums and counts
 //   k_tsdf_apply     per touched voxel: weighted average, scratch cleared
@@ -47,6 +48,20 @@ __global__ void __launch_bounds__(kBlock, OHM_WALK_MIN_BLOCKS) k_walk_miss(Devic
   // every thread gets here: one atomic per warp for the call's CAS count
   cas = __reduce_add_sync(0xffffffffu, cas);
   if ((threadIdx.x & 31) == 0 && cas) atomicAdd(&m.calls->atomics, (unsigned long long)cas);
+}
+
+// The miss walk of maps without the decay layer (filtered walk, see
+// walk_segment_fast).
+template <bool kOcc, bool kCounts, bool kCas>
+__global__ void __launch_bounds__(kBlock, OHM_FAST_MIN_BLOCKS) k_walk_fast(DeviceMap m) {
+  chain_enter();
+  if (latched(m)) return;
+  const long long nseg = (long long)m.calls->segments;
+  unsigned int ops = 0;
+  OHM_GRID_STRIDE(si, nseg) walk_segment_fast<kOcc, kCounts, kCas>(m, si, ops);
+  // every thread gets here: one atomic per warp for the call's atomic count
+  ops = __reduce_add_sync(0xffffffffu, ops);
+  if ((threadIdx.x & 31) == 0 && ops) atomicAdd(&m.calls->atomics, (unsigned long long)ops);
 }
 
 template <bool kOcc, bool kCounts, bool kNdt>
@@ -116,7 +131,7 @@ __global__ void __launch_bounds__(kBlock) k_query(DeviceMap m, const float* pts,
   const long long off = voxel_offset(slot, mo);
   if (occupancy || known) {
     float l = __int_as_float(0x7fc00000);
-    if (slot >= 0 && (m.layers & kLayerOcc)) l = m.occ[off];
+    if (slot >= 0 && (m.layers & kLayerOcc)) l = logodds_read(m.occ[off], m.l_min);
     if (occupancy) occupancy[i] = l;
     if (known) known[i] = (l == l) ? 1 : 0;
   }
@@ -187,7 +202,7 @@ __global__ void __launch_bounds__(kBlock) k_export(DeviceMap m, long long first,
     const uint32_t mo = morton(lin & 31, (lin >> 5) & 31, lin >> 10);
     const long long off = voxel_offset(slot, mo);
     if (keys && lin < 3) keys[3 * r + lin] = m.region_coords[3 * slot + lin];
-    if (occupancy) occupancy[t] = (m.layers & kLayerOcc) ? m.occ[off] : __int_as_float(0x7fc00000);
+    if (occupancy) occupancy[t] = (m.layers & kLayerOcc) ? logodds_read(m.occ[off], m.l_min) : __int_as_float(0x7fc00000);
     if (counts) {
       const unsigned long long c = (m.layers & kLayerCounts) ? m.counts[off] : 0ULL;
       counts[2 * t + 0] = (uint32_t)(c >> 32);
@@ -214,7 +229,7 @@ __global__ void __launch_bounds__(kBlock) k_export(DeviceMap m, long long first,
 // ---------------------------------------------------------------------------
 int walk_blocks_per_sm() {
   int b = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_walk_miss<true, true, false>, kBlock, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_walk_fast<true, false, false>, kBlock, 0);
   return b > 0 ? b : 1;
 }
 
@@ -254,16 +269,23 @@ cudaError_t launch_integrate(ohm_map* map, const CallArgs& args, cudaStream_t st
   }
   if (tsdf) OHM_LAUNCH(OHM_STAGE_PREPARE_TSDF, launch_chained(k_prepare_tsdf, prb, stream, m, args));
   const bool dec = (m.layers & kLayerDecay) != 0;
-  if (occ || cnt || dec) {
-    const int sel = (occ ? 4 : 0) | (cnt ? 2 : 0) | (dec ? 1 : 0);
+  if (dec) {
+    const int sel = (occ ? 2 : 0) | (cnt ? 1 : 0);
     switch (sel) {
-      case 7: OHM_LAUNCH(OHM_STAGE_WALK, launch_chained(k_walk_miss<true, true, true>, wgrid, stream, m)); break;
-      case 6: OHM_LAUNCH(OHM_STAGE_WALK, launch_chained(k_walk_miss<true, true, false>, wgrid, stream, m)); break;
-      case 5: OHM_LAUNCH(OHM_STAGE_WALK, launch_chained(k_walk_miss<true, false, true>, wgrid, stream, m)); break;
-      case 4: OHM_LAUNCH(OHM_STAGE_WALK, launch_chained(k_walk_miss<true, false, false>, wgrid, stream, m)); break;
-      case 3: OHM_LAUNCH(OHM_STAGE_WALK, launch_chained(k_walk_miss<false, true, true>, wgrid, stream, m)); break;
-      case 2: OHM_LAUNCH(OHM_STAGE_WALK, launch_chained(k_walk_miss<false, true, false>, wgrid, stream, m)); break;
+      case 3: OHM_LAUNCH(OHM_STAGE_WALK, launch_chained(k_walk_miss<true, true, true>, wgrid, stream, m)); break;
+      case 2: OHM_LAUNCH(OHM_STAGE_WALK, launch_chained(k_walk_miss<true, false, true>, wgrid, stream, m)); break;
+      case 1: OHM_LAUNCH(OHM_STAGE_WALK, launch_chained(k_walk_miss<false, true, true>, wgrid, stream, m)); break;
       default: OHM_LAUNCH(OHM_STAGE_WALK, launch_chained(k_walk_miss<false, false, true>, wgrid, stream, m)); break;
+    }
+  } else if (occ || cnt) {
+    const bool c = walk_needs_cas(m.layers, m.miss, m.ndt_clear);
+    const int sel = (occ ? 4 : 0) | (cnt ? 2 : 0) | (c ? 1 : 0);
+    switch (sel) {
+      case 7: OHM_LAUNCH(OHM_STAGE_WALK, launch_chained(k_walk_fast<true, true, true>, wgrid, stream, m)); break;
+      case 6: OHM_LAUNCH(OHM_STAGE_WALK, launch_chained(k_walk_fast<true, true, false>, wgrid, stream, m)); break;
+      case 5: OHM_LAUNCH(OHM_STAGE_WALK, launch_chained(k_walk_fast<true, false, true>, wgrid, stream, m)); break;
+      case 4: OHM_LAUNCH(OHM_STAGE_WALK, launch_chained(k_walk_fast<true, false, false>, wgrid, stream, m)); break;
+      default: OHM_LAUNCH(OHM_STAGE_WALK, launch_chained(k_walk_fast<false, true, false>, wgrid, stream, m)); break;
     }
   }
   if (occ || cnt || ndt || mean) {
@@ -336,6 +358,89 @@ cudaError_t probe_cas_rate(int device, long long words, long long ops, double* r
   float ms = 0.f;
   if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
   if (e == cudaSuccess) *rate = (double)threads * 4.0 * rounds / (ms * 1e-3);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(buf);
+  return e;
+}
+
+// Probe kernels for ohm_probe_rate; per round each thread touches kProbeInFlight
+// random locations: a float atomic add of 1 to a word (fire and forget), a
+// load then compare-and-swap of a word, or a load of a word of a random
+// 32-byte sector then a store of it plus one (the sector is read from and
+// written back to memory when the buffer is larger than L2).
+constexpr int kProbeInFlight = 8;
+template <int kKind>
+__global__ void __launch_bounds__(kBlock) k_probe(unsigned int* buf, unsigned long long mask, int rounds) {
+  const unsigned long long threads = (unsigned long long)gridDim.x * blockDim.x;
+  const unsigned long long t = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (int r = 0; r < rounds; ++r) {
+    unsigned long long a[kProbeInFlight];
+#pragma unroll
+    for (int j = 0; j < kProbeInFlight; ++j)
+      a[j] = splitmix64_mix(((unsigned long long)r * threads + t) * kProbeInFlight + j) & mask;
+    if (kKind == OHM_PROBE_L2_ADD) {
+#pragma unroll
+      for (int j = 0; j < kProbeInFlight; ++j) atomicAdd(reinterpret_cast<float*>(buf) + a[j], 1.0f);
+    } else {
+      unsigned int old[kProbeInFlight];
+      if (kKind == OHM_PROBE_SECTOR_RMW) {
+#pragma unroll
+        for (int j = 0; j < kProbeInFlight; ++j) a[j] = (a[j] << 3) | (t & 7);  // word t % 8 of sector a
+      }
+#pragma unroll
+      for (int j = 0; j < kProbeInFlight; ++j) old[j] = buf[a[j]];
+#pragma unroll
+      for (int j = 0; j < kProbeInFlight; ++j) {
+        if (kKind == OHM_PROBE_L2_CAS)
+          atomicCAS(buf + a[j], old[j], old[j] + 1u);
+        else
+          buf[a[j]] = old[j] + 1u;
+      }
+    }
+  }
+}
+
+cudaError_t probe_rate(int device, int kind, long long units, long long ops, double* rate) {
+  int sms = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  if (e != cudaSuccess) return e;
+  const int blocks = sms * 8;
+  const unsigned long long threads = (unsigned long long)blocks * kBlock;
+  int rounds = (int)(ops / (long long)(threads * kProbeInFlight));
+  if (rounds < 1) rounds = 1;
+  const long long words = kind == OHM_PROBE_SECTOR_RMW ? units * 8 : units;
+  unsigned int* buf = nullptr;
+  e = cudaMalloc(reinterpret_cast<void**>(&buf), sizeof(unsigned int) * (size_t)words);
+  if (e != cudaSuccess) return e;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  e = cudaMemset(buf, 0, sizeof(unsigned int) * (size_t)words);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  const unsigned long long mask = (unsigned long long)units - 1;
+  auto launch = [&]() {
+    if (kind == OHM_PROBE_L2_ADD)
+      k_probe<OHM_PROBE_L2_ADD><<<blocks, kBlock>>>(buf, mask, rounds);
+    else if (kind == OHM_PROBE_L2_CAS)
+      k_probe<OHM_PROBE_L2_CAS><<<blocks, kBlock>>>(buf, mask, rounds);
+    else
+      k_probe<OHM_PROBE_SECTOR_RMW><<<blocks, kBlock>>>(buf, mask, rounds);
+  };
+  float best = 0.f;
+  if (e == cudaSuccess) {
+    launch();  // warm-up (and L2 fill for the L2-resident kinds)
+    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+      cudaEventRecord(e0);
+      launch();
+      cudaEventRecord(e1);
+      e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess && (best == 0.f || ms < best)) best = ms;
+    }
+  }
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e == cudaSuccess) *rate = (double)threads * kProbeInFlight * rounds / (best * 1e-3);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   cudaFree(buf);

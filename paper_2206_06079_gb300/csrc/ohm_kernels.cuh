@@ -56,12 +56,20 @@ inline void launch_chained(void (*kernel)(K...), unsigned grid, cudaStream_t str
 // a kernel all updates of a voxel use the same delta, so the result does not
 // depend on their order.  The loop is bounded: every failed CAS means another
 // thread advanced the value one step toward its clamp.
+// Log-odds of a stored occupancy word for an update: an unknown voxel (NaN)
+// starts from the prior 0, and a value stored below l_min stands for l_min
+// (the miss walk may leave it there, see walk_segment_fast).
+__device__ __forceinline__ float logodds_value(float s, float l_min) { return s != s ? 0.0f : fmaxf(s, l_min); }
+
+// Log-odds a stored occupancy word reports: NaN stays unknown, a value stored
+// below l_min reads as l_min.
+__device__ __forceinline__ float logodds_read(float s, float l_min) { return s < l_min ? l_min : s; }
+
 __device__ __forceinline__ void logodds_update(const DeviceMap& m, float* p, float delta) {
   unsigned int* u = reinterpret_cast<unsigned int*>(p);
   unsigned int old = *u;
   for (int it = 0; it < 256; ++it) {
-    const float l = __uint_as_float(old);
-    const float l0 = (l != l) ? 0.0f : l;
+    const float l0 = logodds_value(__uint_as_float(old), m.l_min);
     const float nv = fminf(fmaxf(__fadd_rn(l0, delta), m.l_min), m.l_max);
     const unsigned int nb = __float_as_uint(nv);
     if (nb == old) return;
@@ -141,10 +149,7 @@ __device__ __forceinline__ int32_t region_slot_of(const DeviceMap& m, int32_t vx
   return find_region(m, pack_region(vx >> kRegionShift, vy >> kRegionShift, vz >> kRegionShift));
 }
 
-__device__ __forceinline__ uint32_t local_morton(int32_t vx, int32_t vy, int32_t vz) {
-  const int32_t mask = (1 << kRegionShift) - 1;
-  return morton((uint32_t)(vx & mask), (uint32_t)(vy & mask), (uint32_t)(vz & mask));
-}
+__device__ __forceinline__ uint32_t local_morton(int32_t vx, int32_t vy, int32_t vz) { return region_morton(vx, vy, vz); }
 
 // Sample clearing (Sec. II-D): a miss that took voxel `off` from at or above
 // the threshold (or from unknown) to below it clears the voxel's NDT samples.
@@ -165,8 +170,7 @@ __device__ __forceinline__ void after_miss(const DeviceMap& m, long long off, un
 // the value it expected (see logodds_update).
 static __device__ __noinline__ void logodds_retry(const DeviceMap& m, unsigned int* u, unsigned int cur, float delta) {
   for (int it = 0; it < 256; ++it) {
-    const float l = __uint_as_float(cur);
-    const float l0 = (l != l) ? 0.0f : l;
+    const float l0 = logodds_value(__uint_as_float(cur), m.l_min);
     const unsigned int nb = __float_as_uint(fminf(fmaxf(__fadd_rn(l0, delta), m.l_min), m.l_max));
     if (nb == cur) return;
     const unsigned int prev = atomicCAS(u, cur, nb);
@@ -298,11 +302,11 @@ __device__ __forceinline__ void prepare_occ_ray(const DeviceMap& m, const CallAr
         long long dv = (qe[k] >> F) - (qo[k] >> F);
         l1 += dv < 0 ? -dv : dv;
       }
-      const int32_t S = ray_segment_steps(nmaj, l1, m.seg_steps);
-      nseg = (unsigned int)segment_count(nmaj, S);
+      const SegSplit sp = ray_segment_split(nmaj, l1, m.seg_steps);
+      nseg = (unsigned int)sp.nseg;
       const long long am = sel3(M, qe[0] - qo[0], qe[1] - qo[1], qe[2] - qo[2]);
       r.inv = reciprocal64((unsigned long long)(am < 0 ? -am : am));
-      r.flags = kRayValid | (sample ? kRaySample : 0) | (M << kRayAxisShift) | (int32_t)((uint32_t)S << kRaySegShift);
+      r.flags = kRayValid | (sample ? kRaySample : 0) | (M << kRayAxisShift) | (int32_t)((uint32_t)sp.q << kRaySegShift);
       ray_constants(qo, qe, F, &r);
       r.nseg = (int32_t)nseg;
       if (m.layers & kLayerDecay) {
@@ -381,13 +385,15 @@ __device__ __forceinline__ void walk_segment(const DeviceMap& m, long long si, u
   const float miss = m.miss;
   const int2 sg = m.segs[si];
   const RayRec r = m.rays[sg.x];
-  const int32_t S = (int32_t)((uint32_t)r.flags >> kRaySegShift);  // this ray's dominant-axis steps per segment
   const int M = (r.flags >> kRayAxisShift) & 3;
   const bool last = sg.y == r.nseg - 1;
   const bool sample = (r.flags & kRaySample) != 0;
+  long long K0, K1;
+  segment_bounds(M == 0 ? r.n[0] : (M == 1 ? r.n[1] : r.n[2]), r.nseg, (int32_t)((uint32_t)r.flags >> kRaySegShift),
+                 sg.y, &K0, &K1);
   Walker w;
-  walker_init_rec(w, r, F, M, (long long)sg.y * S);
-  int32_t mrem = last ? INT_MAX : S - 1;
+  walker_init_rec(w, r, F, M, K0);
+  int32_t mrem = last ? INT_MAX : (int32_t)(K1 - K0 - 1);
   int32_t slot = region_slot_of(m, w.vx, w.vy, w.vz);
   if (slot < 0) {
     atomicOr(m.status, kStatusMissing);
@@ -399,10 +405,10 @@ __device__ __forceinline__ void walk_segment(const DeviceMap& m, long long si, u
   unsigned long long pos_in = 0;
   if (kDecay) {
     dr = m.decay_rays[sg.x];
-    if (sg.y > 0) {
+    if (K0 > 0) {
       const int32_t d0M = M == 0 ? r.d0[0] : (M == 1 ? r.d0[1] : r.d0[2]);
       const int32_t AM = M == 0 ? r.A[0] : (M == 1 ? r.A[1] : r.A[2]);
-      pos_in = decay_position((long long)d0M + ((long long)(sg.y * S - 1) << F), AM, r.inv, dr.length);
+      pos_in = decay_position((long long)d0M + ((K0 - 1) << F), AM, r.inv, dr.length);
     }
   }
   bool done = false;
@@ -462,8 +468,7 @@ __device__ __forceinline__ void walk_segment(const DeviceMap& m, long long si, u
       for (int j = 0; j < kWalkBatch; ++j) {
         prev[j] = old[j];
         if (!((todo >> j) & 1u)) continue;
-        const float l = __uint_as_float(old[j]);
-        const float l0 = (l != l) ? 0.0f : l;
+        const float l0 = logodds_value(__uint_as_float(old[j]), m.l_min);
         const unsigned int nb = __float_as_uint(fminf(fmaxf(__fadd_rn(l0, miss), m.l_min), m.l_max));
         if (nb == old[j]) continue;
         prev[j] = atomicCAS(base + off[j], old[j], nb);
@@ -475,8 +480,7 @@ __device__ __forceinline__ void walk_segment(const DeviceMap& m, long long si, u
           logodds_retry(m, base + off[j], prev[j], miss);
         } else if ((todo >> j) & 1u) {
           // this thread's CAS applied the miss (or the voxel was already at the clamp)
-          const float l = __uint_as_float(old[j]);
-          const float l0 = (l != l) ? 0.0f : l;
+          const float l0 = logodds_value(__uint_as_float(old[j]), m.l_min);
           const unsigned int nb = __float_as_uint(fminf(fmaxf(__fadd_rn(l0, miss), m.l_min), m.l_max));
           if (nb != old[j]) after_miss(m, off[j], old[j], nb);
         }
@@ -485,18 +489,199 @@ __device__ __forceinline__ void walk_segment(const DeviceMap& m, long long si, u
   }
 }
 
+// Pool slots of two regions (or -1), their first probes issued together.
+__device__ __forceinline__ void find_region2(const DeviceMap& m, long long k1, long long k2, int32_t* s1, int32_t* s2) {
+  const longlong2 e1 = m.htab[hash_key(k1) & m.hmask];
+  const longlong2 e2 = m.htab[hash_key(k2) & m.hmask];
+  *s1 = e1.x == k1 ? (int32_t)e1.y : (e1.x == kEmptyKey ? -1 : find_region(m, k1));
+  *s2 = e2.x == k2 ? (int32_t)e2.y : (e2.x == kEmptyKey ? -1 : find_region(m, k2));
+}
+
+// Out of line: the rare paths of the filtered walk (a near-tie decided
+// exactly from the ray record, a third region inside one segment), so that
+// neither the record nor the hash loop takes registers in the walk.
+static __device__ __noinline__ int exact_pick_rec(const RayRec* rp, int F, int32_t c0, int32_t c1, int32_t c2) {
+  return exact_pick(*rp, F, c0, c1, c2);
+}
+static __device__ __noinline__ int32_t find_region_rare(const DeviceMap& m, long long key) { return find_region(m, key); }
+
+#ifndef OHM_FAST_BATCH
+#define OHM_FAST_BATCH 8
+#endif
+#ifndef OHM_FAST_MIN_BLOCKS
+#define OHM_FAST_MIN_BLOCKS 4
+#endif
+constexpr int kFastBatch = OHM_FAST_BATCH;
+
+// Clamped compare-and-swap miss of one voxel whose word was read as `old`.
+__device__ __forceinline__ void miss_cas(const DeviceMap& m, unsigned int* u, unsigned int old, unsigned int& ops) {
+  const float l0 = logodds_value(__uint_as_float(old), m.l_min);
+  const unsigned int nb = __float_as_uint(fminf(fmaxf(__fadd_rn(l0, m.miss), m.l_min), m.l_max));
+  if (nb == old) return;
+  ++ops;
+  const unsigned int prev = atomicCAS(u, old, nb);
+  if (prev != old)
+    logodds_retry(m, u, prev, m.miss);
+  else
+    after_miss(m, u - reinterpret_cast<unsigned int*>(m.occ), old, nb);
+}
+
+// Miss phase (Sec. III-C phase one) of one segment with the filtered walk
+// (FWalker): every voxel the ray passes through, except the voxel holding its
+// sample, takes one miss.  The segment's first and last regions are looked up
+// together before the walk; a region boundary inside the segment costs a
+// comparison with the last region's key and only a hash lookup when the
+// segment passes through a third region.
+//
+// Occupancy update.  With kCas false (the miss increment is negative and the
+// map does not clear NDT samples) a miss is a fire-and-forget float atomic add
+// of the increment, and the lower clamp is applied where log-odds are read:
+// a voxel's log-odds is max(stored, l_min).  Within a call every miss of a
+// voxel adds the same delta < 0, so whatever the order the adds produce the
+// floats l, fl(l + delta), fl(fl(l + delta) + delta), ...  While they stay at or
+// above l_min these are the values of the clamped one-at-a-time updates
+// l <- min(max(l + delta, l_min), l_max) (Eq. 2 with the clamp of Sec. II-B);
+// once one drops below l_min the clamped sequence stays at l_min (fl(l_min +
+// delta) <= l_min), which is what max(stored, l_min) reads, however far below
+// the later adds take the stored value.  So the result is bit for bit that of
+// the sequential updates.  A voxel already at or below l_min takes no add (a
+// miss leaves it at l_min), and an unknown voxel (NaN) is first set to
+// fl(0 + delta) by compare-and-swap; a thread that loses that race adds its
+// miss to the value it found.  No value comes near the float subnormal range
+// (create rejects increments and bounds below 2^-100 in magnitude), where the
+// atomic add would flush to zero.  With kCas (NDT sample clearing, which must
+// see the update that crosses its threshold, or a miss increment >= 0) every
+// miss is a clamped compare-and-swap.
+template <bool kOcc, bool kCounts, bool kCas>
+__device__ __forceinline__ void walk_segment_fast(const DeviceMap& m, long long si, unsigned int& ops) {
+  const int F = m.frac_bits;
+  const int2 sg = m.segs[si];
+  const RayRec* rp = m.rays + sg.x;
+  FWalker f;
+  uint32_t mo, neg;
+  int32_t rcx, rcy, rcz, sgn, left, slot, slotE;
+  long long keyE;
+  {
+    const RayRec r = *rp;
+    SegStart s;
+    segment_start(r, F, sg.y, &s);
+    const bool last = sg.y == r.nseg - 1;
+    left = (int32_t)s.visits - ((last && (r.flags & kRaySample)) ? 1 : 0);
+    fwalker_init(f, r, F, s.c);
+    neg = morton_neg(r.flags);
+    sgn = (r.flags >> kRaySignShift) & 7;
+    mo = local_morton(s.v[0], s.v[1], s.v[2]) ^ neg;
+    rcx = s.v[0] >> kRegionShift;
+    rcy = s.v[1] >> kRegionShift;
+    rcz = s.v[2] >> kRegionShift;
+    keyE = pack_region(s.ve[0] >> kRegionShift, s.ve[1] >> kRegionShift, s.ve[2] >> kRegionShift);
+    find_region2(m, pack_region(rcx, rcy, rcz), keyE, &slot, &slotE);
+  }
+  if (left <= 0) return;
+  if (slot < 0 || slotE < 0) {
+    atomicOr(m.status, kStatusMissing);
+    return;
+  }
+  uint32_t base = (uint32_t)slot << (3 * kRegionShift);
+  unsigned int* occ = reinterpret_cast<unsigned int*>(m.occ);
+  while (left > 0) {
+    uint32_t off[kFastBatch];  // voxel offsets (< 2^31: at most 2^16 regions of 2^15 voxels)
+    uint32_t valid = 0;
+#pragma unroll
+    for (int j = 0; j < kFastBatch; ++j) {
+      off[j] = base | (mo ^ neg);
+      if (left > 0) {
+        valid |= 1u << j;
+        --left;
+        if (left > 0) {
+          int axis = fwalker_pick(f);
+          if (axis < 0) axis = exact_pick_rec(rp, F, (int32_t)f.cx, (int32_t)f.cy, (int32_t)f.cz);
+          fwalker_advance(f, axis);
+          if (morton_advance(mo, morton_mask(axis))) {
+            const int32_t d = ((sgn >> axis) & 1) ? -1 : 1;
+            if (axis == 0)
+              rcx += d;
+            else if (axis == 1)
+              rcy += d;
+            else
+              rcz += d;
+            const long long key = pack_region(rcx, rcy, rcz);
+            const int32_t ns = key == keyE ? slotE : find_region_rare(m, key);
+            if (ns < 0) {
+              atomicOr(m.status, kStatusMissing);
+              left = 0;
+            } else {
+              base = (uint32_t)ns << (3 * kRegionShift);
+            }
+          }
+        }
+      }
+    }
+    if (kCounts) {
+#pragma unroll
+      for (int j = 0; j < kFastBatch; ++j)
+        if ((valid >> j) & 1u) atomicAdd(m.counts + off[j], 1ULL);
+    }
+    if (kOcc) {
+      unsigned int old[kFastBatch];
+#pragma unroll
+      for (int j = 0; j < kFastBatch; ++j) old[j] = ((valid >> j) & 1u) ? occ[off[j]] : 0u;
+#pragma unroll
+      for (int j = 0; j < kFastBatch; ++j) {
+        if (!((valid >> j) & 1u)) continue;
+        if (kCas) {
+          miss_cas(m, occ + off[j], old[j], ops);
+        } else {
+          const float l = __uint_as_float(old[j]);
+          if (l > m.l_min) {
+            atomicAdd(reinterpret_cast<float*>(occ + off[j]), m.miss);
+            ++ops;
+          } else if (l != l) {
+            ++ops;
+            const unsigned int prev = atomicCAS(occ + off[j], old[j], __float_as_uint(__fadd_rn(0.0f, m.miss)));
+            if (prev != old[j] && __uint_as_float(prev) > m.l_min) {
+              atomicAdd(reinterpret_cast<float*>(occ + off[j]), m.miss);
+              ++ops;
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
+// Whether a map's misses need the compare-and-swap form of walk_segment_fast.
+__device__ __host__ __forceinline__ bool walk_needs_cas(uint32_t layers, float miss, float ndt_clear) {
+  return !(miss < 0.0f) || ((layers & kLayerNdt) && ndt_clear > -INFINITY);
+}
+
 // Miss-phase walk of one segment with the map's layers chosen at run time.
 __device__ __forceinline__ void walk_segment_any(const DeviceMap& m, long long si, unsigned int& cas) {
-  const int sel = ((m.layers & kLayerOcc) ? 4 : 0) | ((m.layers & kLayerCounts) ? 2 : 0) | ((m.layers & kLayerDecay) ? 1 : 0);
-  switch (sel) {
-    case 7: walk_segment<true, true, true>(m, si, cas); break;
-    case 6: walk_segment<true, true, false>(m, si, cas); break;
-    case 5: walk_segment<true, false, true>(m, si, cas); break;
-    case 4: walk_segment<true, false, false>(m, si, cas); break;
-    case 3: walk_segment<false, true, true>(m, si, cas); break;
-    case 2: walk_segment<false, true, false>(m, si, cas); break;
-    case 1: walk_segment<false, false, true>(m, si, cas); break;
-    default: break;
+  const bool occ = (m.layers & kLayerOcc) != 0, cnt = (m.layers & kLayerCounts) != 0;
+  if (m.layers & kLayerDecay) {
+    if (occ && cnt)
+      walk_segment<true, true, true>(m, si, cas);
+    else if (occ)
+      walk_segment<true, false, true>(m, si, cas);
+    else if (cnt)
+      walk_segment<false, true, true>(m, si, cas);
+    else
+      walk_segment<false, false, true>(m, si, cas);
+    return;
+  }
+  const bool c = walk_needs_cas(m.layers, m.miss, m.ndt_clear);
+  if (occ && cnt) {
+    if (c)
+      walk_segment_fast<true, true, true>(m, si, cas);
+    else
+      walk_segment_fast<true, true, false>(m, si, cas);
+  } else if (occ) {
+    if (c)
+      walk_segment_fast<true, false, true>(m, si, cas);
+    else
+      walk_segment_fast<true, false, false>(m, si, cas);
+  } else if (cnt) {
+    walk_segment_fast<false, true, false>(m, si, cas);
   }
 }
 

@@ -27,10 +27,10 @@ _STATUS_NAMES = {ERR_INVALID: "invalid argument", ERR_CAPACITY: "capacity", ERR_
 
 # Every symbol include/ohm_gb.h declares.
 EXPORTED = ["ohm_map_create", "ohm_map_destroy", "ohm_integrate_rays", "ohm_integrate_rays_async", "ohm_map_sync", "ohm_map_status_async", "ohm_probe_cas_rate",
-            "ohm_query_voxels", "ohm_map_region_count", "ohm_map_export", "ohm_map_stats", "ohm_map_profile", "ohm_map_profile_every",
+            "ohm_query_voxels", "ohm_map_region_count", "ohm_map_export", "ohm_map_stats", "ohm_map_profile", "ohm_map_profile_every", "ohm_probe_rate",
             "ohm_map_profile_read", "ohm_last_error", "ohm_count_rays_noalloc", "ohm_batch_create",
             "ohm_batch_destroy", "ohm_batch_tune", "ohm_batch_integrate", "ohm_batch_sync", "ohm_batch_stats",
-            "ohm_integrate_depth", "ohm_tsdf_backward", "ohm_map_evict", "ohm_map_restore_pending",
+            "ohm_integrate_depth", "ohm_tsdf_backward", "ohm_twist_pose", "ohm_map_evict", "ohm_map_restore_pending",
             "ohm_map_restore_all", "ohm_map_residency"]
 
 BATCH_MAX_MAPS = 32
@@ -69,7 +69,7 @@ class MapParams(ctypes.Structure):
         ("segment_steps", ctypes.c_int32),
         ("device", ctypes.c_int32),
         ("evict_when_full", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("max_probe", ctypes.c_int32),
     ]
 
 
@@ -118,6 +118,8 @@ def load_library(path: str = LIB_PATH):
     lib.ohm_map_status_async.argtypes = [vp, p, vp]
     lib.ohm_probe_cas_rate.restype = st
     lib.ohm_probe_cas_rate.argtypes = [ctypes.c_int32, i64, i64, ctypes.POINTER(ctypes.c_double)]
+    lib.ohm_probe_rate.restype = st
+    lib.ohm_probe_rate.argtypes = [ctypes.c_int32, ctypes.c_int32, i64, i64, ctypes.POINTER(ctypes.c_double)]
     lib.ohm_query_voxels.restype = st
     lib.ohm_query_voxels.argtypes = [vp, p, i64, p, p, p, p, p, p, p, vp]
     lib.ohm_map_region_count.restype = st
@@ -154,6 +156,8 @@ def load_library(path: str = LIB_PATH):
     lib.ohm_tsdf_backward.restype = st
     lib.ohm_tsdf_backward.argtypes = [vp, p, ctypes.c_int32, ctypes.c_int32, dp, dp, ctypes.c_double, ctypes.c_double,
                                       p, p, i64, p, p, vp]
+    lib.ohm_twist_pose.restype = st
+    lib.ohm_twist_pose.argtypes = [dp, dp, dp]
     for name in ("ohm_map_evict",):
         f = getattr(lib, name)
         f.restype = st
@@ -192,6 +196,24 @@ def _ptr(x):
     return x.ctypes.data_as(ctypes.c_void_p)
 
 
+_COUNT_DTYPES = (torch.int32,) + ((torch.uint32,) if hasattr(torch, "uint32") else ())
+
+
+def _keep_for_stream(stream, *pairs):
+    """Copies made by _as_points / _as_flags (for contiguity or dtype) go back
+    to torch's caching allocator when the call returns, tied to the current
+    stream; when the work runs on another stream, record that stream on them
+    so their memory is not reused before that work has read it."""
+    if stream is None:
+        return
+    s = stream if isinstance(stream, torch.cuda.Stream) else torch.cuda.ExternalStream(int(stream))
+    if s == torch.cuda.current_stream():
+        return
+    for orig, t in pairs:
+        if isinstance(t, torch.Tensor) and t.is_cuda and t is not orig:
+            t.record_stream(s)
+
+
 def _as_points(x, name):
     if isinstance(x, torch.Tensor):
         t = x.contiguous()
@@ -219,7 +241,7 @@ def default_params(**kw) -> dict:
              hit=float(np.float32(math.log(0.7 / 0.3))), miss=float(np.float32(math.log(0.4 / 0.6))),
              l_min=-2.0, l_max=3.5, ndt_clear_below=float("-inf"), max_range=20.0, min_range=0.0, tsdf_trunc=0.2,
              tsdf_wmax=float(1 << 20), max_regions=4096, max_ndt_regions=1024, max_rays=1 << 18, segment_steps=0, device=0,
-             evict_when_full=0, reserved=0)
+             evict_when_full=0, max_probe=0)
     p.update(kw)
     return p
 
@@ -268,6 +290,7 @@ class Map:
         o = _as_points(origins, "origins")
         e = _as_points(endpoints, "endpoints")
         f = _as_flags(flags)
+        _keep_for_stream(stream, (origins, o), (endpoints, e), (flags, f))
         lib = load_library()
         fn = lib.ohm_integrate_rays if sync else lib.ohm_integrate_rays_async
         _check(fn(self._h, _ptr(o), int(o.shape[0]), _ptr(e), _ptr(f), int(e.shape[0]), _stream_handle(stream)))
@@ -296,6 +319,7 @@ class Map:
         d = depth.contiguous()
         if d.dtype != torch.float32 or not d.is_cuda:
             raise TypeError("depth must be a CUDA float32 tensor")
+        _keep_for_stream(stream, (depth, d))
         k, p = self._frame_args(K, pose)
         h, w = d.shape
         _check(load_library().ohm_integrate_depth(self._h, _ptr(d), int(w), int(h), k, p, float(z_min), float(z_max),
@@ -324,6 +348,7 @@ class Map:
         int64 summed path length in 2^-20 m units, the decay layer; mean:
         (n, 4) float32 voxel-mean position x y z and sample count)."""
         p = _as_points(points, "points")
+        _keep_for_stream(stream, (points, p))
         n = int(p.shape[0])
         dev = self.device
         out = dict(occupancy=torch.empty(n, dtype=torch.float32, device=dev),
@@ -431,12 +456,46 @@ def probe_cas_rate(device=0, words=1 << 28, ops=1 << 26) -> float:
     return float(r.value)
 
 
+PROBE_L2_ADD, PROBE_L2_CAS, PROBE_SECTOR_RMW = 0, 1, 2
+
+
+def probe_rate(kind, units, ops=1 << 28, device=0) -> float:
+    """Operations per second of one of the library's ceiling probes (see
+    ohm_probe_rate): PROBE_L2_ADD, PROBE_L2_CAS or PROBE_SECTOR_RMW."""
+    r = ctypes.c_double()
+    _check(load_library().ohm_probe_rate(int(device), int(kind), int(units), int(ops), ctypes.byref(r)))
+    return float(r.value)
+
+
 def count_rays_noalloc(grid: dict, origins, endpoints, flags, hits, misses, stream=None):
     """Add each ray's per-voxel hit and miss counts into the caller's dense
     uint32 grids `hits` and `misses` (CUDA tensors of dims[0]*dims[1]*dims[2]
     elements, x fastest) without any device allocation by the library.  All
     inputs must be CUDA tensors.  `grid` holds voxel_size, map_origin,
-    frac_bits, segment_steps, max_range, corner and dims (see ohm_count_grid)."""
+    frac_bits, segment_steps, max_range, corner and dims (see ohm_count_grid).
+
+    The C entry point writes to whatever the pointers address, so the sizes
+    are checked here: hits and misses contiguous 32-bit CUDA tensors on the
+    current device with at least prod(dims) elements, flags at least one byte
+    per ray; anything else raises OhmError(ERR_INVALID) before the call."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n_cells = 1
+    for d in grid["dims"]:
+        n_cells *= int(d)
+    for name, t in (("hits", hits), ("misses", misses)):
+        if not isinstance(t, torch.Tensor) or t.device != dev:
+            raise OhmError(ERR_INVALID, "count_rays_noalloc: %s must be a CUDA tensor on the current device" % name)
+        if t.dtype not in _COUNT_DTYPES or not t.is_contiguous():
+            raise OhmError(ERR_INVALID, "count_rays_noalloc: %s must be a contiguous 32-bit integer tensor" % name)
+        if t.numel() < n_cells:
+            raise OhmError(ERR_INVALID, "count_rays_noalloc: %s holds %d elements, the grid has %d voxels"
+                           % (name, t.numel(), n_cells))
+    for name, t in (("origins", origins), ("endpoints", endpoints), ("flags", flags)):
+        if t is not None and (not isinstance(t, torch.Tensor) or t.device != dev):
+            raise OhmError(ERR_INVALID, "count_rays_noalloc: %s must be a CUDA tensor on the current device" % name)
+    n_rays = int(endpoints.numel()) // 3
+    if flags is not None and int(flags.numel()) < n_rays:
+        raise OhmError(ERR_INVALID, "count_rays_noalloc: flags holds %d bytes for %d rays" % (flags.numel(), n_rays))
     g = CountGrid()
     g.voxel_size = float(grid["voxel_size"])
     for i in range(3):
@@ -449,6 +508,7 @@ def count_rays_noalloc(grid: dict, origins, endpoints, flags, hits, misses, stre
     o = _as_points(origins, "origins")
     e = _as_points(endpoints, "endpoints")
     f = _as_flags(flags)
+    _keep_for_stream(stream, (origins, o), (endpoints, e), (flags, f))
     _check(load_library().ohm_count_rays_noalloc(ctypes.byref(g), _ptr(o), int(o.shape[0]), _ptr(e), _ptr(f),
                                                  int(e.shape[0]), _ptr(hits), _ptr(misses), _stream_handle(stream)))
 
@@ -512,18 +572,13 @@ class Batch:
 
 
 def twist_pose(xi, pose0):
-    """exp(xi) applied on the left of a 3 x 4 camera-to-world pose (float64 numpy)."""
-    xi = np.asarray(xi, np.float64)
-    rho, phi = xi[:3], xi[3:]
-    th = float(np.linalg.norm(phi))
-    Kx = np.array([[0, -phi[2], phi[1]], [phi[2], 0, -phi[0]], [-phi[1], phi[0], 0]])
-    if th < 1e-12:
-        R, V = np.eye(3) + Kx, np.eye(3) + 0.5 * Kx
-    else:
-        R = np.eye(3) + np.sin(th) / th * Kx + (1 - np.cos(th)) / th ** 2 * Kx @ Kx
-        V = np.eye(3) + (1 - np.cos(th)) / th ** 2 * Kx + (th - np.sin(th)) / th ** 3 * Kx @ Kx
-    P0 = np.asarray(pose0, np.float64).reshape(3, 4)
-    return np.concatenate([R @ P0[:, :3], (R @ P0[:, 3] + V @ rho)[:, None]], 1)
+    """exp(xi) applied on the left of a 3 x 4 camera-to-world pose, computed
+    by the library (ohm_twist_pose); float64 numpy (3, 4)."""
+    x = (ctypes.c_double * 6)(*[float(v) for v in np.asarray(xi, np.float64).reshape(6)])
+    p0 = (ctypes.c_double * 12)(*[float(v) for v in np.asarray(pose0, np.float64).reshape(12)])
+    out = (ctypes.c_double * 12)()
+    _check(load_library().ohm_twist_pose(x, p0, out))
+    return np.array(out[:], np.float64).reshape(3, 4)
 
 
 class TsdfFrame(torch.autograd.Function):

@@ -21,7 +21,7 @@ def room_params(**kw):
     """Single room scan: 32,768 rays, occupancy, 0.1 m voxels, 20 m range."""
     p = dict(voxel_size=0.1, map_origin=(0.0, 0.0, 0.0), frac_bits=16, layers=OCC, hit=HIT, miss=MISS,
              l_min=-2.0, l_max=3.5, ndt_clear_below=float("-inf"), max_range=20.0, min_range=0.0, tsdf_trunc=0.2, tsdf_wmax=float(1 << 20),
-             max_regions=1024, max_ndt_regions=1024, max_rays=32768, segment_steps=0, device=0, evict_when_full=0, reserved=0)
+             max_regions=1024, max_ndt_regions=1024, max_rays=32768, segment_steps=0, device=0, evict_when_full=0, max_probe=0)
     p.update(kw)
     return p
 
@@ -36,7 +36,7 @@ def tunnel_params(**kw):
     missing returns."""
     p = dict(voxel_size=0.1, map_origin=(0.0, 0.0, 0.0), frac_bits=16, layers=OCC | NDT, hit=HIT, miss=MISS,
              l_min=-2.0, l_max=3.5, ndt_clear_below=float("-inf"), max_range=50.0, min_range=0.0, tsdf_trunc=0.2, tsdf_wmax=float(1 << 20),
-             max_regions=24576, max_ndt_regions=4096, max_rays=131072, segment_steps=0, device=0, evict_when_full=0, reserved=0)
+             max_regions=24576, max_ndt_regions=4096, max_rays=131072, segment_steps=0, device=0, evict_when_full=0, max_probe=0)
     p.update(kw)
     return p
 
@@ -52,7 +52,7 @@ def tsdf_params(**kw):
     """Depth-camera TSDF: 640 x 480 frames, 0.05 m voxels, tau = 0.2 m."""
     p = dict(voxel_size=0.05, map_origin=(0.0, 0.0, 0.0), frac_bits=16, layers=TSDF, hit=HIT, miss=MISS,
              l_min=-2.0, l_max=3.5, ndt_clear_below=float("-inf"), max_range=10.0, min_range=0.0, tsdf_trunc=0.2, tsdf_wmax=float(1 << 20),
-             max_regions=2048, max_ndt_regions=1, max_rays=640 * 480, segment_steps=0, device=0, evict_when_full=0, reserved=0)
+             max_regions=2048, max_ndt_regions=1, max_rays=640 * 480, segment_steps=0, device=0, evict_when_full=0, max_probe=0)
     p.update(kw)
     return p
 

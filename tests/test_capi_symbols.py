@@ -94,3 +94,43 @@ def test_sampled_profiling_rejects_bad_arguments_without_a_device():
     lib = ohm.load_library()
     assert lib.ohm_map_profile_every(None, 0, 2) == ohm.ERR_INVALID
     assert b"NULL" in lib.ohm_last_error()
+
+
+def _doc_before(name):
+    """The comment block right before a declaration in the header."""
+    text = open(HEADER).read()
+    i = re.search(r"\n[a-z][^\n]*[ *]%s\(" % name, text).start()  # the declaration line
+    head = text[:i]
+    j = head.rindex("/*")
+    k = head.rindex("*/")
+    assert k > j and text[k + 2:i].count(";") == 0, name
+    return head[j:k]
+
+
+def test_boundary_declarations_cite_the_paper():
+    """Every entry point of the method's boundary (create, integrate, query,
+    export, destroy, error report) names the passage that defines it."""
+    for name in ("ohm_map_create", "ohm_integrate_rays", "ohm_query_voxels", "ohm_map_export",
+                 "ohm_map_destroy", "ohm_last_error"):
+        assert "Sec." in _doc_before(name), name
+
+
+def test_twist_pose_is_the_rigid_motion_of_the_twist():
+    """ohm_twist_pose (library host code) against the oracle's exponential of
+    the twist, from zero rotation through small angles to large ones, and the
+    result's rotation is orthonormal."""
+    import numpy as np
+    from oracle import adjoint
+    build_lib.build()
+    rng = np.random.default_rng(0)
+    for s in (0.0, 1e-13, 1e-6, 1e-3, 0.7, 2.5, 3.1):
+        xi = rng.normal(size=6)
+        xi[3:] *= (s / np.linalg.norm(xi[3:])) if s else 0.0
+        P0 = np.concatenate([np.linalg.qr(rng.normal(size=(3, 3)))[0], rng.normal(size=(3, 1))], 1)
+        T = adjoint.twist_matrix(xi)
+        ref = np.concatenate([T[:3, :3] @ P0[:, :3], (T[:3, :3] @ P0[:, 3] + T[:3, 3])[:, None]], 1)
+        got = ohm.twist_pose(xi, P0)
+        assert np.abs(got - ref).max() < 1e-12, s
+        if s > 1e-6:
+            R = got[:, :3]
+            assert np.abs(R @ R.T - np.eye(3)).max() < 1e-12

@@ -86,11 +86,21 @@ def test_gpu_adjoint_matches_oracle(size):
     assert scale > 0
     err = np.abs(gd - gz_ref)
     assert np.linalg.norm(gd - gz_ref) <= 1e-3 * np.linalg.norm(gz_ref)
-    big = np.abs(gz_ref) > 1e-2 * scale
-    # per pixel: relative 1e-3; a pixel may differ where float32 and float64
-    # disagree on whether one of its voxels sits exactly at the clamp
-    frac_ok = np.mean(err[big] <= 1e-3 * np.abs(gz_ref[big]) + 1e-6 * scale)
-    assert frac_ok >= 0.995, frac_ok
+    # per pixel: relative 1e-3.  The only pixels exempt are those whose band
+    # holds a voxel with |s| within KINK of the clamp at +-tau, where the
+    # GPU (float32 s from the quantised ray) and the oracle (float64 s at the
+    # continuous geometry) may disagree on whether that voxel is clamped:
+    # quantisation moves a point by at most half a 2^-16-voxel unit (4e-7 m)
+    # and float32 s is good to about 1e-7 m here, so KINK = 2e-6 m is safe.
+    KINK = 2e-6
+    bad = np.flatnonzero(err > 1e-3 * np.abs(gz_ref) + 1e-6 * scale)
+    margin = adjoint.band_margin(om, o[0], e, f, o64, e64)
+    kinked = np.flatnonzero(margin < KINK)
+    unexplained = np.setdiff1d(bad, kinked)
+    assert len(unexplained) == 0, ("%d pixels off by more than 1e-3 without a voxel at the clamp "
+                                   "(%d off in all, %d pixels with a voxel within %g m of the clamp)"
+                                   % (len(unexplained), len(bad), len(kinked), KINK))
+    assert len(kinked) <= 0.01 * len(gz_ref), (len(kinked), len(gz_ref))
     assert np.linalg.norm(gxi - gxi_ref) <= 1e-3 * np.linalg.norm(gxi_ref), (gxi, gxi_ref)
 
 
@@ -135,7 +145,7 @@ def test_gpu_adjoint_against_finite_differences():
         Lp = adjoint.frame_eval(om, o[0], e, f, Tp[:3, :3] @ o64 + Tp[:3, 3], e64 @ Tp[:3, :3].T + Tp[:3, 3], qvox, g64)[0]
         Lm = adjoint.frame_eval(om, o[0], e, f, Tm[:3, :3] @ o64 + Tm[:3, 3], e64 @ Tm[:3, :3].T + Tm[:3, 3], qvox, g64)[0]
         fdxi[k] = (Lp - Lm) / (2 * hstep)
-    assert np.linalg.norm(gxi.cpu().numpy() - fdxi) <= 2e-3 * np.linalg.norm(fdxi), (gxi, fdxi)
+    assert np.linalg.norm(gxi.cpu().numpy() - fdxi) <= 1e-3 * np.linalg.norm(fdxi), (gxi, fdxi)
 
 
 def test_autograd_function_wraps_the_kernel():

@@ -116,8 +116,7 @@ def test_tsdf_frames(size):
     p = W.tsdf_params(max_rays=w * h)
     gm, om = _pair(p)
     scene = synth.depth_scene()
-    frames = 3 if w < 640 else 1
-    for i in range(frames):
+    for i in range(3):
         rays = W.tsdf_rays(i * 7, width=w, height=h, scene=scene)
         visits = _integrate_both(gm, om, rays)
         assert gm.stats()["visits"] == visits
@@ -240,6 +239,31 @@ def test_ndt_pool_exhaustion_leaves_map_unchanged():
     _integrate_both(gm, om, tiny)
     compare_dense(gm, om, counts=False)
     compare_ndt(gm, om)
+
+
+def test_hash_probe_limit_leaves_map_unchanged():
+    """A tiny probe bound (max_probe = 1: every region key must sit in its
+    home bucket) makes the bounded insertion give up as soon as two of a
+    call's region keys share a bucket.  The call returns OHM_ERR_PROBE_LIMIT,
+    changes nothing, and the map keeps matching the oracle that never saw it."""
+    p = W.room_params(layers=W.OCC | W.COUNTS, max_regions=4096, max_probe=1)
+    gm, om = _pair(p)
+    tiny = synth.room_scan(n=500, room_min=(-0.5, -0.5, 0.5), room_max=(0.5, 0.5, 1.5))
+    _integrate_both(gm, om, tiny)
+    before = gm.export(counts=True)
+    n_before = gm.region_count()
+    # rays to the walls of a 40 x 40 x 10 m box pass through a few hundred of
+    # the 8192 buckets' keys: a shared bucket is all but certain
+    big = synth.room_scan(seed=3, n=32768, room_min=(-20, -20, -5), room_max=(20, 20, 5))
+    with pytest.raises(ohm.OhmError) as ei:
+        gm.integrate(*big.numpy())
+    assert ei.value.code == ohm.ERR_PROBE_LIMIT
+    assert gm.region_count() == n_before
+    after = gm.export(counts=True)
+    assert torch.equal(before["occupancy"].view(torch.int32), after["occupancy"].view(torch.int32))
+    assert torch.equal(before["counts"], after["counts"])
+    _integrate_both(gm, om, tiny)
+    compare_dense(gm, om)
 
 
 @pytest.mark.parametrize("thr", [-1.0, 0.5])

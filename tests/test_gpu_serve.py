@@ -1,14 +1,15 @@
 """Served stream: continuous batching of mixed-sensor scans from several
 robots into resident maps gives, map for map, exactly what integrating each
 robot's scans alone and in order gives -- with and without eviction to host
-memory."""
+memory -- and that is what the oracle computes from the same scans."""
 import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_2206_06079_gb300 import ohm, serve, synth, workloads as W
 
-from .parity import assert_maps_identical
+from .parity import assert_maps_identical, compare_dense, compare_ndt
 
 pytestmark = pytest.mark.gpu
 
@@ -55,6 +56,14 @@ def test_served_maps_equal_maps_integrated_alone(budget):
     for a, b in zip(served, alone):
         a.restore_all()
         assert_maps_identical(a, b)
+    # one served map (a different robot for each budget) against the oracle fed
+    # that robot's scans in arrival order
+    rb = 0 if budget is None else 1
+    om = oracle.OracleMap(**W.oracle_params(_params()))
+    for r in sorted((r for r in reqs if r.map_index == rb), key=lambda r: r.arrival):
+        om.integrate(*(t.cpu().numpy() for t in r.rays))
+    compare_dense(served[rb], om, counts=False)
+    compare_ndt(served[rb], om)
 
 
 def test_realtime_loop_reports_latency():

@@ -21,11 +21,15 @@ def checker(tmp_path_factory):
     return exe
 
 
-def _run(exe, rays, F=16, S=64, inv=False):
+_EXIT = {2: "Morton mismatch", 3: "bad ray record", 4: "region tracking mismatch", 5: "segment end / visit count mismatch"}
+
+
+def _run(exe, rays, F=16, S=64, mode="plain", stats=None):
     lines = ["%d %d %d" % (F, S, len(rays))] + ["%d %d %d %d %d %d" % tuple(int(v) for v in (*a, *b)) for a, b in rays]
-    args = [exe, "inv"] if inv else [exe]
-    out = subprocess.run(args, input="\n".join(lines) + "\n", capture_output=True, text=True)
-    assert out.returncode == 0, "walker check exited %d (Morton mismatch = 2)" % out.returncode
+    out = subprocess.run([exe, mode], input="\n".join(lines) + "\n", capture_output=True, text=True)
+    assert out.returncode == 0, "walker check exited %d (%s)" % (out.returncode, _EXIT.get(out.returncode, "?"))
+    if stats is not None:
+        stats["exact"] = int(out.stderr.split()[1])
     tok = out.stdout.split()
     res, i = [], 0
     for _ in rays:
@@ -53,30 +57,52 @@ def _rays(seed, n, lattice):
     return out
 
 
-@pytest.mark.parametrize("S", [1, 2, 5, 8, 64, 1 << 20])
+@pytest.mark.parametrize("S", [1, 2, 5, 8, 24, 64, 1 << 20])
 @pytest.mark.parametrize("lattice", [False, True])
-@pytest.mark.parametrize("inv", [False, True])
-def test_device_walker_matches_oracle(checker, S, lattice, inv):
+@pytest.mark.parametrize("mode", ["plain", "rec", "fast"])
+def test_device_walker_matches_oracle(checker, S, lattice, mode):
     rays = _rays(100 + S + lattice, 150, lattice)
-    got = _run(checker, rays, S=S, inv=inv)
+    stats = {}
+    got = _run(checker, rays, S=S, mode=mode, stats=stats)
     for (a, b), g in zip(rays, got):
         assert np.array_equal(g, oracle.walk(a, b)), (a, b)
+    if mode == "fast" and lattice:
+        # lattice rays are full of exact ties: the exact fallback must have run
+        assert stats["exact"] > 0
+
+
+def test_fast_walk_near_ties(checker):
+    """Rays whose crossings along two axes come within a few fixed-point units
+    of each other (end points one unit off exact diagonals and lattice
+    points): the FP32 filter must hand these to the exact rule."""
+    rng = np.random.default_rng(11)
+    rays = []
+    for _ in range(400):
+        a = rng.integers(-20, 20, size=3) * U + rng.integers(0, U, size=3)
+        d = rng.integers(-150, 150) * U
+        b = a + np.array([d, d, rng.integers(-150, 150) * U]) + rng.integers(-2, 3, size=3)
+        rays.append((a, b))
+    stats = {}
+    for S in (3, 24):
+        for (a, b), g in zip(rays, _run(checker, rays, S=S, mode="fast", stats=stats)):
+            assert np.array_equal(g, oracle.walk(a, b)), (a, b)
+    assert stats["exact"] > 0
 
 
 def test_golden_ties_through_device_walker(checker):
     import json
     spec = json.load(open(os.path.join(HERE, "golden", "walk_ties.json")))
     rays = [(np.array(c["a"]), np.array(c["b"])) for c in spec["cases"]]
-    for S, inv in ((1, False), (1, True), (64, True)):
-        for c, g in zip(spec["cases"], _run(checker, rays, S=S, inv=inv)):
-            assert g.tolist() == c["visits"], c["name"]
+    for S, mode in ((1, "plain"), (1, "rec"), (64, "rec"), (1, "fast"), (3, "fast"), (64, "fast")):
+        for c, g in zip(spec["cases"], _run(checker, rays, S=S, mode=mode)):
+            assert g.tolist() == c["visits"], (c["name"], mode, S)
 
 
 def test_region_resolution_walk_covers_voxel_regions(checker):
     """The region pass walks the same line with 2^(F+5) units; it must visit
     exactly the regions of the voxels the voxel walk visits."""
     rays = _rays(7, 200, True) + _rays(8, 200, False)
-    reg = _run(checker, rays, F=16 + 5, S=1 << 20)
+    reg = _run(checker, rays, F=16 + 5, S=1 << 20, mode="plain")
     for (a, b), r in zip(rays, reg):
         v = oracle.walk(a, b)
         want = []

@@ -69,3 +69,27 @@ def test_noalloc_rejects_what_it_cannot_hold():
     e = torch.zeros((ohm.NOALLOC_MAX_RAYS, 3), dtype=torch.float32, device="cuda")
     with pytest.raises(ohm.OhmError):
         ohm.count_rays_noalloc(far, e[:1], e, None, h, m)
+
+
+def test_noalloc_wrapper_checks_caller_buffers():
+    """The C entry point cannot see the sizes of caller buffers; the binding
+    rejects short, strided or wrongly typed outputs and short flags before
+    anything is enqueued."""
+    grid = dict(voxel_size=0.1, map_origin=(0.0, 0.0, 0.0), frac_bits=16, segment_steps=0, max_range=20.0,
+                corner=(0, 0, 0), dims=(8, 8, 8))
+    rays = synth.room_scan(seed=5, n=64)
+    o, e = rays.origins.cuda(), rays.endpoints.cuda()
+    ok = torch.zeros(512, dtype=torch.int32, device="cuda")
+    bad_outputs = [torch.zeros(511, dtype=torch.int32, device="cuda"),            # short
+                   torch.zeros(1024, dtype=torch.int32, device="cuda")[::2],       # strided
+                   torch.zeros(512, dtype=torch.int64, device="cuda"),             # 64-bit
+                   torch.zeros(512, dtype=torch.int32)]                            # host
+    for bad in bad_outputs:
+        for args in ((bad, ok), (ok, bad)):
+            with pytest.raises(ohm.OhmError) as ei:
+                ohm.count_rays_noalloc(grid, o, e, None, *args)
+            assert ei.value.code == ohm.ERR_INVALID
+    with pytest.raises(ohm.OhmError) as ei:
+        ohm.count_rays_noalloc(grid, o, e, torch.zeros(63, dtype=torch.uint8, device="cuda"), ok, ok.clone())
+    assert ei.value.code == ohm.ERR_INVALID and "flags" in str(ei.value)
+    assert int(ok.abs().sum()) == 0  # nothing ran
