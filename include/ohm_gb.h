@@ -106,7 +106,9 @@ typedef struct {
 /* Create a map (Sec. III-A: a map is a sparse set of regions of 32^3 voxels,
  * each region holding one contiguous block per layer, found from its region
  * key in O(1)).  Fills `*out` on success.  Allocates the region pool, the
- * region hash table (capacity: the next power of two >= 2 * max_regions), the
+ * region hash table (capacity: the next power of two >= 2 * max_regions, and
+ * at least 2^18 entries with evict_when_full, since evicted regions keep their
+ * keys), the
  * enabled layers and per-call scratch sized for max_rays, on `device`.
  * Errors: OHM_ERR_INVALID for out-of-range parameters (including
  * max_range * 2^frac_bits / voxel_size >= 2^30, which would overflow the exact
@@ -360,6 +362,42 @@ ohm_status ohm_tsdf_backward(ohm_map* map, const float* depth, int32_t width, in
                              const double* intrinsics, const double* pose, double z_min, double z_max,
                              const float* query_points, const float* grad_query, int64_t n_query, float* grad_depth,
                              double* grad_twist, void* stream);
+
+/* Integrate one ray set given in a sensor frame: origins (n_origins = 1 or
+ * n) and endpoints are moved to the world by pose (3 x 4 row-major
+ * camera-to-world [R | t], host), p_k = ((R_k0 x + R_k1 y) + R_k2 z) + t_k in
+ * double with one rounding per operation, rounded to float, then integrated as
+ * by ohm_integrate_rays_async (Sec. III-B).  All ray arrays are device memory;
+ * n must not exceed max_rays.  Returns once enqueued; failures are reported by
+ * ohm_map_sync. */
+ohm_status ohm_integrate_posed(ohm_map* map, const double* pose, const float* origins, int64_t n_origins,
+                               const float* endpoints, const uint8_t* flags, int64_t n, void* stream);
+
+/* Adjoint of the NDT-OM statistics (Sec. II-D, III-C: per voxel the mean and
+ * the population covariance of its samples) for the ray set just integrated by
+ * ohm_integrate_posed with the same arguments.  With mean(v) and C(v) after
+ * that call, it computes the gradient of
+ *   L = sum_q grad_mean[q] . mean(v_q) + grad_cov[q] . C(v_q)
+ * (query_points: n_query x 3 world points; grad_mean n_query x 3; grad_cov
+ * n_query x 6, packed xx xy xz yy yz zz; queries of voxels without samples
+ * contribute nothing) with respect to every ray's sensor-frame endpoint
+ * (grad_endpoints, n x 3 floats; zero for rays without a sample) and to the
+ * pose as a left twist xi = (rho, phi) moving each world point p to
+ * p + rho + phi x p (grad_twist, 6 doubles), holding fixed which rays carry a
+ * sample and the voxel of each sample: for sample j in a voxel with n samples
+ * summing to S (positions relative to the voxel's corner),
+ *   dL/dp_j = (1/n) [gm + (G + G^T)(p_j - S/n)],  G = upper-triangular(gc),
+ * with p_j and S the stored (fixed-point) positions.  Each ray's quantisation
+ * is recomputed, nothing is stored by the forward pass.  Call it before any
+ * other integration into the map.  Needs the NDT layer and ndt_clear_below =
+ * -INFINITY (OHM_ERR_UNSUPPORTED otherwise: sample clearing changes the
+ * statistics discontinuously).  The first call allocates 36 bytes of weights
+ * per voxel of the NDT pool.  All arrays are device memory except pose.
+ * Returns once enqueued.  The paper has no counterpart. */
+ohm_status ohm_ndt_backward(ohm_map* map, const double* pose, const float* origins, int64_t n_origins,
+                            const float* endpoints, const uint8_t* flags, int64_t n, const float* query_points,
+                            const float* grad_mean, const float* grad_cov, int64_t n_query, float* grad_endpoints,
+                            double* grad_twist, void* stream);
 
 /* The pose exp(xi) pose0 of the adjoint's pose parametrisation: the left
  * twist xi = (rho, phi) (6 doubles) as a rigid motion (rotation by Rodrigues'

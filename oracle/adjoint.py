@@ -1,7 +1,8 @@
-"""TSDF adjoint reference (TEST INFRASTRUCTURE ONLY): depth-image rays, the
-chain rule from endpoint / origin gradients to per-pixel depth and pose-twist
-gradients, and finite differences, in float64 numpy around the C++ oracle's
-frozen-voxel-set loss (oracle_tsdf_frame_eval).
+"""TSDF and NDT-OM adjoint references (TEST INFRASTRUCTURE ONLY): depth-image
+and posed lidar rays, the chain rule from endpoint / origin gradients to
+per-pixel depth and pose-twist gradients, in float64 numpy around the C++
+oracle's frozen-voxel-set losses (oracle_tsdf_frame_eval,
+oracle_ndt_frame_eval).
 
 Depth back-projection (the same formula, operation for operation, as the CUDA
 library's depth entry point): for pixel (u, v) with depth z,
@@ -70,6 +71,56 @@ def frame_eval(omap, o_nom, e_nom, flags, o_eval, e_eval, qvox, g):
     if rc:
         raise ValueError("oracle_tsdf_frame_eval failed")
     return loss.value, ge, go
+
+
+def posed_rays(origins, endpoints, pose):
+    """Sensor-frame float rays moved to the world by a 3 x 4 camera-to-world
+    pose [R | t], the same formula, operation for operation, as the CUDA
+    library's posed entry point: p_k = ((R_k0 x + R_k1 y) + R_k2 z) + t_k in
+    double, stored as float32.  Returns (origins, endpoints) float32 and the
+    endpoints before rounding (float64)."""
+    P = np.asarray(pose, np.float64).reshape(3, 4)
+
+    def move(x):
+        x = np.asarray(x, np.float32).reshape(-1, 3).astype(np.float64)
+        out = np.empty_like(x)
+        for k in range(3):
+            out[:, k] = ((P[k, 0] * x[:, 0] + P[k, 1] * x[:, 1]) + P[k, 2] * x[:, 2]) + P[k, 3]
+        return out
+    o64, e64 = move(origins), move(endpoints)
+    return o64.astype(np.float32), e64.astype(np.float32), e64
+
+
+def ndt_frame_eval(omap, o_nom, e_nom, flags, e_eval, qvox, gm, gc):
+    """(L, dL/de (n, 3)) of the NDT-OM frame loss from the C++ oracle
+    (oracle_ndt_frame_eval), float64.  o_nom: one origin or one per ray."""
+    o_nom = np.ascontiguousarray(o_nom, np.float32).reshape(-1, 3)
+    e_nom = np.ascontiguousarray(e_nom, np.float32).reshape(-1, 3)
+    n = e_nom.shape[0]
+    f = np.ascontiguousarray(flags, np.uint8) if flags is not None else np.zeros(n, np.uint8)
+    e_eval = np.ascontiguousarray(e_eval, np.float64).reshape(-1, 3)
+    qvox = np.ascontiguousarray(qvox, np.int64).reshape(-1, 3)
+    gm = np.ascontiguousarray(gm, np.float64).reshape(-1, 3)
+    gc = np.ascontiguousarray(gc, np.float64).reshape(-1, 6)
+    loss = ctypes.c_double()
+    ge = np.zeros((n, 3), np.float64)
+    lib = _load()
+    lib.oracle_ndt_frame_eval.restype = ctypes.c_int
+    lib.oracle_ndt_frame_eval.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64] + [ctypes.c_void_p] * 2 + \
+        [ctypes.c_int64] + [ctypes.c_void_p] * 4 + [ctypes.c_int64] + [ctypes.c_void_p] * 2
+    rc = lib.oracle_ndt_frame_eval(omap._h, _ptr(o_nom), o_nom.shape[0], _ptr(e_nom), _ptr(f), n, _ptr(e_eval),
+                                   _ptr(qvox), _ptr(gm), _ptr(gc), qvox.shape[0], ctypes.byref(loss), _ptr(ge))
+    if rc:
+        raise ValueError("oracle_ndt_frame_eval failed")
+    return loss.value, ge
+
+
+def twist_from_point_gradients(points, grad):
+    """Gradient with respect to a left twist (rho, phi) moving every point p
+    to p + rho + phi x p, from per-point gradients: (sum g, sum p x g)."""
+    points = np.asarray(points, np.float64).reshape(-1, 3)
+    grad = np.asarray(grad, np.float64).reshape(-1, 3)
+    return np.concatenate([grad.sum(0), np.cross(points, grad).sum(0)])
 
 
 def band_margin(omap, o_nom, e_nom, flags, o_eval, e_eval):

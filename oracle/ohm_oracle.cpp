@@ -824,6 +824,122 @@ int oracle_tsdf_frame_eval(void* h, const float* o_nom, const float* e_nom, cons
   return 0;
 }
 
+// NDT-OM adjoint (Sec. II-D / III-C sample statistics; the voxel assignment
+// of every sample held fixed).
+//
+// The nominal float rays fix, through the quantisation and truncation of
+// oracle_integrate, which rays carry a sample and the voxel v_j of each.  At
+// continuous sample positions e_eval (world metres, double) the NDT state of
+// a voxel v after the frame is, relative to its lower corner c(v),
+//   n = n0 + #{j: v_j = v},  S = S0 + sum_j (e_j - c),  Q = Q0 + sum_j (e_j - c)(e_j - c)^T,
+//   mean = c + S / n,  C = Q / n - (S / n)(S / n)^T      (population covariance)
+// with n0, S0, Q0 the map's moments before the frame (the map's integer sums
+// scaled to metres; the map is not modified).  For query voxels v_q with
+// weights gm_q (3) and gc_q (6, packed xx xy xz yy yz zz)
+//   L = sum_q [ gm_q . mean(v_q) + gc_q . packed C(v_q) ]     (n(v_q) > 0; else 0)
+// and, with d_j = e_j - c - S / n and G the upper-triangular matrix of the
+// summed gc of v_j's queries,
+//   dL/de_j = (1/n) [ gm + (G + G^T) d_j ].
+// grad_e: n x 3 (zeros for rays without a sample).  Returns 0, or -1 on bad
+// arguments or a map without the NDT layer.
+int oracle_ndt_frame_eval(void* h, const float* o_nom, int64_t n_origins, const float* e_nom, const uint8_t* flags,
+                          int64_t n, const double* e_eval, const int64_t* qvox, const double* gm, const double* gc,
+                          int64_t m_q, double* loss, double* grad_e) {
+  Map& m = *static_cast<Map*>(h);
+  if (!(m.p.layers & kLayerNdt) || (n_origins != 1 && n_origins != n)) return -1;
+  typedef std::tuple<int64_t, int64_t, int64_t> Key;
+  const double cell = m.p.voxel_size / (double)m.unit;  // metres per fixed-point unit
+  // the frame's samples and their voxels
+  std::vector<int> has(n, 0);
+  std::vector<Voxel> vox((size_t)n);
+  for (int64_t j = 0; j < n; ++j) {
+    PreparedRay r;
+    const float* o = o_nom + (n_origins == 1 ? 0 : 3 * j);
+    if (!prepare_ray(m, o, e_nom + 3 * j, flags ? flags[j] : 0, &r) || !r.has_sample) continue;
+    for (int a = 0; a < 3; ++a) vox[(size_t)j].v[a] = floor_div(r.qe[a], m.unit);
+    has[(size_t)j] = 1;
+  }
+  // per voxel: n, S (3), Q (3 x 3) in metres relative to the corner
+  struct Stat {
+    double n = 0.0, S[3] = {0.0, 0.0, 0.0}, Q[3][3] = {{0.0}};
+  };
+  std::map<Key, Stat> stat;
+  auto corner = [&](const Voxel& v, int a) { return m.p.map_origin[a] + (double)v.v[a] * m.p.voxel_size; };
+  auto stat_of = [&](const Voxel& v) -> Stat& {
+    const Key k = std::make_tuple(v.v[0], v.v[1], v.v[2]);
+    auto it = stat.find(k);
+    if (it != stat.end()) return it->second;
+    Stat s;
+    auto rit = m.regions.find(region_of(v));
+    if (rit != m.regions.end() && !rit->second.ndt.empty()) {
+      const __int128* q = &rit->second.ndt[(size_t)local_index(v) * 10];
+      s.n = (double)q[0];
+      for (int a = 0; a < 3; ++a) s.S[a] = (double)q[1 + a] * cell;
+      const int pa[6] = {0, 0, 0, 1, 1, 2}, pb[6] = {0, 1, 2, 1, 2, 2};
+      for (int k6 = 0; k6 < 6; ++k6) {
+        s.Q[pa[k6]][pb[k6]] = (double)q[4 + k6] * cell * cell;
+        s.Q[pb[k6]][pa[k6]] = s.Q[pa[k6]][pb[k6]];
+      }
+    }
+    return stat.emplace(k, s).first->second;
+  };
+  for (int64_t j = 0; j < n; ++j) {
+    if (!has[(size_t)j]) continue;
+    Stat& s = stat_of(vox[(size_t)j]);
+    double p[3];
+    for (int a = 0; a < 3; ++a) p[a] = e_eval[3 * j + a] - corner(vox[(size_t)j], a);
+    s.n += 1.0;
+    for (int a = 0; a < 3; ++a) {
+      s.S[a] += p[a];
+      for (int b = 0; b < 3; ++b) s.Q[a][b] += p[a] * p[b];
+    }
+  }
+  // upstream weights per voxel, summed over its queries
+  std::map<Key, std::array<double, 9>> G;
+  for (int64_t q = 0; q < m_q; ++q) {
+    auto& g = G[std::make_tuple(qvox[3 * q], qvox[3 * q + 1], qvox[3 * q + 2])];
+    for (int a = 0; a < 3; ++a) g[a] += gm[3 * q + a];
+    for (int k6 = 0; k6 < 6; ++k6) g[3 + k6] += gc[6 * q + k6];
+  }
+  const int pa[6] = {0, 0, 0, 1, 1, 2}, pb[6] = {0, 1, 2, 1, 2, 2};
+  double L = 0.0;
+  for (const auto& kv : G) {
+    Voxel v;
+    v.v[0] = std::get<0>(kv.first);
+    v.v[1] = std::get<1>(kv.first);
+    v.v[2] = std::get<2>(kv.first);
+    const Stat& s = stat_of(v);
+    if (!(s.n > 0.0)) continue;
+    double mu[3];
+    for (int a = 0; a < 3; ++a) mu[a] = s.S[a] / s.n;
+    for (int a = 0; a < 3; ++a) L += kv.second[a] * (corner(v, a) + mu[a]);
+    for (int k6 = 0; k6 < 6; ++k6)
+      L += kv.second[3 + k6] * (s.Q[pa[k6]][pb[k6]] / s.n - mu[pa[k6]] * mu[pb[k6]]);
+  }
+  *loss = L;
+  if (grad_e) {
+    for (int64_t j = 0; j < n; ++j) {
+      double* ge = grad_e + 3 * j;
+      ge[0] = ge[1] = ge[2] = 0.0;
+      if (!has[(size_t)j]) continue;
+      const Voxel& v = vox[(size_t)j];
+      auto gi = G.find(std::make_tuple(v.v[0], v.v[1], v.v[2]));
+      if (gi == G.end()) continue;
+      const Stat& s = stat_of(v);
+      double d[3];
+      for (int a = 0; a < 3; ++a) d[a] = e_eval[3 * j + a] - corner(v, a) - s.S[a] / s.n;
+      double Gm[3][3] = {{0.0}};
+      for (int k6 = 0; k6 < 6; ++k6) Gm[pa[k6]][pb[k6]] = gi->second[3 + k6];
+      for (int k = 0; k < 3; ++k) {
+        double t = gi->second[k];
+        for (int b = 0; b < 3; ++b) t += (Gm[k][b] + Gm[b][k]) * d[b];
+        ge[k] = t / s.n;
+      }
+    }
+  }
+  return 0;
+}
+
 // For each ray of a frame (band voxels frozen as in oracle_tsdf_frame_eval),
 // the distance of the clamp from the nearest unclamped value among its band
 // voxels: min over the band of | |s_j(v)| - tau | with s_j(v) = (e - centre).u

@@ -15,6 +15,16 @@
 //   dL/de = (sum w) u + (sum w r_perp) / d,  dL/do = -(sum w r_perp) / d,
 //   dL/dz = dL/de . R p~,  p~ = ((u - cx) / fx, (v - cy) / fy, 1),
 //   dL/drho += dL/de + dL/do,  dL/dphi += e x dL/de + o x dL/do.
+//
+// ohm_integrate_posed moves sensor-frame rays to the world by a pose and
+// integrates them; ohm_ndt_backward gives the gradient of
+// L = sum_q gm_q . mean(v_q) + gc_q . packed C(v_q), mean and C the NDT-OM
+// sample statistics (Sec. II-D, III-C) right after that frame, with respect to
+// the frame's sensor-frame endpoints and its pose twist, the voxel of every
+// sample held fixed.  With n, S the voxel's count and sum of sample positions
+// p (relative to its corner) and d = p_j - S / n,
+//   dL/dp_j = (1 / n) [ gm + (G + G^T) d ],  G = upper-triangular(gc),
+// then dL/de_sensor = R^T dL/dp_j and the twist as for the TSDF.
 #include <string>
 
 #include "ohm_kernels.cuh"
@@ -207,6 +217,144 @@ __global__ void __launch_bounds__(kBlock) k_tsdf_backward(DeviceMap m, DepthFram
   }
 }
 
+// A camera-to-world pose [R | t], row major.
+struct Pose34 {
+  double m[12];
+};
+
+// p_k = ((R_k0 x + R_k1 y) + R_k2 z) + t_k in double, one rounding per
+// operation, rounded to float (the depth back-projection's order).
+__device__ __forceinline__ void pose_point(const Pose34& P, const float* in, float* out) {
+  const double x = in[0], y = in[1], z = in[2];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    double a = __dmul_rn(P.m[4 * k], x);
+    a = __dadd_rn(a, __dmul_rn(P.m[4 * k + 1], y));
+    a = __dadd_rn(a, __dmul_rn(P.m[4 * k + 2], z));
+    out[k] = __double2float_rn(__dadd_rn(a, P.m[4 * k + 3]));
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_pose_rays(Pose34 P, CallArgs in, float* origins, float* endpoints,
+                                                      uint8_t* flags) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < in.n; i += (long long)gridDim.x * blockDim.x) {
+    pose_point(P, in.endpoints + 3 * i, endpoints + 3 * i);
+    if (i < in.n_origins) pose_point(P, in.origins + 3 * i, origins + 3 * i);
+    flags[i] = in.flags ? in.flags[i] : 0;
+  }
+}
+
+// Upstream weights of the NDT statistics per voxel: 9 floats (mean x y z,
+// covariance xx xy xz yy yz zz) per voxel of every NDT block.
+__device__ __forceinline__ float* ndt_grad_of(const DeviceMap& m, const float* p) {
+  long long q[3];
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) ok = ok && isfinite(p[k]) && quantise(p[k], m.origin[k], m.scale, &q[k]);
+  ok = ok && in_extent(q, m.frac_bits);
+  if (!ok) return nullptr;
+  const int F = m.frac_bits;
+  const int32_t vx = (int32_t)(q[0] >> F), vy = (int32_t)(q[1] >> F), vz = (int32_t)(q[2] >> F);
+  const int32_t slot = region_slot_of(m, vx, vy, vz);
+  const int32_t ns = slot < 0 ? -1 : m.ndt_slot[slot];
+  if (ns < 0) return nullptr;  // no samples in the region: nothing to differentiate
+  return m.ndt_grad + ((long long)ns * kRegionVoxels + local_morton(vx, vy, vz)) * 9;
+}
+
+__global__ void __launch_bounds__(kBlock) k_ndt_grad_scatter(DeviceMap m, const float* pts, const float* gmean,
+                                                             const float* gcov, long long n, int clear) {
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    float* g = ndt_grad_of(m, pts + 3 * q);
+    if (!g) continue;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      if (clear)
+        g[k] = 0.f;
+      else
+        atomicAdd(g + k, k < 3 ? gmean[3 * q + k] : gcov[6 * q + k - 3]);
+    }
+  }
+}
+
+// Per ray of the frame (world rays in `a`, as integrated): the sample's voxel
+// by the quantisation and truncation of the forward pass, then dL/dp from the
+// voxel's moments and weights.
+__global__ void __launch_bounds__(kBlock) k_ndt_backward(DeviceMap m, CallArgs a, Pose34 P, float* grad_e,
+                                                         double* grad_twist) {
+  __shared__ double red[kBlock / 32][6];
+  const int F = m.frac_bits;
+  const long long U = 1LL << F;
+  const double cell = m.voxel_size / (double)U;
+  double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  const long long n = a.n;
+  const long long nb = ((n + kBlock - 1) / kBlock) * kBlock;  // every thread of a block reaches the reduction
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += (long long)gridDim.x * blockDim.x) {
+    if (i >= n) continue;
+    double gp[3] = {0.0, 0.0, 0.0};
+    float o[3], e[3];
+    uint8_t flag;
+    load_ray(a, i, o, e, &flag);
+    long long qo[3], qe[3];
+    bool ok = (flag & kFlagNoReturn) == 0 && quantise_ray(m, o, e, qo, qe);
+    if (ok) {
+      double d[3];
+      ok = ray_length(qo, qe, d) <= m.rmax_q && in_extent(qo, F) && in_extent(qe, F);
+    }
+    if (ok) {
+      const int32_t v[3] = {(int32_t)(qe[0] >> F), (int32_t)(qe[1] >> F), (int32_t)(qe[2] >> F)};
+      const int32_t slot = region_slot_of(m, v[0], v[1], v[2]);
+      const int32_t ns = slot < 0 ? -1 : m.ndt_slot[slot];
+      if (ns < 0) {
+        atomicOr(m.status, kStatusMissing);
+      } else {
+        const uint32_t mo = local_morton(v[0], v[1], v[2]);
+        const float* g = m.ndt_grad + ((long long)ns * kRegionVoxels + mo) * 9;
+        float w[9];
+        bool any = false;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+          w[k] = g[k];
+          any = any || w[k] != 0.f;
+        }
+        const long long* mom = m.ndt + (long long)ns * 10 * kRegionVoxels + mo;
+        const double cnt = (double)mom[0];
+        if (any && cnt > 0.0) {
+          double dv[3];
+#pragma unroll
+          for (int k = 0; k < 3; ++k)
+            dv[k] = (double)(qe[k] - (long long)v[k] * U) * cell - (double)mom[(long long)(1 + k) * kRegionVoxels] * cell / cnt;
+          // (G + G^T) d with G upper triangular from the packed xx xy xz yy yz zz
+          const double Gs[3][3] = {{2.0 * w[3], w[4], w[5]}, {w[4], 2.0 * w[6], w[7]}, {w[5], w[7], 2.0 * w[8]}};
+#pragma unroll
+          for (int k = 0; k < 3; ++k) gp[k] = ((double)w[k] + Gs[k][0] * dv[0] + Gs[k][1] * dv[1] + Gs[k][2] * dv[2]) / cnt;
+        }
+      }
+    }
+    // sensor frame: dL/de = R^T dL/dp
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      grad_e[3 * i + c] = (float)(P.m[c] * gp[0] + P.m[4 + c] * gp[1] + P.m[8 + c] * gp[2]);
+    const double E[3] = {e[0], e[1], e[2]};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) acc[k] += gp[k];
+    acc[3] += E[1] * gp[2] - E[2] * gp[1];
+    acc[4] += E[2] * gp[0] - E[0] * gp[2];
+    acc[5] += E[0] * gp[1] - E[1] * gp[0];
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const double v = warp_sum(acc[k]);
+    if (lane == 0) red[wid][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    double v = 0.0;
+    for (int i = 0; i < kBlock / 32; ++i) v += red[i][threadIdx.x];
+    atomicAdd(grad_twist + threadIdx.x, v);
+  }
+}
+
 bool frame_from(const float* depth, int32_t width, int32_t height, const double* K, const double* pose, double z_min,
                 double z_max, DepthFrame* f) {
   if (!depth || width < 1 || height < 1 || !K || !pose || !(z_max > z_min)) return false;
@@ -324,6 +472,120 @@ ohm_status ohm_tsdf_backward(ohm_map* map, const float* depth, int32_t width, in
   if (e == cudaSuccess) note_work(map, s);
   if (prev >= 0 && prev != map->device) cudaSetDevice(prev);
   if (e != cudaSuccess) return afail(OHM_ERR_CUDA, std::string("tsdf_backward: ") + cudaGetErrorString(e));
+  return OHM_OK;
+}
+
+static ohm_status posed_args(ohm_map* map, const double* pose, const float* origins, int64_t n_origins,
+                             const float* endpoints, const uint8_t* flags, int64_t n, const char* who,
+                             ohm::Pose34* P) {
+  using namespace ohm;
+  if (!map || !pose) return afail(OHM_ERR_INVALID, std::string(who) + ": NULL map or pose");
+  if (n < 0 || n > map->p.max_rays) return afail(OHM_ERR_INVALID, std::string(who) + ": n outside [0, max_rays]");
+  if (n > 0 && (!origins || !endpoints || (n_origins != 1 && n_origins != n)))
+    return afail(OHM_ERR_INVALID, std::string(who) + ": bad origins / endpoints");
+  if (n > 0 && (!is_device(origins) || !is_device(endpoints) || (flags && !is_device(flags))))
+    return afail(OHM_ERR_INVALID, std::string(who) + ": rays must be device memory");
+  for (int k = 0; k < 12; ++k) {
+    if (!std::isfinite(pose[k])) return afail(OHM_ERR_INVALID, std::string(who) + ": pose not finite");
+    P->m[k] = pose[k];
+  }
+  return OHM_OK;
+}
+
+// Transform into the map's staging buffers; returns the call arguments.
+static cudaError_t stage_posed(ohm_map* map, const ohm::Pose34& P, const float* origins, int64_t n_origins,
+                               const float* endpoints, const uint8_t* flags, int64_t n, cudaStream_t s,
+                               ohm::CallArgs* a) {
+  using namespace ohm;
+  CallArgs in;
+  in.origins = origins;
+  in.endpoints = endpoints;
+  in.flags = flags;
+  in.n = n;
+  in.n_origins = n_origins;
+  const int blocks = (int)((n + kBlock - 1) / kBlock < 4096 ? (n + kBlock - 1) / kBlock : 4096);
+  k_pose_rays<<<blocks > 0 ? blocks : 1, kBlock, 0, s>>>(P, in, map->stage_origins, map->stage_endpoints,
+                                                         map->stage_flags);
+  map->launches += 1;
+  a->origins = map->stage_origins;
+  a->endpoints = map->stage_endpoints;
+  a->flags = map->stage_flags;
+  a->n = n;
+  a->n_origins = n_origins;
+  return cudaGetLastError();
+}
+
+ohm_status ohm_integrate_posed(ohm_map* map, const double* pose, const float* origins, int64_t n_origins,
+                               const float* endpoints, const uint8_t* flags, int64_t n, void* stream) {
+  using namespace ohm;
+  Pose34 P;
+  const ohm_status st = posed_args(map, pose, origins, n_origins, endpoints, flags, n, "integrate_posed", &P);
+  if (st != OHM_OK || n == 0) return st;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != map->device) cudaSetDevice(map->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CallArgs a;
+  cudaError_t e = stage_posed(map, P, origins, n_origins, endpoints, flags, n, s, &a);
+  if (e == cudaSuccess) e = launch_integrate(map, a, s);
+  if (e == cudaSuccess) note_work(map, s);
+  if (prev >= 0 && prev != map->device) cudaSetDevice(prev);
+  if (e != cudaSuccess) return afail(OHM_ERR_CUDA, std::string("integrate_posed: ") + cudaGetErrorString(e));
+  return OHM_OK;
+}
+
+ohm_status ohm_ndt_backward(ohm_map* map, const double* pose, const float* origins, int64_t n_origins,
+                            const float* endpoints, const uint8_t* flags, int64_t n, const float* query_points,
+                            const float* grad_mean, const float* grad_cov, int64_t n_query, float* grad_endpoints,
+                            double* grad_twist, void* stream) {
+  using namespace ohm;
+  Pose34 P;
+  ohm_status st = posed_args(map, pose, origins, n_origins, endpoints, flags, n, "ndt_backward", &P);
+  if (st != OHM_OK) return st;
+  if (!(map->p.layers & OHM_LAYER_NDT)) return afail(OHM_ERR_UNSUPPORTED, "ndt_backward: map has no NDT layer");
+  if (map->p.ndt_clear_below > -INFINITY)
+    return afail(OHM_ERR_UNSUPPORTED, "ndt_backward: sample clearing changes the statistics discontinuously; "
+                                      "the adjoint needs ndt_clear_below = -inf");
+  if (n_query < 0 || (n_query > 0 && (!query_points || !grad_mean || !grad_cov)) || (n > 0 && !grad_endpoints) ||
+      !grad_twist)
+    return afail(OHM_ERR_INVALID, "ndt_backward: NULL buffer");
+  if ((n > 0 && !is_device(grad_endpoints)) || !is_device(grad_twist) ||
+      (n_query > 0 && (!is_device(query_points) || !is_device(grad_mean) || !is_device(grad_cov))))
+    return afail(OHM_ERR_INVALID, "ndt_backward: buffers must be device memory");
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != map->device) cudaSetDevice(map->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSuccess;
+  if (!map->d.ndt_grad) {
+    // upstream weights per NDT voxel, allocated on the first backward call
+    const size_t bytes = sizeof(float) * 9 * (size_t)map->d.max_ndt * kRegionVoxels;
+    e = cudaMalloc(reinterpret_cast<void**>(&map->d.ndt_grad), bytes);
+    if (e == cudaSuccess) e = cudaMemset(map->d.ndt_grad, 0, bytes);
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(grad_twist, 0, 6 * sizeof(double), s);
+  const int qb = (int)(n_query > 0 ? ((n_query + kBlock - 1) / kBlock < 4096 ? (n_query + kBlock - 1) / kBlock : 4096) : 0);
+  if (e == cudaSuccess && qb) {
+    k_ndt_grad_scatter<<<qb, kBlock, 0, s>>>(map->d, query_points, grad_mean, grad_cov, n_query, 0);
+    map->launches += 1;
+  }
+  if (e == cudaSuccess && n > 0) {
+    CallArgs a;
+    e = stage_posed(map, P, origins, n_origins, endpoints, flags, n, s, &a);
+    const int pb = (int)((n + kBlock - 1) / kBlock < 4096 ? (n + kBlock - 1) / kBlock : 4096);
+    if (e == cudaSuccess) {
+      k_ndt_backward<<<pb, kBlock, 0, s>>>(map->d, a, P, grad_endpoints, grad_twist);
+      map->launches += 1;
+    }
+  }
+  if (e == cudaSuccess && qb) {
+    k_ndt_grad_scatter<<<qb, kBlock, 0, s>>>(map->d, query_points, grad_mean, grad_cov, n_query, 1);
+    map->launches += 1;
+  }
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e == cudaSuccess) note_work(map, s);
+  if (prev >= 0 && prev != map->device) cudaSetDevice(prev);
+  if (e != cudaSuccess) return afail(OHM_ERR_CUDA, std::string("ndt_backward: ") + cudaGetErrorString(e));
   return OHM_OK;
 }
 

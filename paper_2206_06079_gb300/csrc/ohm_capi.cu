@@ -76,7 +76,7 @@ void free_map(ohm_map* m) {
   if (!m) return;
   ohm::DeviceMap& d = m->d;
   void* ptrs[] = {d.htab, d.region_count, d.region_coords, d.occ, d.counts, d.decay, d.vmean, d.vmean_acc, d.mean_list, d.ndt_slot, d.ndt_count,
-                  d.ndt, d.tsdf, d.tsdf_cnt, d.tsdf_sum, d.grad, d.status, d.calls, d.rays, d.decay_rays, d.trays, d.segs, d.touched,
+                  d.ndt, d.tsdf, d.tsdf_cnt, d.tsdf_sum, d.grad, d.ndt_grad, d.status, d.calls, d.rays, d.decay_rays, d.trays, d.segs, d.touched,
                   d.stamp, d.born, d.ndt_born, d.free_slots, d.ndt_free, d.free_info, d.restore_keys,
                   m->stage_origins, m->stage_endpoints, m->stage_flags, m->hin_origins[0], m->hin_origins[1],
                   m->hin_endpoints[0], m->hin_endpoints[1], m->hin_flags[0], m->hin_flags[1]};
@@ -222,7 +222,10 @@ ohm_status ohm_map_create(const ohm_map_params* params, ohm_map** out) {
   ohm::DeviceMap& d = m->d;
   const long long R = p.max_regions;
   const long long V = ohm::kRegionVoxels;
-  const long long H = next_pow2(2 * R > 1024 ? 2 * R : 1024);
+  // evicted regions keep their keys: a map that evicts when full may know
+  // many more keys than its pool holds
+  const long long h_min = p.evict_when_full ? (1LL << 18) : 1024;
+  const long long H = next_pow2(2 * R > h_min ? 2 * R : h_min);
   m->hash_capacity = H;
   d.hmask = (uint32_t)(H - 1);
   const int32_t probe_cap = (int32_t)(H < 4096 ? H : 4096);
@@ -410,6 +413,11 @@ ohm_status ohm_integrate_rays(ohm_map* map, const float* origins, int64_t n_orig
       if (e == cudaSuccess) e = ohm::cache_evict(map, resident * 3 / 4, &evicted);
       if (e != cudaSuccess) return cuda_fail(e, "integrate: evict");
       if (evicted == 0) return fail(OHM_ERR_CAPACITY, "integrate: the call alone needs more regions than the pool");
+      // the call may also have reached evicted regions (a capacity failure is
+      // what its status reports): bring those back before repeating it
+      int64_t restored = 0;
+      st = ohm_map_restore_pending(map, &restored, stream);
+      if (st != OHM_OK) return st;
       continue;
     }
     if (st != OHM_ERR_EVICTED) return st;

@@ -148,6 +148,7 @@ struct DeviceMap {
   uint32_t* tsdf_cnt;            // [max_regions][32768] per-call scratch, zero between calls
   long long* tsdf_sum;           // [max_regions][32768] per-call scratch, 2^-32 m units
   float* grad;                   // [max_regions][32768] adjoint weights, allocated by the first backward call
+  float* ndt_grad;               // [max_ndt][32768][9] NDT adjoint weights, allocated by the first NDT backward call
   int32_t* status;
   CallCounters* calls;
   // region cache (Sec. III-A: regions move between device and host memory)

@@ -57,8 +57,16 @@ __global__ void __launch_bounds__(kBlock, OHM_FAST_MIN_BLOCKS) k_walk_fast(Devic
   chain_enter();
   if (latched(m)) return;
   const long long nseg = (long long)m.calls->segments;
+  const long long stride = (long long)gridDim.x * blockDim.x;
   unsigned int ops = 0;
-  OHM_GRID_STRIDE(si, nseg) walk_segment_fast<kOcc, kCounts, kCas>(m, si, ops);
+  long long si = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int2 sg = si < nseg ? m.segs[si] : make_int2(0, 0);
+  for (; si < nseg; si += stride) {
+    // the next segment's table entry is loaded while this one walks
+    const int2 next = si + stride < nseg ? m.segs[si + stride] : make_int2(-1, 0);
+    walk_segment_fast<kOcc, kCounts, kCas>(m, sg, ops, next.x >= 0 ? m.rays + next.x : nullptr);
+    sg = next;
+  }
   // every thread gets here: one atomic per warp for the call's atomic count
   ops = __reduce_add_sync(0xffffffffu, ops);
   if ((threadIdx.x & 31) == 0 && ops) atomicAdd(&m.calls->atomics, (unsigned long long)ops);

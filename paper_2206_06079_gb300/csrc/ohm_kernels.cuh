@@ -183,6 +183,21 @@ static __device__ __noinline__ void logodds_retry(const DeviceMap& m, unsigned i
   atomicOr(m.status, kStatusCasLimit);
 }
 
+// Clamped compare-and-swap miss of one voxel whose word was read as `old`
+// (with NDT sample clearing: clears its samples if the miss crosses the
+// threshold).
+__device__ __forceinline__ void miss_cas(const DeviceMap& m, unsigned int* u, unsigned int old, unsigned int& ops) {
+  const float l0 = logodds_value(__uint_as_float(old), m.l_min);
+  const unsigned int nb = __float_as_uint(fminf(fmaxf(__fadd_rn(l0, m.miss), m.l_min), m.l_max));
+  if (nb == old) return;
+  ++ops;
+  const unsigned int prev = atomicCAS(u, old, nb);
+  if (prev != old)
+    logodds_retry(m, u, prev, m.miss);
+  else
+    after_miss(m, u - reinterpret_cast<unsigned int*>(m.occ), old, nb);
+}
+
 // Launch shapes (measured on GB300, tunnel scans of 131,072 rays):
 //  OHM_WALK_BATCH          voxels in flight per thread in the miss walk
 //  OHM_WALK_MIN_BLOCKS     blocks of 256 threads per SM the walk is compiled for
@@ -247,6 +262,34 @@ __device__ __forceinline__ bool quantise_call_ray(const DeviceMap& m, const Call
     ok = ok && isfinite(e[k]) && quantise(e[k], m.origin[k], m.scale, &qe[k]);
   }
   return ok;
+}
+
+// Segment table entries (ray i, segment j) of the rays of a full warp, in
+// (j, lane) order: the first segments of the warp's 32 rays, then their second
+// segments, and so on.  Neighbouring rays' j-th segments lie close together in
+// space, so the walk's warps (which take consecutive entries) touch compact
+// patches of the map; the stores of each j are coalesced.  Every lane calls
+// this together with its ray's segment count (0 for none).
+__device__ __forceinline__ void write_segments(const DeviceMap& m, long long i, unsigned int nseg) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const unsigned int total = __reduce_add_sync(full, nseg);
+  unsigned long long base = 0;
+  if (lane == 0 && total) base = atomicAdd(&m.calls->segments, (unsigned long long)total);
+  base = __shfl_sync(full, base, 0);
+  if (total == 0) return;
+  if (base + total > (unsigned long long)m.max_segs) {
+    if (lane == 0) atomicOr(m.status, kStatusScratch);
+    return;
+  }
+  const unsigned int rounds = __reduce_max_sync(full, nseg);
+  const unsigned int below = (1u << lane) - 1u;
+  unsigned long long pos = base;
+  for (unsigned int j = 0; j < rounds; ++j) {
+    const unsigned int has = __ballot_sync(full, nseg > j);
+    if (nseg > j) m.segs[pos + __popc(has & below)] = make_int2((int)i, (int)j);
+    pos += __popc(has);
+  }
 }
 
 // Per ray: fixed-point quantisation, max-range truncation, region walk with
@@ -321,14 +364,7 @@ __device__ __forceinline__ void prepare_occ_ray(const DeviceMap& m, const CallAr
     }
     m.rays[i] = r;
   }
-  const unsigned long long base = warp_reserve(&m.calls->segments, nseg);
-  if (nseg > 0) {
-    if (base + nseg > (unsigned long long)m.max_segs) {
-      atomicOr(m.status, kStatusScratch);
-    } else {
-      for (unsigned int j = 0; j < nseg; ++j) m.segs[base + j] = make_int2((int)i, (int)j);
-    }
-  }
+  write_segments(m, i, nseg);
   warp_add(&m.calls->visits, &m.calls->total_visits, nvisit);
 }
 
@@ -461,30 +497,12 @@ __device__ __forceinline__ void walk_segment(const DeviceMap& m, long long si, u
     }
     if (kOcc) {
       unsigned int* base = reinterpret_cast<unsigned int*>(m.occ);
-      unsigned int old[kWalkBatch], prev[kWalkBatch];
+      unsigned int old[kWalkBatch];
 #pragma unroll
       for (int j = 0; j < kWalkBatch; ++j) old[j] = (todo >> j) & 1u ? base[off[j]] : 0u;
 #pragma unroll
-      for (int j = 0; j < kWalkBatch; ++j) {
-        prev[j] = old[j];
-        if (!((todo >> j) & 1u)) continue;
-        const float l0 = logodds_value(__uint_as_float(old[j]), m.l_min);
-        const unsigned int nb = __float_as_uint(fminf(fmaxf(__fadd_rn(l0, miss), m.l_min), m.l_max));
-        if (nb == old[j]) continue;
-        prev[j] = atomicCAS(base + off[j], old[j], nb);
-        ++cas;
-      }
-#pragma unroll
-      for (int j = 0; j < kWalkBatch; ++j) {
-        if (prev[j] != old[j]) {
-          logodds_retry(m, base + off[j], prev[j], miss);
-        } else if ((todo >> j) & 1u) {
-          // this thread's CAS applied the miss (or the voxel was already at the clamp)
-          const float l0 = logodds_value(__uint_as_float(old[j]), m.l_min);
-          const unsigned int nb = __float_as_uint(fminf(fmaxf(__fadd_rn(l0, miss), m.l_min), m.l_max));
-          if (nb != old[j]) after_miss(m, off[j], old[j], nb);
-        }
-      }
+      for (int j = 0; j < kWalkBatch; ++j)
+        if ((todo >> j) & 1u) miss_cas(m, base + off[j], old[j], cas);
     }
   }
 }
@@ -513,18 +531,6 @@ static __device__ __noinline__ int32_t find_region_rare(const DeviceMap& m, long
 #endif
 constexpr int kFastBatch = OHM_FAST_BATCH;
 
-// Clamped compare-and-swap miss of one voxel whose word was read as `old`.
-__device__ __forceinline__ void miss_cas(const DeviceMap& m, unsigned int* u, unsigned int old, unsigned int& ops) {
-  const float l0 = logodds_value(__uint_as_float(old), m.l_min);
-  const unsigned int nb = __float_as_uint(fminf(fmaxf(__fadd_rn(l0, m.miss), m.l_min), m.l_max));
-  if (nb == old) return;
-  ++ops;
-  const unsigned int prev = atomicCAS(u, old, nb);
-  if (prev != old)
-    logodds_retry(m, u, prev, m.miss);
-  else
-    after_miss(m, u - reinterpret_cast<unsigned int*>(m.occ), old, nb);
-}
 
 // Miss phase (Sec. III-C phase one) of one segment with the filtered walk
 // (FWalker): every voxel the ray passes through, except the voxel holding its
@@ -553,9 +559,9 @@ __device__ __forceinline__ void miss_cas(const DeviceMap& m, unsigned int* u, un
 // see the update that crosses its threshold, or a miss increment >= 0) every
 // miss is a clamped compare-and-swap.
 template <bool kOcc, bool kCounts, bool kCas>
-__device__ __forceinline__ void walk_segment_fast(const DeviceMap& m, long long si, unsigned int& ops) {
+__device__ __forceinline__ void walk_segment_fast(const DeviceMap& m, int2 sg, unsigned int& ops,
+                                                  const RayRec* prefetch = nullptr) {
   const int F = m.frac_bits;
-  const int2 sg = m.segs[si];
   const RayRec* rp = m.rays + sg.x;
   FWalker f;
   uint32_t mo, neg;
@@ -577,6 +583,8 @@ __device__ __forceinline__ void walk_segment_fast(const DeviceMap& m, long long 
     keyE = pack_region(s.ve[0] >> kRegionShift, s.ve[1] >> kRegionShift, s.ve[2] >> kRegionShift);
     find_region2(m, pack_region(rcx, rcy, rcz), keyE, &slot, &slotE);
   }
+  // the record of the thread's next segment, into L2 while this one walks
+  if (prefetch) asm volatile("prefetch.global.L2 [%0];" ::"l"(prefetch));
   if (left <= 0) return;
   if (slot < 0 || slotE < 0) {
     atomicOr(m.status, kStatusMissing);
@@ -584,6 +592,7 @@ __device__ __forceinline__ void walk_segment_fast(const DeviceMap& m, long long 
   }
   uint32_t base = (uint32_t)slot << (3 * kRegionShift);
   unsigned int* occ = reinterpret_cast<unsigned int*>(m.occ);
+  const unsigned int miss0 = __float_as_uint(__fadd_rn(0.0f, m.miss));  // an unknown voxel's first miss
   while (left > 0) {
     uint32_t off[kFastBatch];  // voxel offsets (< 2^31: at most 2^16 regions of 2^15 voxels)
     uint32_t valid = 0;
@@ -626,23 +635,35 @@ __device__ __forceinline__ void walk_segment_fast(const DeviceMap& m, long long 
       unsigned int old[kFastBatch];
 #pragma unroll
       for (int j = 0; j < kFastBatch; ++j) old[j] = ((valid >> j) & 1u) ? occ[off[j]] : 0u;
+      if (kCas) {
 #pragma unroll
-      for (int j = 0; j < kFastBatch; ++j) {
-        if (!((valid >> j) & 1u)) continue;
-        if (kCas) {
-          miss_cas(m, occ + off[j], old[j], ops);
-        } else {
+        for (int j = 0; j < kFastBatch; ++j)
+          if ((valid >> j) & 1u) miss_cas(m, occ + off[j], old[j], ops);
+      } else {
+        // adds go out at once; the compare-and-swaps that set unknown voxels
+        // are all issued before any of their results is looked at.  A CAS
+        // that won returns the NaN it replaced; one that lost returns the
+        // (known) value another thread wrote, to which this ray's miss is then
+        // added -- so the word read back replaces the one loaded.
+        uint32_t init = 0;
+#pragma unroll
+        for (int j = 0; j < kFastBatch; ++j) {
+          if (!((valid >> j) & 1u)) continue;
           const float l = __uint_as_float(old[j]);
           if (l > m.l_min) {
             atomicAdd(reinterpret_cast<float*>(occ + off[j]), m.miss);
             ++ops;
           } else if (l != l) {
+            old[j] = atomicCAS(occ + off[j], old[j], miss0);
+            init |= 1u << j;
             ++ops;
-            const unsigned int prev = atomicCAS(occ + off[j], old[j], __float_as_uint(__fadd_rn(0.0f, m.miss)));
-            if (prev != old[j] && __uint_as_float(prev) > m.l_min) {
-              atomicAdd(reinterpret_cast<float*>(occ + off[j]), m.miss);
-              ++ops;
-            }
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < kFastBatch; ++j) {
+          if (((init >> j) & 1u) && __uint_as_float(old[j]) > m.l_min) {
+            atomicAdd(reinterpret_cast<float*>(occ + off[j]), m.miss);
+            ++ops;
           }
         }
       }
@@ -670,18 +691,19 @@ __device__ __forceinline__ void walk_segment_any(const DeviceMap& m, long long s
     return;
   }
   const bool c = walk_needs_cas(m.layers, m.miss, m.ndt_clear);
+  const int2 sg = m.segs[si];
   if (occ && cnt) {
     if (c)
-      walk_segment_fast<true, true, true>(m, si, cas);
+      walk_segment_fast<true, true, true>(m, sg, cas);
     else
-      walk_segment_fast<true, true, false>(m, si, cas);
+      walk_segment_fast<true, true, false>(m, sg, cas);
   } else if (occ) {
     if (c)
-      walk_segment_fast<true, false, true>(m, si, cas);
+      walk_segment_fast<true, false, true>(m, sg, cas);
     else
-      walk_segment_fast<true, false, false>(m, si, cas);
+      walk_segment_fast<true, false, false>(m, sg, cas);
   } else if (cnt) {
-    walk_segment_fast<false, true, false>(m, si, cas);
+    walk_segment_fast<false, true, false>(m, sg, cas);
   }
 }
 

@@ -30,7 +30,7 @@ EXPORTED = ["ohm_map_create", "ohm_map_destroy", "ohm_integrate_rays", "ohm_inte
             "ohm_query_voxels", "ohm_map_region_count", "ohm_map_export", "ohm_map_stats", "ohm_map_profile", "ohm_map_profile_every", "ohm_probe_rate",
             "ohm_map_profile_read", "ohm_last_error", "ohm_count_rays_noalloc", "ohm_batch_create",
             "ohm_batch_destroy", "ohm_batch_tune", "ohm_batch_integrate", "ohm_batch_sync", "ohm_batch_stats",
-            "ohm_integrate_depth", "ohm_tsdf_backward", "ohm_twist_pose", "ohm_map_evict", "ohm_map_restore_pending",
+            "ohm_integrate_depth", "ohm_tsdf_backward", "ohm_twist_pose", "ohm_integrate_posed", "ohm_ndt_backward", "ohm_map_evict", "ohm_map_restore_pending",
             "ohm_map_restore_all", "ohm_map_residency"]
 
 BATCH_MAX_MAPS = 32
@@ -156,6 +156,10 @@ def load_library(path: str = LIB_PATH):
     lib.ohm_tsdf_backward.restype = st
     lib.ohm_tsdf_backward.argtypes = [vp, p, ctypes.c_int32, ctypes.c_int32, dp, dp, ctypes.c_double, ctypes.c_double,
                                       p, p, i64, p, p, vp]
+    lib.ohm_integrate_posed.restype = st
+    lib.ohm_integrate_posed.argtypes = [vp, dp, p, i64, p, p, i64, vp]
+    lib.ohm_ndt_backward.restype = st
+    lib.ohm_ndt_backward.argtypes = [vp, dp, p, i64, p, p, i64, p, p, p, i64, p, p, vp]
     lib.ohm_twist_pose.restype = st
     lib.ohm_twist_pose.argtypes = [dp, dp, dp]
     for name in ("ohm_map_evict",):
@@ -342,6 +346,43 @@ class Map:
                                                 _ptr(q), _ptr(g), int(q.shape[0]), _ptr(gd), _ptr(gt),
                                                 _stream_handle(stream)))
         return gd, gt
+
+    @staticmethod
+    def _pose_arg(pose):
+        P = np.asarray(pose, np.float64).reshape(3, 4)
+        return (ctypes.c_double * 12)(*[float(v) for v in P.reshape(-1)])
+
+    def integrate_posed(self, pose, origins, endpoints, flags=None, stream=None, sync=True):
+        """Integrate sensor-frame rays (CUDA tensors) moved to the world by a
+        3 x 4 camera-to-world pose."""
+        o = _as_points(origins, "origins")
+        e = _as_points(endpoints, "endpoints")
+        f = _as_flags(flags)
+        _keep_for_stream(stream, (origins, o), (endpoints, e), (flags, f))
+        _check(load_library().ohm_integrate_posed(self._h, self._pose_arg(pose), _ptr(o), int(o.shape[0]), _ptr(e),
+                                                  _ptr(f), int(e.shape[0]), _stream_handle(stream)))
+        if sync:
+            self.sync(stream)
+
+    def ndt_backward(self, pose, origins, endpoints, flags, query_points, grad_mean, grad_cov, stream=None):
+        """(dL/d endpoints (n x 3, sensor frame), dL/d twist (6,)) for
+        L = sum_q grad_mean[q] . mean(q) + grad_cov[q] . cov(q) of the NDT
+        statistics right after integrate_posed of the same rays (the voxel of
+        every sample held fixed)."""
+        o = _as_points(origins, "origins")
+        e = _as_points(endpoints, "endpoints")
+        f = _as_flags(flags)
+        q = _as_points(query_points, "query_points")
+        gmean = grad_mean.contiguous().float()
+        gcov = grad_cov.contiguous().float()
+        ge = torch.empty((e.shape[0], 3), dtype=torch.float32, device=e.device)
+        gt = torch.empty(6, dtype=torch.float64, device=e.device)
+        _keep_for_stream(stream, (origins, o), (endpoints, e), (flags, f), (query_points, q), (grad_mean, gmean),
+                         (grad_cov, gcov))
+        _check(load_library().ohm_ndt_backward(self._h, self._pose_arg(pose), _ptr(o), int(o.shape[0]), _ptr(e),
+                                               _ptr(f), int(e.shape[0]), _ptr(q), _ptr(gmean), _ptr(gcov),
+                                               int(q.shape[0]), _ptr(ge), _ptr(gt), _stream_handle(stream)))
+        return ge, gt
 
     def query(self, points, stream=None, ndt=False, tsdf=False, counts=False, path_sum=False, mean=False):
         """Look up world points; returns a dict of CUDA tensors (path_sum:
@@ -606,3 +647,34 @@ class TsdfFrame(torch.autograd.Function):
         depth, q = ctx.saved_tensors
         gd, gt = ctx.gmap.tsdf_backward(depth, ctx.K, ctx.pose, q, grad_out, *ctx.z)
         return gd, gt.to(dtype=ctx.xi_like[0], device=ctx.xi_like[1]), None, None, None, None, None, None
+
+
+class NdtFrame(torch.autograd.Function):
+    """NDT-OM mean (q x 3) and covariance (q x 6, packed xx xy xz yy yz zz)
+    at query points after integrating one ray set given in a sensor frame,
+    differentiable in the sensor-frame endpoints and in a pose twist xi
+    applied on the left of pose0.
+
+    forward(endpoints, xi, gmap, pose0, origins, flags, query_points)
+    integrates the rays seen from exp(xi) pose0 into gmap (a side effect) and
+    returns (mean, cov) of the query voxels (zeros where a voxel holds no
+    sample).  backward gives dL/d endpoints and the tangent-space pose gradient
+    at the evaluated pose (the derivative with respect to xi at xi = 0), with
+    the voxel of every sample held fixed (ohm_ndt_backward)."""
+
+    @staticmethod
+    def forward(ctx, endpoints, xi, gmap, pose0, origins, flags, query_points):
+        pose = twist_pose(xi.detach().cpu().numpy(), pose0)
+        gmap.integrate_posed(pose, origins, endpoints.detach(), flags)
+        r = gmap.query(query_points, ndt=True)["ndt"]
+        ctx.gmap, ctx.pose = gmap, pose
+        ctx.xi_like = (xi.dtype, xi.device)
+        ctx.save_for_backward(endpoints.detach(), origins, flags if flags is not None else torch.empty(0),
+                              query_points)
+        return r[:, 1:4].contiguous(), r[:, 4:10].contiguous()
+
+    @staticmethod
+    def backward(ctx, grad_mean, grad_cov):
+        e, o, f, q = ctx.saved_tensors
+        ge, gt = ctx.gmap.ndt_backward(ctx.pose, o, e, f if f.numel() else None, q, grad_mean, grad_cov)
+        return ge, gt.to(dtype=ctx.xi_like[0], device=ctx.xi_like[1]), None, None, None, None, None

@@ -150,3 +150,30 @@ def assert_maps_identical(a: ohm.Map, b: ohm.Map):
     assert ea.keys() == eb.keys()
     for k in ea:
         assert torch.equal(ea[k], eb[k]), "layer %s differs" % k
+
+
+def compare_resident_with_oracle(gm: ohm.Map, om: oracle.OracleMap):
+    """For a map whose pool evicted regions to host memory: every region live
+    on the device (a pool slot with an observed voxel; released slots read as
+    unobserved) equals the oracle's region of the same key, occupancy bit for
+    bit and NDT moments exactly.  Returns the number of regions compared."""
+    n = gm.region_count()
+    L = gm.params["layers"]
+    ndt = bool(L & ohm.LAYER_NDT)
+    ex = gm.export(occupancy=True, ndt=ndt, count=n)
+    keys = ex["keys"].cpu().numpy().astype(np.int64)
+    occ = ex["occupancy"].cpu().numpy()
+    live = np.flatnonzero(~np.isnan(occ).all(1))
+    ref = om.export(occupancy=True, counts=False, ndt=ndt, tsdf=False, path=False, mean=False)
+    index = {tuple(k): i for i, k in enumerate(ref["keys"].tolist())}
+    for s in live:
+        j = index.get(tuple(keys[s].tolist()))
+        assert j is not None, "a live region is unknown to the oracle"
+        o = ref["occupancy"][j]
+        known = ~np.isnan(o)
+        assert np.array_equal(~np.isnan(occ[s]), known), "known voxel sets differ"
+        assert np.array_equal(occ[s][known].view(np.uint32), o[known].view(np.uint32)), "occupancy differs"
+        if ndt:
+            g = ex["ndt"][s].cpu().numpy()
+            assert np.array_equal(g, ref["ndt"][j]), "NDT moments differ"
+    return len(live)

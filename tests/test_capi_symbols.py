@@ -79,6 +79,7 @@ def test_create_rejects_bad_parameters_before_touching_a_device():
         (dict(layers=W.OCC | W.MEAN, max_rays=(1 << 22) + 1), "mean layer"),
         (dict(max_range=1e5), "2^30"),
         (dict(l_min=1.0, l_max=0.0), "l_min"),
+        (dict(miss=-1e-35), "2^-100"),
         (dict(ndt_clear_below=float("nan")), "NaN"),
         (dict(layers=W.NDT, max_ndt_regions=0), "max_ndt_regions"),
     ]

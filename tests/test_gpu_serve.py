@@ -9,7 +9,7 @@ import torch
 import oracle
 from paper_2206_06079_gb300 import ohm, serve, synth, workloads as W
 
-from .parity import assert_maps_identical, compare_dense, compare_ndt
+from .parity import assert_maps_identical, compare_dense, compare_ndt, compare_resident_with_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -21,9 +21,11 @@ def _built():
     assert torch.cuda.is_available()
 
 
-def _params():
-    return W.tunnel_params(layers=W.OCC | W.NDT, voxel_size=0.1, max_range=30.0, max_rays=131072,
-                           max_regions=8192, max_ndt_regions=4096)
+def _params(**kw):
+    p = dict(layers=W.OCC | W.NDT, voxel_size=0.1, max_range=30.0, max_rays=131072, max_regions=8192,
+             max_ndt_regions=4096)
+    p.update(kw)
+    return W.tunnel_params(**p)
 
 
 def _requests(n_robots, duration, seed=0):
@@ -41,15 +43,19 @@ def _requests(n_robots, duration, seed=0):
 
 @pytest.mark.parametrize("budget", [None, 150])
 def test_served_maps_equal_maps_integrated_alone(budget):
+    """budget: regions each served map keeps resident; above it the loop
+    moves least recently used regions to host memory, and later scans that
+    reach them fault, restore them and repeat."""
     n = 3
     reqs = _requests(n, 1.0)
     torch.cuda.synchronize()
     served = [ohm.Map(**_params()) for _ in range(n)]
-    loop = serve.ServeLoop(served, budget_regions=budget)
+    loop = serve.ServeLoop(served, budget_regions=budget, budget_every=2)
     stats = loop.run(list(reqs), realtime=False)
     assert len(stats.latencies_ms) == len(reqs)
+    assert stats.rays == sum(r.n for r in reqs)
     if budget is not None:
-        assert stats.evicted_regions > 0
+        assert stats.evicted_regions > 0 and stats.faults > 0
     alone = [ohm.Map(**_params()) for _ in range(n)]
     for r in sorted(reqs, key=lambda r: (r.map_index, r.arrival)):
         alone[r.map_index].integrate(*r.rays)
@@ -64,6 +70,26 @@ def test_served_maps_equal_maps_integrated_alone(budget):
         om.integrate(*(t.cpu().numpy() for t in r.rays))
     compare_dense(served[rb], om, counts=False)
     compare_ndt(served[rb], om)
+
+
+def test_small_pools_evict_and_repeat_scans():
+    """Pools smaller than a robot's map (the HBM cap): scans that find no free
+    region fail without changing anything, the loop evicts least recently used
+    regions and repeats them, in order; every region left on the device equals
+    the oracle's."""
+    # one lidar scan here touches at most ~560 regions and a robot's map grows
+    # past 600 within about 1.5 s: pools of 600 must evict
+    n = 2
+    reqs = _requests(n, 2.5, seed=2)
+    torch.cuda.synchronize()
+    served = [ohm.Map(**_params(max_regions=600, max_ndt_regions=600, evict_when_full=1)) for _ in range(n)]
+    stats = serve.ServeLoop(served).run(list(reqs), realtime=False)
+    assert len(stats.latencies_ms) == len(reqs)
+    assert stats.capacity_faults > 0 and stats.evicted_regions > 0
+    om = oracle.OracleMap(**W.oracle_params(_params()))
+    for r in sorted((r for r in reqs if r.map_index == 0), key=lambda r: r.arrival):
+        om.integrate(*(t.cpu().numpy() for t in r.rays))
+    assert compare_resident_with_oracle(served[0], om) > 50
 
 
 def test_realtime_loop_reports_latency():
