@@ -30,7 +30,7 @@ UNIT = "rays/s"
 WORKLOAD = ("tunnel lidar trajectory: 128x1024 = 131072 rays/scan, 100-scan sinusoidal tunnel (r = 3 m, 200 m), "
             "10% missing returns to 50 m, occupancy + NDT-OM, 0.1 m voxels, 32^3 regions")
 SCANS = 100
-WALK_PROFILE = os.path.join(ROOT, "profiles", "walk_miss_tunnel_traffic.json")
+WALK_PROFILE = os.path.join(ROOT, "profiles", "walk_fast_tunnel_traffic.json")
 
 
 def _dist():
@@ -370,8 +370,12 @@ def run_ours(args):
     if ws == 1 and not args.no_extras:
         extras["room"] = room_leg(dev)
         extras["tsdf"] = tsdf_leg(dev, frames=16, warmup=3)
+        extras["ndt_adjoint"] = ndt_adjoint_leg(dev)
         extras["multimap"] = multimap_leg(dev, steps=20, warmup=3)
-        extras["served"] = served_leg(dev, duration=8.0, pool_regions=1000)
+        extras["served"] = served_leg(dev, duration=8.0, pool_regions=1150)
+        # offered load far above what one GPU serves: rays/s over the wall
+        # time until the backlog is drained is the sustained maximum
+        extras["served_saturation"] = served_leg(dev, duration=3.0, rate_scale=24.0, pool_regions=1600)
 
     if rank == 0:
         clocks = ClockSampler.summarise(rows)
@@ -509,6 +513,52 @@ def tsdf_leg(dev, frames=16, warmup=3, n_query=20000):
             "frames": frames, "warmup": warmup, "adjoint_query_voxels": n_query}
 
 
+def ndt_adjoint_leg(dev, scans=8, warmup=3, n_query=20000):
+    """NDT-OM adjoint on tunnel scans: each scan is given in the sensor frame
+    and integrated by ohm_integrate_posed, then ohm_ndt_backward gives the
+    gradient of a loss on the mean and covariance of n_query voxels with
+    respect to every endpoint and the pose twist.  Device ms per scan for the
+    forward call and for forward + backward."""
+    import numpy as np
+    import torch
+    from paper_2206_06079_gb300 import ohm, workloads as W
+    rng = np.random.default_rng(9)
+    frames = []
+    for i in range(warmup + scans):
+        s = W.tunnel_rays(i, device=dev)
+        pose = np.concatenate([np.eye(3), rng.uniform(-0.2, 0.2, size=(3, 1))], 1)
+        t = torch.from_numpy(pose[:, 3]).to(dev)
+        frames.append((pose, (s.origins.double() - t).float(), (s.endpoints.double() - t).float(), s.flags))
+    q = torch.from_numpy(rng.uniform([0, -6, -3], [20, 6, 3], size=(n_query, 3)).astype(np.float32)).to(dev)
+    gmean = torch.from_numpy(rng.normal(size=(n_query, 3)).astype(np.float32)).to(dev)
+    gcov = torch.from_numpy(rng.normal(size=(n_query, 6)).astype(np.float32)).to(dev)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    out = {}
+    for with_backward in (False, True):
+        gm = ohm.Map(**W.tunnel_params(device=dev.index))
+        for pose, o, e, f in frames[:warmup]:
+            gm.integrate_posed(pose, o, e, f, sync=False)
+            if with_backward:
+                gm.ndt_backward(pose, o, e, f, q, gmean, gcov)
+        gm.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for pose, o, e, f in frames[warmup:]:
+            gm.integrate_posed(pose, o, e, f, sync=False)
+            if with_backward:
+                gm.ndt_backward(pose, o, e, f, q, gmean, gcov)
+        e1.record(stream)
+        gm.sync()
+        out["forward_backward_ms_per_scan" if with_backward else "forward_ms_per_scan"] = e0.elapsed_time(e1) / scans
+        gm.close()
+    out["backward_ms_per_scan"] = out["forward_backward_ms_per_scan"] - out["forward_ms_per_scan"]
+    out.update({"workload": "tunnel scans (131072 rays) in the sensor frame with a pose, occupancy + NDT-OM; "
+                            "gradient of mean/covariance losses on %d query voxels" % n_query,
+                "scans": scans, "warmup": warmup})
+    return out
+
+
 MULTIMAP_KINDS = ("lidar16x1800", "lidar64x1024", "lidar128x2048", "depth424x240")
 
 
@@ -623,9 +673,9 @@ def served_leg(dev, duration=8.0, budget_frac=1.0, n_robots=8, realtime=True, ra
     per_region = 4 * 32768 + 8 * 10 * 32768          # occupancy + an NDT block
     # each map's region pool is its share of the cap: a scan that needs more
     # fails, the loop evicts least recently used regions and repeats it (one
-    # 128 x 1024 lidar scan here touches up to about 850 regions)
+    # 128 x 1024 lidar scan here touches up to about 1100 regions)
     if pool_regions is None:
-        pool_regions = max(1000, int(60e9 * budget_frac / n_robots / per_region))
+        pool_regions = max(1150, int(60e9 * budget_frac / n_robots / per_region))
     cap = pool_regions * per_region * n_robots
     params = W.tunnel_params(layers=W.OCC | W.NDT, max_range=30.0, max_rays=131072, max_regions=pool_regions,
                              max_ndt_regions=pool_regions, evict_when_full=1, device=dev.index)
@@ -664,7 +714,8 @@ def served_leg(dev, duration=8.0, budget_frac=1.0, n_robots=8, realtime=True, ra
             "rays_per_s": stats["rays_per_s"], "offered_rays_per_s": offered, "latency_ms": stats["latency_ms"],
             "requests": stats["requests"], "steps": stats["steps"], "duration_s": duration,
             "evicted_regions": stats["evicted_regions"], "restored_regions": stats["restored_regions"],
-            "faults": stats["faults"], "capacity_faults": stats["capacity_faults"], "resident_regions_end": resident,
+            "faults": stats["faults"], "capacity_faults": stats["capacity_faults"], "wall_s": stats["wall_s"],
+            "saturated": offered > 1.02 * stats["rays_per_s"], "resident_regions_end": resident,
             "host_regions_end": host, "hbm_cap_gb": cap / 1e9, "pool_regions_per_map": pool_regions,
             "pipeline_depth": loop.depth}
 

@@ -524,7 +524,7 @@ static __device__ __noinline__ int exact_pick_rec(const RayRec* rp, int F, int32
 static __device__ __noinline__ int32_t find_region_rare(const DeviceMap& m, long long key) { return find_region(m, key); }
 
 #ifndef OHM_FAST_BATCH
-#define OHM_FAST_BATCH 8
+#define OHM_FAST_BATCH 4
 #endif
 #ifndef OHM_FAST_MIN_BLOCKS
 #define OHM_FAST_MIN_BLOCKS 4
@@ -593,12 +593,14 @@ __device__ __forceinline__ void walk_segment_fast(const DeviceMap& m, int2 sg, u
   uint32_t base = (uint32_t)slot << (3 * kRegionShift);
   unsigned int* occ = reinterpret_cast<unsigned int*>(m.occ);
   const unsigned int miss0 = __float_as_uint(__fadd_rn(0.0f, m.miss));  // an unknown voxel's first miss
-  while (left > 0) {
-    uint32_t off[kFastBatch];  // voxel offsets (< 2^31: at most 2^16 regions of 2^15 voxels)
+  // Software pipeline over batches of kFastBatch voxels: the next batch is
+  // walked and its loads issued while the previous batch's loads are in
+  // flight, then the previous batch's updates go out.
+  auto fill = [&](uint32_t (&off)[kFastBatch]) -> uint32_t {
     uint32_t valid = 0;
 #pragma unroll
     for (int j = 0; j < kFastBatch; ++j) {
-      off[j] = base | (mo ^ neg);
+      off[j] = base | (mo ^ neg);  // voxel offset (< 2^31: at most 2^16 regions of 2^15 voxels)
       if (left > 0) {
         valid |= 1u << j;
         --left;
@@ -626,48 +628,66 @@ __device__ __forceinline__ void walk_segment_fast(const DeviceMap& m, int2 sg, u
         }
       }
     }
+    return valid;
+  };
+  auto issue = [&](const uint32_t (&off)[kFastBatch], uint32_t valid, unsigned int (&old)[kFastBatch]) {
     if (kCounts) {
 #pragma unroll
       for (int j = 0; j < kFastBatch; ++j)
         if ((valid >> j) & 1u) atomicAdd(m.counts + off[j], 1ULL);
     }
     if (kOcc) {
-      unsigned int old[kFastBatch];
 #pragma unroll
       for (int j = 0; j < kFastBatch; ++j) old[j] = ((valid >> j) & 1u) ? occ[off[j]] : 0u;
-      if (kCas) {
+    }
+  };
+  auto apply = [&](const uint32_t (&off)[kFastBatch], uint32_t valid, unsigned int (&old)[kFastBatch]) {
+    if (!kOcc) return;
+    if (kCas) {
 #pragma unroll
-        for (int j = 0; j < kFastBatch; ++j)
-          if ((valid >> j) & 1u) miss_cas(m, occ + off[j], old[j], ops);
-      } else {
-        // adds go out at once; the compare-and-swaps that set unknown voxels
-        // are all issued before any of their results is looked at.  A CAS
-        // that won returns the NaN it replaced; one that lost returns the
-        // (known) value another thread wrote, to which this ray's miss is then
-        // added -- so the word read back replaces the one loaded.
-        uint32_t init = 0;
+      for (int j = 0; j < kFastBatch; ++j)
+        if ((valid >> j) & 1u) miss_cas(m, occ + off[j], old[j], ops);
+      return;
+    }
+    // adds go out at once; the compare-and-swaps that set unknown voxels
+    // are all issued before any of their results is looked at.  A CAS
+    // that won returns the NaN it replaced; one that lost returns the
+    // (known) value another thread wrote, to which this ray's miss is then
+    // added -- so the word read back replaces the one loaded.
+    uint32_t init = 0;
 #pragma unroll
-        for (int j = 0; j < kFastBatch; ++j) {
-          if (!((valid >> j) & 1u)) continue;
-          const float l = __uint_as_float(old[j]);
-          if (l > m.l_min) {
-            atomicAdd(reinterpret_cast<float*>(occ + off[j]), m.miss);
-            ++ops;
-          } else if (l != l) {
-            old[j] = atomicCAS(occ + off[j], old[j], miss0);
-            init |= 1u << j;
-            ++ops;
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < kFastBatch; ++j) {
-          if (((init >> j) & 1u) && __uint_as_float(old[j]) > m.l_min) {
-            atomicAdd(reinterpret_cast<float*>(occ + off[j]), m.miss);
-            ++ops;
-          }
-        }
+    for (int j = 0; j < kFastBatch; ++j) {
+      if (!((valid >> j) & 1u)) continue;
+      const float l = __uint_as_float(old[j]);
+      if (l > m.l_min) {
+        atomicAdd(reinterpret_cast<float*>(occ + off[j]), m.miss);
+        ++ops;
+      } else if (l != l) {
+        old[j] = atomicCAS(occ + off[j], old[j], miss0);
+        init |= 1u << j;
+        ++ops;
       }
     }
+#pragma unroll
+    for (int j = 0; j < kFastBatch; ++j) {
+      if (((init >> j) & 1u) && __uint_as_float(old[j]) > m.l_min) {
+        atomicAdd(reinterpret_cast<float*>(occ + off[j]), m.miss);
+        ++ops;
+      }
+    }
+  };
+  uint32_t offA[kFastBatch], offB[kFastBatch];
+  unsigned int oldA[kFastBatch], oldB[kFastBatch];
+  uint32_t vA = fill(offA), vB;
+  issue(offA, vA, oldA);
+  while (vA) {
+    vB = fill(offB);
+    issue(offB, vB, oldB);
+    apply(offA, vA, oldA);
+    if (!vB) break;
+    vA = fill(offA);
+    issue(offA, vA, oldA);
+    apply(offB, vB, oldB);
   }
 }
 

@@ -119,11 +119,13 @@ class ServeLoop:
         no-ops.  Free or restore regions and integrate all of them again, in
         order; returns the requests integrated."""
         m = self.maps[i]
+        msg = ""
         todo = [h[i] for _, h in self._inflight if h[i] is not None]
         for r in todo:
             # a repeat either restores what it reached or frees room; a later
             # no-op step of the map cleared the failed call's restore list, so
             # it may take a repeat to ask for those regions again
+            n_capacity, emptied = 0, False
             for _ in range(16):
                 if err == ohm.ERR_EVICTED:
                     self.stats.faults += 1
@@ -131,13 +133,24 @@ class ServeLoop:
                 elif err == ohm.ERR_CAPACITY:
                     # make room, then bring back what the failed call asked for:
                     # a call can run out of slots and reach evicted regions at
-                    # once (the status reports the capacity failure)
+                    # once (the status reports the capacity failure).  Evict
+                    # the least recently used quarter; after three such
+                    # faults move every region out, so that the repeats bring
+                    # back only what this scan touches.  A capacity fault on
+                    # a pool holding nothing else means the scan alone does
+                    # not fit.
                     self.stats.capacity_faults += 1
+                    n_capacity += 1
+                    if emptied:
+                        raise ohm.OhmError(err, "served scan alone needs more regions than map %d's pool (%s)"
+                                           % (i, msg))
                     resident, _ = m.residency(self.stream)
-                    self.stats.evicted_regions += m.evict(resident * 3 // 4, self.stream)
+                    keep = resident * 3 // 4 if n_capacity < 3 else 0
+                    emptied = keep == 0
+                    self.stats.evicted_regions += m.evict(keep, self.stream)
                     self.stats.restored_regions += m.restore_pending(self.stream)
                 elif err is not None:
-                    raise ohm.OhmError(err, "served scan failed")
+                    raise ohm.OhmError(err, "served scan failed (%s)" % msg)
                 try:
                     with torch.cuda.stream(self.stream):
                         m.integrate(*r.rays, stream=self.stream, sync=False)
@@ -145,9 +158,9 @@ class ServeLoop:
                     err = None
                     break
                 except ohm.OhmError as e:
-                    err = e.code
+                    err, msg = e.code, str(e)
             else:
-                raise ohm.OhmError(err, "served scan could not be integrated")
+                raise ohm.OhmError(err, "served scan could not be integrated (%s)" % msg)
         return todo
 
     def _complete(self, r, now):

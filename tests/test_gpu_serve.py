@@ -77,19 +77,20 @@ def test_small_pools_evict_and_repeat_scans():
     region fail without changing anything, the loop evicts least recently used
     regions and repeats them, in order; every region left on the device equals
     the oracle's."""
-    # one lidar scan here touches at most ~560 regions and a robot's map grows
-    # past 600 within about 1.5 s: pools of 600 must evict
+    # over these 3.5 s one lidar scan of robot 1 touches at most 669 regions
+    # and its map grows to 742 (robot 0: 628 and 685, counted with the
+    # oracle): pools of 700 hold every scan but make robot 1 evict
     n = 2
-    reqs = _requests(n, 2.5, seed=2)
+    reqs = _requests(n, 3.5, seed=2)
     torch.cuda.synchronize()
-    served = [ohm.Map(**_params(max_regions=600, max_ndt_regions=600, evict_when_full=1)) for _ in range(n)]
+    served = [ohm.Map(**_params(max_regions=700, max_ndt_regions=700, evict_when_full=1)) for _ in range(n)]
     stats = serve.ServeLoop(served).run(list(reqs), realtime=False)
     assert len(stats.latencies_ms) == len(reqs)
     assert stats.capacity_faults > 0 and stats.evicted_regions > 0
     om = oracle.OracleMap(**W.oracle_params(_params()))
-    for r in sorted((r for r in reqs if r.map_index == 0), key=lambda r: r.arrival):
+    for r in sorted((r for r in reqs if r.map_index == 1), key=lambda r: r.arrival):
         om.integrate(*(t.cpu().numpy() for t in r.rays))
-    assert compare_resident_with_oracle(served[0], om) > 50
+    assert compare_resident_with_oracle(served[1], om) > 300
 
 
 def test_realtime_loop_reports_latency():
