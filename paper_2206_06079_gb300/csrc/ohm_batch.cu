@@ -48,8 +48,11 @@ struct BatchShared {
 
 enum PrefixKind { kRaysPadded, kRays, kSegments, kTouched, kMeanTouched };
 
-// Load the descriptors and build the prefix table of the requested kind.
-__device__ void batch_stage(BatchShared& sh, const BatchDesc* desc, const BatchStep* step, PrefixKind kind) {
+// Load the descriptors and build the prefix table of the requested kind
+// (segments: of the maps whose walk is `variant` only, unless it is kAnyWalk).
+constexpr int kAnyWalk = -2;
+__device__ void batch_stage(BatchShared& sh, const BatchDesc* desc, const BatchStep* step, PrefixKind kind,
+                            int variant = kAnyWalk) {
   const int nm = desc->n_maps;
   const int words = (int)(sizeof(DeviceMap) / sizeof(int)) * nm;
   const int* src = reinterpret_cast<const int*>(desc->maps);
@@ -68,7 +71,9 @@ __device__ void batch_stage(BatchShared& sh, const BatchDesc* desc, const BatchS
       else if (kind == kRays)
         c = live ? step->n[i] : 0;
       else if (kind == kSegments)
-        c = live ? (long long)m.calls->segments : 0;
+        c = live && (variant == kAnyWalk || walk_variant(m.layers, m.miss, m.ndt_clear) == variant)
+                ? (long long)m.calls->segments
+                : 0;
       else if (kind == kMeanTouched)
         c = (m.layers & kLayerMean) ? mean_touched_count(m) : 0;  // failed maps too: their sums are cleared
       else
@@ -135,17 +140,47 @@ __global__ void __launch_bounds__(kBlock) k_batch_ndt_alloc(const BatchDesc* des
   }
 }
 
+// Miss walk of the maps with the decay layer (walk_segment).
 __global__ void __launch_bounds__(kBlock, OHM_WALK_MIN_BLOCKS) k_batch_walk(const BatchDesc* desc, const BatchStep* step) {
   chain_enter();
   __shared__ BatchShared sh;
-  batch_stage(sh, desc, step, kSegments);
+  batch_stage(sh, desc, step, kSegments, kWalkDecay);
   const long long total = sh.pref[sh.n_maps];
   OHM_BATCH_STRIDE(g, total) {
     const int mi = batch_find(sh, g);
     const DeviceMap& m = sh.maps[mi];
     const long long si = g - sh.pref[mi];
     unsigned int cas = 0;  // not attributed per map in a batched step
-    walk_segment_any(m, si, cas);
+    const bool occ = (m.layers & kLayerOcc) != 0, cnt = (m.layers & kLayerCounts) != 0;
+    if (occ && cnt)
+      walk_segment<true, true, true>(m, si, cas);
+    else if (occ)
+      walk_segment<true, false, true>(m, si, cas);
+    else if (cnt)
+      walk_segment<false, true, true>(m, si, cas);
+    else
+      walk_segment<false, false, true>(m, si, cas);
+  }
+}
+
+// Filtered miss walk of the maps whose walk is kVariant (walk_variant): one
+// launch per variant present in the batch, so that each kernel holds only its
+// own update code (one kernel for every variant spills heavily).
+#ifndef OHM_BATCH_PIPE
+#define OHM_BATCH_PIPE false
+#endif
+template <int kVariant>
+__global__ void __launch_bounds__(kBlock, OHM_FAST_MIN_BLOCKS) k_batch_walk_fast(const BatchDesc* desc, const BatchStep* step) {
+  chain_enter();
+  __shared__ BatchShared sh;
+  batch_stage(sh, desc, step, kSegments, kVariant);
+  const long long total = sh.pref[sh.n_maps];
+  OHM_BATCH_STRIDE(g, total) {
+    const int mi = batch_find(sh, g);
+    const DeviceMap& m = sh.maps[mi];
+    unsigned int ops = 0;  // not attributed per map in a batched step
+    walk_segment_fast<(kVariant & 4) != 0, (kVariant & 2) != 0, (kVariant & 1) != 0, OHM_BATCH_PIPE>(
+        m, m.segs[g - sh.pref[mi]], ops);
   }
 }
 
@@ -238,6 +273,7 @@ struct ohm_batch {
   cudaGraphExec_t exec;
   bool have_exec;
   bool any_ndt, any_tsdf, any_occ, any_mean;
+  uint32_t walk_variants;      // bit v: some map's walk is variant v (walk_variant)
   long long launches;
   long long graph_launches;
   int graph_kernels;           // kernel nodes in the captured step
@@ -286,10 +322,16 @@ cudaError_t enqueue_step(ohm_batch* b, cudaStream_t s, int* count) {
     launch_chained(k_batch_prepare, ray_grid, s, b->d_desc, b->d_step, 1);
     ++n;
   }
-  if (b->any_occ) {
-    launch_chained(k_batch_walk, grid * OHM_WALK_OVERSUBSCRIBE, s, b->d_desc, b->d_step);  // oversubscribed like k_walk_miss
-    ++n;
-  }
+  // oversubscribed grid-stride launches, like the single-map walk
+  const int wgrid = grid * OHM_WALK_OVERSUBSCRIBE;
+  const uint32_t wv = b->walk_variants;
+  if (wv & (1u << kWalkDecay)) launch_chained(k_batch_walk, wgrid, s, b->d_desc, b->d_step);
+  if (wv & (1u << 7)) launch_chained(k_batch_walk_fast<7>, wgrid, s, b->d_desc, b->d_step);
+  if (wv & (1u << 6)) launch_chained(k_batch_walk_fast<6>, wgrid, s, b->d_desc, b->d_step);
+  if (wv & (1u << 5)) launch_chained(k_batch_walk_fast<5>, wgrid, s, b->d_desc, b->d_step);
+  if (wv & (1u << 4)) launch_chained(k_batch_walk_fast<4>, wgrid, s, b->d_desc, b->d_step);
+  if (wv & (1u << 2)) launch_chained(k_batch_walk_fast<2>, wgrid, s, b->d_desc, b->d_step);
+  n += __builtin_popcount(wv);
   if (b->any_occ || b->any_ndt || b->any_mean) {
     launch_chained(k_batch_hits, ray_grid, s, b->d_desc, b->d_step);
     ++n;
@@ -347,6 +389,8 @@ ohm_status ohm_batch_create(ohm_map* const* maps, int32_t n_maps, ohm_batch** ou
     b->any_ndt = b->any_ndt || (L & OHM_LAYER_NDT);
     b->any_tsdf = b->any_tsdf || (L & OHM_LAYER_TSDF);
     b->any_mean = b->any_mean || (L & OHM_LAYER_MEAN);
+    const int v = ohm::walk_variant(maps[i]->d.layers, maps[i]->d.miss, maps[i]->d.ndt_clear);
+    if (v != ohm::kWalkNone) b->walk_variants |= 1u << v;
   }
   b->walk_blocks_per_sm = ohm::walk_blocks_per_sm();
   cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);

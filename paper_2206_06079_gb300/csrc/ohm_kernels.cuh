@@ -11,6 +11,11 @@
 namespace ohm {
 
 constexpr int kBlock = 256;
+// regions whose first hash probes one thread of the prepare walk loads together
+#ifndef OHM_REGION_BATCH
+#define OHM_REGION_BATCH 4
+#endif
+constexpr int kRegionBatch = OHM_REGION_BATCH;
 
 __device__ __forceinline__ bool latched(const DeviceMap& m) { return *(volatile int32_t*)m.status != 0; }
 
@@ -130,14 +135,60 @@ __device__ __forceinline__ void load_ray(const CallArgs& a, long long i, float o
 // into the hash table.  The same exact walk at region resolution visits
 // exactly the regions of the voxels the voxel walk visits: region boundaries
 // are voxel boundaries, crossed at the same t in the same tie order.
+//
+// The lookups of successive regions do not depend on one another, and a
+// 131,072-ray scan runs as one wave, so the kernel lasts as long as its
+// longest chain of dependent loads (a ray to the range limit crosses dozens
+// of regions).  So the walk goes kRegionBatch regions ahead and loads their
+// first probe entries together.  A first entry holding the key with a slot
+// is the common case (the region exists): it is stamped as insert_region
+// would.  Every other case goes through insert_region.  A ray visits a
+// region once, so a batch holds distinct keys.
 __device__ __forceinline__ void insert_ray_regions(const DeviceMap& m, const long long a[3], const long long b[3]) {
   Walker w;
   walker_init(w, a, b, m.frac_bits + kRegionShift, 0, 0);
-  insert_region(m, w.vx, w.vy, w.vz);
-  while (w.total > 0) {
-    int32_t c, s;
-    walker_step(w, walker_choose(w), &c, &s);
-    insert_region(m, w.vx, w.vy, w.vz);
+  const int32_t seq = m.calls->seq;
+  bool more = true;
+  while (more) {
+    long long key[kRegionBatch];
+    uint32_t h[kRegionBatch];
+    unsigned n = 0;
+#pragma unroll
+    for (int j = 0; j < kRegionBatch; ++j) {
+      key[j] = kEmptyKey;
+      h[j] = 0;
+      if (more) {
+        key[j] = pack_region(w.vx, w.vy, w.vz);
+        h[j] = hash_key(key[j]) & m.hmask;
+        n = j + 1;
+        if (w.total > 0) {
+          int32_t c, s;
+          walker_step(w, walker_choose(w), &c, &s);
+        } else {
+          more = false;
+        }
+      }
+    }
+    longlong2 e[kRegionBatch];
+#pragma unroll
+    for (int j = 0; j < kRegionBatch; ++j)
+      if (j < (int)n) e[j] = m.htab[h[j]];
+#pragma unroll
+    for (int j = 0; j < kRegionBatch; ++j) {
+      if (j < (int)n) {
+        if (e[j].x == key[j] && e[j].y >= 0) {
+          m.stamp[e[j].y] = seq;
+        } else {
+          const unsigned long long k = (unsigned long long)key[j];
+          const int32_t mask = (1 << 21) - 1;
+          // sign-extend the 21-bit fields of the packed key
+          const int rx = (int32_t)((uint32_t)((k >> 42) & mask) << 11) >> 11;
+          const int ry = (int32_t)((uint32_t)((k >> 21) & mask) << 11) >> 11;
+          const int rz = (int32_t)((uint32_t)(k & mask) << 11) >> 11;
+          insert_region(m, rx, ry, rz);
+        }
+      }
+    }
   }
 }
 
@@ -523,13 +574,23 @@ static __device__ __noinline__ int exact_pick_rec(const RayRec* rp, int F, int32
 }
 static __device__ __noinline__ int32_t find_region_rare(const DeviceMap& m, long long key) { return find_region(m, key); }
 
+// Voxels per batch of the filtered walk: pipelined (two batches in flight,
+// the single-map walk kernel) and plain (one batch stepped, loaded and
+// applied at a time, the multi-map batch kernel, whose run-time choice of
+// layers leaves fewer registers for the pipeline).
 #ifndef OHM_FAST_BATCH
 #define OHM_FAST_BATCH 4
+#endif
+#ifndef OHM_FAST_BATCH_PLAIN
+#define OHM_FAST_BATCH_PLAIN 8
 #endif
 #ifndef OHM_FAST_MIN_BLOCKS
 #define OHM_FAST_MIN_BLOCKS 4
 #endif
 constexpr int kFastBatch = OHM_FAST_BATCH;
+constexpr int kFastBatchPlain = OHM_FAST_BATCH_PLAIN;
+template <bool kPipe>
+constexpr int kFastBatchOf = kPipe ? kFastBatch : kFastBatchPlain;
 
 
 // Miss phase (Sec. III-C phase one) of one segment with the filtered walk
@@ -558,7 +619,13 @@ constexpr int kFastBatch = OHM_FAST_BATCH;
 // atomic add would flush to zero.  With kCas (NDT sample clearing, which must
 // see the update that crosses its threshold, or a miss increment >= 0) every
 // miss is a clamped compare-and-swap.
-template <bool kOcc, bool kCounts, bool kCas>
+//
+// kPipe: walk the next batch of voxels and issue its loads while the loads of
+// the batch before are in flight, then apply that batch (a software pipeline
+// of two batches); otherwise walk, load and apply one batch at a time.  The
+// pipeline wins where many voxels are still unknown (their compare-and-swaps
+// wait for a result) and costs a little on well-observed maps.
+template <bool kOcc, bool kCounts, bool kCas, bool kPipe = true>
 __device__ __forceinline__ void walk_segment_fast(const DeviceMap& m, int2 sg, unsigned int& ops,
                                                   const RayRec* prefetch = nullptr) {
   const int F = m.frac_bits;
@@ -593,13 +660,10 @@ __device__ __forceinline__ void walk_segment_fast(const DeviceMap& m, int2 sg, u
   uint32_t base = (uint32_t)slot << (3 * kRegionShift);
   unsigned int* occ = reinterpret_cast<unsigned int*>(m.occ);
   const unsigned int miss0 = __float_as_uint(__fadd_rn(0.0f, m.miss));  // an unknown voxel's first miss
-  // Software pipeline over batches of kFastBatch voxels: the next batch is
-  // walked and its loads issued while the previous batch's loads are in
-  // flight, then the previous batch's updates go out.
-  auto fill = [&](uint32_t (&off)[kFastBatch]) -> uint32_t {
+  auto fill = [&](uint32_t (&off)[kFastBatchOf<kPipe>]) -> uint32_t {
     uint32_t valid = 0;
 #pragma unroll
-    for (int j = 0; j < kFastBatch; ++j) {
+    for (int j = 0; j < kFastBatchOf<kPipe>; ++j) {
       off[j] = base | (mo ^ neg);  // voxel offset (< 2^31: at most 2^16 regions of 2^15 voxels)
       if (left > 0) {
         valid |= 1u << j;
@@ -630,22 +694,22 @@ __device__ __forceinline__ void walk_segment_fast(const DeviceMap& m, int2 sg, u
     }
     return valid;
   };
-  auto issue = [&](const uint32_t (&off)[kFastBatch], uint32_t valid, unsigned int (&old)[kFastBatch]) {
+  auto issue = [&](const uint32_t (&off)[kFastBatchOf<kPipe>], uint32_t valid, unsigned int (&old)[kFastBatchOf<kPipe>]) {
     if (kCounts) {
 #pragma unroll
-      for (int j = 0; j < kFastBatch; ++j)
+      for (int j = 0; j < kFastBatchOf<kPipe>; ++j)
         if ((valid >> j) & 1u) atomicAdd(m.counts + off[j], 1ULL);
     }
     if (kOcc) {
 #pragma unroll
-      for (int j = 0; j < kFastBatch; ++j) old[j] = ((valid >> j) & 1u) ? occ[off[j]] : 0u;
+      for (int j = 0; j < kFastBatchOf<kPipe>; ++j) old[j] = ((valid >> j) & 1u) ? occ[off[j]] : 0u;
     }
   };
-  auto apply = [&](const uint32_t (&off)[kFastBatch], uint32_t valid, unsigned int (&old)[kFastBatch]) {
+  auto apply = [&](const uint32_t (&off)[kFastBatchOf<kPipe>], uint32_t valid, unsigned int (&old)[kFastBatchOf<kPipe>]) {
     if (!kOcc) return;
     if (kCas) {
 #pragma unroll
-      for (int j = 0; j < kFastBatch; ++j)
+      for (int j = 0; j < kFastBatchOf<kPipe>; ++j)
         if ((valid >> j) & 1u) miss_cas(m, occ + off[j], old[j], ops);
       return;
     }
@@ -656,7 +720,7 @@ __device__ __forceinline__ void walk_segment_fast(const DeviceMap& m, int2 sg, u
     // added -- so the word read back replaces the one loaded.
     uint32_t init = 0;
 #pragma unroll
-    for (int j = 0; j < kFastBatch; ++j) {
+    for (int j = 0; j < kFastBatchOf<kPipe>; ++j) {
       if (!((valid >> j) & 1u)) continue;
       const float l = __uint_as_float(old[j]);
       if (l > m.l_min) {
@@ -669,25 +733,35 @@ __device__ __forceinline__ void walk_segment_fast(const DeviceMap& m, int2 sg, u
       }
     }
 #pragma unroll
-    for (int j = 0; j < kFastBatch; ++j) {
+    for (int j = 0; j < kFastBatchOf<kPipe>; ++j) {
       if (((init >> j) & 1u) && __uint_as_float(old[j]) > m.l_min) {
         atomicAdd(reinterpret_cast<float*>(occ + off[j]), m.miss);
         ++ops;
       }
     }
   };
-  uint32_t offA[kFastBatch], offB[kFastBatch];
-  unsigned int oldA[kFastBatch], oldB[kFastBatch];
-  uint32_t vA = fill(offA), vB;
-  issue(offA, vA, oldA);
-  while (vA) {
-    vB = fill(offB);
-    issue(offB, vB, oldB);
-    apply(offA, vA, oldA);
-    if (!vB) break;
-    vA = fill(offA);
+  if constexpr (kPipe) {
+    uint32_t offA[kFastBatchOf<kPipe>], offB[kFastBatchOf<kPipe>];
+    unsigned int oldA[kFastBatchOf<kPipe>], oldB[kFastBatchOf<kPipe>];
+    uint32_t vA = fill(offA), vB;
     issue(offA, vA, oldA);
-    apply(offB, vB, oldB);
+    while (vA) {
+      vB = fill(offB);
+      issue(offB, vB, oldB);
+      apply(offA, vA, oldA);
+      if (!vB) break;
+      vA = fill(offA);
+      issue(offA, vA, oldA);
+      apply(offB, vB, oldB);
+    }
+  } else {
+    while (left > 0) {
+      uint32_t off[kFastBatchOf<kPipe>];
+      unsigned int old[kFastBatchOf<kPipe>];
+      const uint32_t v = fill(off);
+      issue(off, v, old);
+      apply(off, v, old);
+    }
   }
 }
 
@@ -696,35 +770,16 @@ __device__ __host__ __forceinline__ bool walk_needs_cas(uint32_t layers, float m
   return !(miss < 0.0f) || ((layers & kLayerNdt) && ndt_clear > -INFINITY);
 }
 
-// Miss-phase walk of one segment with the map's layers chosen at run time.
-__device__ __forceinline__ void walk_segment_any(const DeviceMap& m, long long si, unsigned int& cas) {
-  const bool occ = (m.layers & kLayerOcc) != 0, cnt = (m.layers & kLayerCounts) != 0;
-  if (m.layers & kLayerDecay) {
-    if (occ && cnt)
-      walk_segment<true, true, true>(m, si, cas);
-    else if (occ)
-      walk_segment<true, false, true>(m, si, cas);
-    else if (cnt)
-      walk_segment<false, true, true>(m, si, cas);
-    else
-      walk_segment<false, false, true>(m, si, cas);
-    return;
-  }
-  const bool c = walk_needs_cas(m.layers, m.miss, m.ndt_clear);
-  const int2 sg = m.segs[si];
-  if (occ && cnt) {
-    if (c)
-      walk_segment_fast<true, true, true>(m, sg, cas);
-    else
-      walk_segment_fast<true, true, false>(m, sg, cas);
-  } else if (occ) {
-    if (c)
-      walk_segment_fast<true, false, true>(m, sg, cas);
-    else
-      walk_segment_fast<true, false, false>(m, sg, cas);
-  } else if (cnt) {
-    walk_segment_fast<false, true, false>(m, sg, cas);
-  }
+// Which miss walk a map takes: kWalkDecay (walk_segment, decay layer), else
+// the filtered walk's template arguments as bits (4: occupancy, 2: counts,
+// 1: every miss a compare-and-swap), or kWalkNone (no layer the walk updates).
+constexpr int kWalkNone = -1;
+constexpr int kWalkDecay = 8;
+__device__ __host__ __forceinline__ int walk_variant(uint32_t layers, float miss, float ndt_clear) {
+  const bool occ = (layers & kLayerOcc) != 0, cnt = (layers & kLayerCounts) != 0;
+  if (layers & kLayerDecay) return kWalkDecay;
+  if (!occ && !cnt) return kWalkNone;
+  return (occ ? 4 : 0) | (cnt ? 2 : 0) | ((occ && walk_needs_cas(layers, miss, ndt_clear)) ? 1 : 0);
 }
 
 // Position of a sample inside its voxel (fixed-point offset 0 .. 2^F - 1) in
