@@ -224,12 +224,13 @@ __global__ void __launch_bounds__(kBlock) k_batch_mean_apply(const BatchDesc* de
 __global__ void __launch_bounds__(kBlock) k_batch_tsdf_walk(const BatchDesc* desc, const BatchStep* step) {
   chain_enter();
   __shared__ BatchShared sh;
-  batch_stage(sh, desc, step, kRays);
-  const long long total = sh.pref[sh.n_maps];
+  batch_stage(sh, desc, step, kRaysPadded);
+  const long long total = sh.pref[sh.n_maps];  // a multiple of 32: whole warps iterate together
   OHM_BATCH_STRIDE(g, total) {
     const int mi = batch_find(sh, g);
     const DeviceMap& m = sh.maps[mi];
-    if (m.layers & kLayerTsdf) tsdf_walk_ray(m, g - sh.pref[mi]);
+    const long long i = g - sh.pref[mi];
+    if (m.layers & kLayerTsdf) tsdf_walk_ray(m, i, i < step->n[mi] && !latched(m));
   }
 }
 

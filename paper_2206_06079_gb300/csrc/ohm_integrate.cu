@@ -96,7 +96,9 @@ __global__ void __launch_bounds__(kBlock) k_prepare_tsdf(DeviceMap m, CallArgs a
 __global__ void __launch_bounds__(kBlock) k_tsdf_walk(DeviceMap m, long long n) {
   chain_enter();
   if (latched(m)) return;
-  OHM_GRID_STRIDE(i, n) tsdf_walk_ray(m, i);
+  // whole warps iterate together (the walk is warp-collective)
+  const long long np = (n + 31) & ~31LL;
+  OHM_GRID_STRIDE(i, np) tsdf_walk_ray(m, i, i < n);
 }
 
 __global__ void __launch_bounds__(kBlock) k_tsdf_apply(DeviceMap m) {

@@ -884,48 +884,131 @@ __device__ __forceinline__ void prepare_tsdf_ray(const DeviceMap& m, const CallA
 // d - (c - o).u), truncated to [-tau, tau], summed in 2^-32 m fixed point
 // with a count.  The first visitor of a voxel in this call records it for the
 // apply pass.
-__device__ __forceinline__ void tsdf_walk_ray(const DeviceMap& m, long long i) {
+//
+// Every lane of the warp calls this together (active = false for a lane
+// without a ray of this map); blocks have kBlock threads.  Neighbouring
+// pixels' rays cross the same band voxels (a 5 cm voxel at 1-2 m is crossed by
+// hundreds of them per frame), so the updates are aggregated per warp: each
+// thread walks kTsdfBatch voxels ahead; for each of them the lanes holding the
+// same voxel (__match_any_sync) form a group whose lowest lane adds the
+// group's count and sum of s with one atomic each (the s values pass through
+// shared memory).  The sums are of integers, so the result does not depend on
+// the grouping.  The first visitors the counts reveal are appended to the
+// touched list with one atomic per warp and batch.
+#ifndef OHM_TSDF_BATCH
+#define OHM_TSDF_BATCH 4
+#endif
+constexpr int kTsdfBatch = OHM_TSDF_BATCH;
+__device__ __forceinline__ void tsdf_walk_ray(const DeviceMap& m, long long i, bool active) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
   const int F = m.frac_bits;
   const long long U = 1LL << F;
   const long long half = U >> 1;
   const float to_m = (float)(m.voxel_size / (double)(1LL << F));
-  const TsdfRec r = m.trays[i];
-  if (!(r.flags & kRayValid)) return;
+  bool walking = false;
   Walker w;
-  walker_init(w, r.a, r.b, F, 0, 0);
-  int32_t slot = region_slot_of(m, w.vx, w.vy, w.vz);
-  if (slot < 0) {
-    atomicOr(m.status, kStatusMissing);
-    return;
-  }
-  uint32_t mo = local_morton(w.vx, w.vy, w.vz);
-  for (;;) {
-    const float ex = (float)(r.e[0] - ((long long)w.vx * U + half));
-    const float ey = (float)(r.e[1] - ((long long)w.vy * U + half));
-    const float ez = (float)(r.e[2] - ((long long)w.vz * U + half));
-    float s = (ex * r.u[0] + ey * r.u[1] + ez * r.u[2]) * to_m;
-    s = fminf(fmaxf(s, -m.tau_m), m.tau_m);
-    const long long sq = __float2ll_rn(s * 4294967296.0f);
-    const long long off = voxel_offset(slot, mo);
-    const unsigned int prev = atomicAdd(m.tsdf_cnt + off, 1u);
-    atomicAdd(reinterpret_cast<unsigned long long*>(m.tsdf_sum) + off, (unsigned long long)sq);
-    if (prev == 0) {
-      const unsigned long long t = atomicAdd(&m.calls->touched, 1ULL);
-      if (t < (unsigned long long)m.max_touched)
-        m.touched[t] = (int32_t)off;
-      else
-        atomicOr(m.status, kStatusScratch);
-    }
-    if (w.total == 0) break;
-    const int axis = walker_choose(w);
-    int32_t c, sg;
-    walker_step(w, axis, &c, &sg);
-    mo = morton_step(mo, morton_mask(axis), sg);
-    if ((c & ((1 << kRegionShift) - 1)) == (sg > 0 ? 0 : (1 << kRegionShift) - 1)) {
+  int32_t slot = -1;
+  uint32_t mo = 0;
+  long long e[3] = {0, 0, 0};
+  float u[3] = {0.f, 0.f, 0.f};
+  if (active) {
+    const TsdfRec r = m.trays[i];
+    if (r.flags & kRayValid) {
+      walker_init(w, r.a, r.b, F, 0, 0);
       slot = region_slot_of(m, w.vx, w.vy, w.vz);
       if (slot < 0) {
         atomicOr(m.status, kStatusMissing);
-        break;
+      } else {
+        walking = true;
+        mo = local_morton(w.vx, w.vy, w.vz);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          e[k] = r.e[k];
+          u[k] = r.u[k];
+        }
+      }
+    }
+  }
+  unsigned int* cnt = m.tsdf_cnt;
+  unsigned long long* sum = reinterpret_cast<unsigned long long*>(m.tsdf_sum);
+  __shared__ long long sbuf[kBlock];
+  while (__any_sync(full, walking)) {
+    uint32_t off[kTsdfBatch];  // voxel offsets (< 2^31: at most 2^16 regions of 2^15 voxels)
+    long long sq[kTsdfBatch];
+    uint32_t valid = 0;
+#pragma unroll
+    for (int j = 0; j < kTsdfBatch; ++j) {
+      off[j] = 0;
+      sq[j] = 0;
+      if (walking) {
+        const float ex = (float)(e[0] - ((long long)w.vx * U + half));
+        const float ey = (float)(e[1] - ((long long)w.vy * U + half));
+        const float ez = (float)(e[2] - ((long long)w.vz * U + half));
+        float sv = (ex * u[0] + ey * u[1] + ez * u[2]) * to_m;
+        sv = fminf(fmaxf(sv, -m.tau_m), m.tau_m);
+        sq[j] = __float2ll_rn(sv * 4294967296.0f);
+        off[j] = (uint32_t)voxel_offset(slot, mo);
+        valid |= 1u << j;
+        if (w.total == 0) {
+          walking = false;
+        } else {
+          const int axis = walker_choose(w);
+          int32_t c, sg;
+          walker_step(w, axis, &c, &sg);
+          mo = morton_step(mo, morton_mask(axis), sg);
+          if ((c & ((1 << kRegionShift) - 1)) == (sg > 0 ? 0 : (1 << kRegionShift) - 1)) {
+            slot = region_slot_of(m, w.vx, w.vy, w.vz);
+            if (slot < 0) {
+              atomicOr(m.status, kStatusMissing);
+              walking = false;
+            }
+          }
+        }
+      }
+    }
+    unsigned int prev[kTsdfBatch];
+#pragma unroll
+    for (int j = 0; j < kTsdfBatch; ++j) {
+      const bool vj = (valid >> j) & 1u;
+      const unsigned grp = __match_any_sync(full, vj ? off[j] : 0xffffffffu);  // offsets are < 2^31
+      sbuf[threadIdx.x] = sq[j];
+      __syncwarp();
+      prev[j] = 1u;
+      if (vj && lane == __ffs(grp) - 1) {
+        long long tot = 0;
+        for (unsigned g = grp; g; g &= g - 1) tot += sbuf[(threadIdx.x & ~31u) + __ffs(g) - 1];
+        prev[j] = atomicAdd(cnt + off[j], (unsigned int)__popc(grp));
+        atomicAdd(sum + off[j], (unsigned long long)tot);
+      }
+      __syncwarp();
+    }
+    // first visitors of a voxel in this call: one table range per warp
+    uint32_t first = 0;
+#pragma unroll
+    for (int j = 0; j < kTsdfBatch; ++j)
+      if (prev[j] == 0) first |= 1u << j;
+    const unsigned int nf = __popc(first);
+    unsigned int incl = nf;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const unsigned int t = __shfl_up_sync(full, incl, d);
+      if (lane >= d) incl += t;
+    }
+    const unsigned int total = __shfl_sync(full, incl, 31);
+    if (total == 0) continue;
+    unsigned long long base = 0;
+    if (lane == 31) base = atomicAdd(&m.calls->touched, (unsigned long long)total);
+    base = __shfl_sync(full, base, 31);
+    unsigned long long pos = base + (incl - nf);
+#pragma unroll
+    for (int j = 0; j < kTsdfBatch; ++j) {
+      if ((first >> j) & 1u) {
+        if (pos < (unsigned long long)m.max_touched)
+          m.touched[pos] = (int32_t)off[j];
+        else
+          atomicOr(m.status, kStatusScratch);
+        ++pos;
       }
     }
   }
