@@ -187,23 +187,24 @@ __global__ void __launch_bounds__(kBlock, OHM_FAST_MIN_BLOCKS) k_batch_walk_fast
 __global__ void __launch_bounds__(kBlock) k_batch_hits(const BatchDesc* desc, const BatchStep* step) {
   chain_enter();
   __shared__ BatchShared sh;
-  batch_stage(sh, desc, step, kRays);
-  const long long total = sh.pref[sh.n_maps];
+  batch_stage(sh, desc, step, kRaysPadded);
+  const long long total = sh.pref[sh.n_maps];  // a multiple of 32: whole warps iterate together
   OHM_BATCH_STRIDE(g, total) {
     const int mi = batch_find(sh, g);
     const DeviceMap& m = sh.maps[mi];
     const long long i = g - sh.pref[mi];
+    const bool a = i < step->n[mi] && !latched(m);
     const int sel = ((m.layers & kLayerOcc) ? 4 : 0) | ((m.layers & kLayerCounts) ? 2 : 0) | ((m.layers & kLayerNdt) ? 1 : 0);
     switch (sel) {
-      case 7: hit_ray<true, true, true>(m, i); break;
-      case 6: hit_ray<true, true, false>(m, i); break;
-      case 5: hit_ray<true, false, true>(m, i); break;
-      case 4: hit_ray<true, false, false>(m, i); break;
-      case 3: hit_ray<false, true, true>(m, i); break;
-      case 2: hit_ray<false, true, false>(m, i); break;
-      case 1: hit_ray<false, false, true>(m, i); break;
+      case 7: hit_ray<true, true, true>(m, i, a); break;
+      case 6: hit_ray<true, true, false>(m, i, a); break;
+      case 5: hit_ray<true, false, true>(m, i, a); break;
+      case 4: hit_ray<true, false, false>(m, i, a); break;
+      case 3: hit_ray<false, true, true>(m, i, a); break;
+      case 2: hit_ray<false, true, false>(m, i, a); break;
+      case 1: hit_ray<false, false, true>(m, i, a); break;
       default:
-        if (m.layers & kLayerMean) hit_ray<false, false, false>(m, i);
+        if (m.layers & kLayerMean) hit_ray<false, false, false>(m, i, a);
         break;
     }
   }

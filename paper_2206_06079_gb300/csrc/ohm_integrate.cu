@@ -76,7 +76,9 @@ template <bool kOcc, bool kCounts, bool kNdt>
 __global__ void __launch_bounds__(kBlock) k_hits(DeviceMap m, long long n) {
   chain_enter();
   if (latched(m)) return;
-  OHM_GRID_STRIDE(i, n) hit_ray<kOcc, kCounts, kNdt>(m, i);
+  // whole warps iterate together (the update is warp-collective)
+  const long long np = (n + 31) & ~31LL;
+  OHM_GRID_STRIDE(i, np) hit_ray<kOcc, kCounts, kNdt>(m, i, i < n);
 }
 
 // Runs for failed calls too: it then only clears the per-call sums.

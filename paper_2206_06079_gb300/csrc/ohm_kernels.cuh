@@ -788,38 +788,89 @@ __device__ __forceinline__ unsigned long long sub_voxel10(long long offset, int 
   return F >= 10 ? (unsigned long long)(offset >> (F - 10)) : (unsigned long long)(offset << (10 - F));
 }
 
+// Clamped log-odds update of a voxel by n hits of the same delta: n steps
+// l <- min(max(l + delta, l_min), l_max) from the stored value, written with
+// one compare-and-swap (retried while other threads change the word).  The
+// step map composes, so n hits at once equal n hits one after another.
+__device__ __forceinline__ void logodds_update_n(const DeviceMap& m, float* p, float delta, unsigned int n) {
+  unsigned int* u = reinterpret_cast<unsigned int*>(p);
+  unsigned int old = *u;
+  for (int it = 0; it < 256; ++it) {
+    float v = logodds_value(__uint_as_float(old), m.l_min);
+    for (unsigned int t = 0; t < n; ++t) {
+      const float nv = fminf(fmaxf(__fadd_rn(v, delta), m.l_min), m.l_max);
+      if (nv == v) break;  // at a clamp: later steps change nothing
+      v = nv;
+    }
+    const unsigned int nb = __float_as_uint(v);
+    if (nb == old) return;
+    const unsigned int prev = atomicCAS(u, old, nb);
+    if (prev == old) return;
+    old = prev;
+  }
+  atomicOr(m.status, kStatusCasLimit);
+}
+
 // Sample phase (Sec. III-C phase two) for one ray: the voxel holding its
 // sample takes a hit; with the NDT layer it also accumulates the sample's
 // exact integer moments (count, sum, outer-product sum of the position inside
 // the voxel), from which mean and covariance are formed when queried.
+//
+// Every lane of the warp calls this together (active = false for a lane
+// without a ray of this map).  Neighbouring rays often end in the same voxel,
+// and concurrent compare-and-swaps on one word retry, so the lanes holding the
+// same voxel (__match_any_sync) form a group whose lowest lane applies all of
+// the group's occupancy hits, n clamped steps in one compare-and-swap, and
+// adds the group's hit count.  The voxel-mean fields and NDT moments are
+// fire-and-forget integer adds per lane (summing them across the group first
+// was measured slower).
 template <bool kOcc, bool kCounts, bool kNdt>
-__device__ __forceinline__ void hit_ray(const DeviceMap& m, long long i) {
+__device__ __forceinline__ void hit_ray(const DeviceMap& m, long long i, bool active) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
   const int F = m.frac_bits;
   const long long U = 1LL << F;
-  const RayRec r = m.rays[i];
-  if (!(r.flags & kRaySample)) return;
-  long long b[3];
-  ray_end(r, F, b);
-  const int32_t vx = (int32_t)(b[0] >> F), vy = (int32_t)(b[1] >> F), vz = (int32_t)(b[2] >> F);
-  const int32_t slot = region_slot_of(m, vx, vy, vz);
-  if (slot < 0) {
-    atomicOr(m.status, kStatusMissing);
-    return;
+  bool ok = false;
+  long long b[3] = {0, 0, 0};
+  int32_t vx = 0, vy = 0, vz = 0, slot = 0;
+  uint32_t mo = 0;
+  if (active) {
+    const RayRec r = m.rays[i];
+    if (r.flags & kRaySample) {
+      ray_end(r, F, b);
+      vx = (int32_t)(b[0] >> F);
+      vy = (int32_t)(b[1] >> F);
+      vz = (int32_t)(b[2] >> F);
+      slot = region_slot_of(m, vx, vy, vz);
+      if (slot < 0) {
+        atomicOr(m.status, kStatusMissing);
+      } else {
+        ok = true;
+        mo = local_morton(vx, vy, vz);
+      }
+    }
   }
-  const uint32_t mo = local_morton(vx, vy, vz);
-  const long long off = voxel_offset(slot, mo);
-  if (kOcc) logodds_update(m, m.occ + off, m.hit);
-  if (kCounts) atomicAdd(m.counts + off, 1ULL << 32);
+  // the NDT block is looked up before the occupancy update, so that the two
+  // loads are in flight together
+  int32_t ns = -1;
+  if (kNdt && ok) ns = m.ndt_slot[slot];
+  const long long off = ok ? voxel_offset(slot, mo) : 0;
+  const unsigned grp = __match_any_sync(full, ok ? (uint32_t)off : 0xffffffffu);  // offsets are < 2^31
+  const bool lead = ok && lane == __ffs(grp) - 1;
+  const unsigned int n = __popc(grp);
+  if (kOcc && lead) logodds_update_n(m, m.occ + off, m.hit, n);
+  if (kCounts && lead) atomicAdd(m.counts + off, (unsigned long long)n << 32);
+  if (!ok) return;
   if (m.layers & kLayerMean) {
     // 10-bit position inside the voxel per axis; per-call sums (x | y << 32, z | count << 32)
-    const unsigned long long p[3] = {sub_voxel10(b[0] - (long long)vx * U, F), sub_voxel10(b[1] - (long long)vy * U, F),
-                                     sub_voxel10(b[2] - (long long)vz * U, F)};
-    atomicAdd(m.vmean_acc + 2 * off, p[0] | (p[1] << 32));
-    const unsigned long long prev = atomicAdd(m.vmean_acc + 2 * off + 1, p[2] | (1ULL << 32));
+    const unsigned long long p0 =
+        sub_voxel10(b[0] - (long long)vx * U, F) | (sub_voxel10(b[1] - (long long)vy * U, F) << 32);
+    const unsigned long long p1 = sub_voxel10(b[2] - (long long)vz * U, F) | (1ULL << 32);
+    atomicAdd(m.vmean_acc + 2 * off, p0);
+    const unsigned long long prev = atomicAdd(m.vmean_acc + 2 * off + 1, p1);
     if ((prev >> 32) == 0) m.mean_list[atomicAdd(&m.calls->mean_touched, 1)] = (int32_t)off;
   }
   if (kNdt) {
-    const int32_t ns = m.ndt_slot[slot];
     if (ns < 0) {
       atomicOr(m.status, kStatusMissing);
       return;
