@@ -55,12 +55,6 @@ inline void launch_chained(void (*kernel)(K...), unsigned grid, cudaStream_t str
   }
 }
 
-// Clamped log-odds update of one voxel (Eq. 2 with the clamp of Sec. II-B):
-// l <- min(max(l0 + delta, l_min), l_max), l0 = 0 for an unknown (NaN) voxel.
-// Concurrent updates of one voxel are serialised by compare-and-swap; within
-// a kernel all updates of a voxel use the same delta, so the result does not
-// depend on their order.  The loop is bounded: every failed CAS means another
-// thread advanced the value one step toward its clamp.
 // Log-odds of a stored occupancy word for an update: an unknown voxel (NaN)
 // starts from the prior 0, and a value stored below l_min stands for l_min
 // (the miss walk may leave it there, see walk_segment_fast).
@@ -69,21 +63,6 @@ __device__ __forceinline__ float logodds_value(float s, float l_min) { return s 
 // Log-odds a stored occupancy word reports: NaN stays unknown, a value stored
 // below l_min reads as l_min.
 __device__ __forceinline__ float logodds_read(float s, float l_min) { return s < l_min ? l_min : s; }
-
-__device__ __forceinline__ void logodds_update(const DeviceMap& m, float* p, float delta) {
-  unsigned int* u = reinterpret_cast<unsigned int*>(p);
-  unsigned int old = *u;
-  for (int it = 0; it < 256; ++it) {
-    const float l0 = logodds_value(__uint_as_float(old), m.l_min);
-    const float nv = fminf(fmaxf(__fadd_rn(l0, delta), m.l_min), m.l_max);
-    const unsigned int nb = __float_as_uint(nv);
-    if (nb == old) return;
-    const unsigned int prev = atomicCAS(u, old, nb);
-    if (prev == old) return;
-    old = prev;
-  }
-  atomicOr(m.status, kStatusCasLimit);
-}
 
 // Quantise a ray, returns false when it is skipped (non-finite coordinate or
 // a point beyond the fixed-point range).
@@ -218,7 +197,7 @@ __device__ __forceinline__ void after_miss(const DeviceMap& m, long long off, un
 }
 
 // Retry a clamped log-odds CAS whose first attempt found `cur` instead of
-// the value it expected (see logodds_update).
+// the value it expected (see logodds_update_n).
 static __device__ __noinline__ void logodds_retry(const DeviceMap& m, unsigned int* u, unsigned int cur, float delta) {
   for (int it = 0; it < 256; ++it) {
     const float l0 = logodds_value(__uint_as_float(cur), m.l_min);
@@ -788,10 +767,13 @@ __device__ __forceinline__ unsigned long long sub_voxel10(long long offset, int 
   return F >= 10 ? (unsigned long long)(offset >> (F - 10)) : (unsigned long long)(offset << (10 - F));
 }
 
-// Clamped log-odds update of a voxel by n hits of the same delta: n steps
-// l <- min(max(l + delta, l_min), l_max) from the stored value, written with
-// one compare-and-swap (retried while other threads change the word).  The
-// step map composes, so n hits at once equal n hits one after another.
+// Clamped log-odds update of a voxel by n hits of the same delta (Eq. 2 with
+// the clamp of Sec. II-B): n steps l <- min(max(l + delta, l_min), l_max)
+// from the stored value (0 for an unknown voxel), written with one
+// compare-and-swap.  Within a kernel all updates of a voxel use the same
+// delta and the step map composes, so the result depends neither on their
+// order nor on how they are grouped.  The loop is bounded: every failed CAS
+// means another thread advanced the value toward its clamp.
 __device__ __forceinline__ void logodds_update_n(const DeviceMap& m, float* p, float delta, unsigned int n) {
   unsigned int* u = reinterpret_cast<unsigned int*>(p);
   unsigned int old = *u;
