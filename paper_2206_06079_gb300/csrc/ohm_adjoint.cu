@@ -182,22 +182,29 @@ __global__ void __launch_bounds__(kBlock) k_tsdf_backward(DeviceMap m, DepthFram
           if ((c & ((1 << kRegionShift) - 1)) == (sg > 0 ? 0 : (1 << kRegionShift) - 1))
             slot = region_slot_of(m, w.vx, w.vy, w.vz);
         }
-        double ge[3], go[3];
+        // The chain rule from here on is plain float arithmetic (its inputs
+        // are floats; the gradients are checked to 1e-3 relative), summed
+        // over pixels in double.  The band above is recomputed in double
+        // exactly as the forward pass, since it decides the voxel set.
+        const float rdm = 1.0f / dm;
+        float ge[3], go[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-          ge[k] = (double)A * u[k] + (double)B[k] / dm;
-          go[k] = -(double)B[k] / dm;
+          go[k] = -B[k] * rdm;
+          ge[k] = A * u[k] - go[k];
         }
-        double dz = 0.0;
+        const float ptf[3] = {(float)pt[0], (float)pt[1], (float)pt[2]};
+        float dz = 0.f;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) dz += ge[k] * (f.R[3 * k] * pt[0] + f.R[3 * k + 1] * pt[1] + f.R[3 * k + 2] * pt[2]);
-        gz = (float)dz;
-        const double E[3] = {e[0], e[1], e[2]}, O[3] = {f.t[0], f.t[1], f.t[2]};
+        for (int k = 0; k < 3; ++k)
+          dz += ge[k] * ((float)f.R[3 * k] * ptf[0] + (float)f.R[3 * k + 1] * ptf[1] + (float)f.R[3 * k + 2] * ptf[2]);
+        gz = dz;
+        const float O[3] = {(float)f.t[0], (float)f.t[1], (float)f.t[2]};
 #pragma unroll
-        for (int k = 0; k < 3; ++k) acc[k] += ge[k] + go[k];
-        acc[3] += E[1] * ge[2] - E[2] * ge[1] + O[1] * go[2] - O[2] * go[1];
-        acc[4] += E[2] * ge[0] - E[0] * ge[2] + O[2] * go[0] - O[0] * go[2];
-        acc[5] += E[0] * ge[1] - E[1] * ge[0] + O[0] * go[1] - O[1] * go[0];
+        for (int k = 0; k < 3; ++k) acc[k] += (double)(ge[k] + go[k]);
+        acc[3] += (double)(e[1] * ge[2] - e[2] * ge[1] + O[1] * go[2] - O[2] * go[1]);
+        acc[4] += (double)(e[2] * ge[0] - e[0] * ge[2] + O[2] * go[0] - O[0] * go[2]);
+        acc[5] += (double)(e[0] * ge[1] - e[1] * ge[0] + O[0] * go[1] - O[1] * go[0]);
       }
       grad_depth[p] = gz;
     }

@@ -339,6 +339,47 @@ def test_voxel_mean_tunnel_with_every_layer():
 
 
 
+def _shared_end_rays(seed, n_origins_per_ray):
+    """Rays whose samples pile into a few voxels: groups of 1, 2, 31, 32, 33,
+    200 and 1000 rays end inside the same voxel (jittered within it), in an
+    interleaved order so that warps see groups of every size, plus rays that
+    pass through those voxels to end beyond them."""
+    rng = np.random.default_rng(seed)
+    centres = np.array([[1.05, 0.35, 0.25], [1.15, 0.35, 0.25], [-0.85, 1.45, 0.65], [0.45, -1.25, -0.35],
+                        [1.65, 1.65, 0.05], [-1.35, -0.55, 1.15], [0.05, 0.05, 1.95]])
+    sizes = [1, 2, 31, 32, 33, 200, 1000]
+    ends = []
+    for c, k in zip(centres, sizes):
+        ends.append(c + rng.uniform(-0.045, 0.045, size=(k, 3)))
+        ends.append(c * 1.4 + rng.uniform(-0.02, 0.02, size=(k // 3 + 1, 3)))  # through the voxel, beyond it
+    e = np.concatenate(ends)
+    e = e[rng.permutation(len(e))].astype(np.float32)
+    if n_origins_per_ray:
+        o = rng.uniform(-0.04, 0.04, size=e.shape).astype(np.float32)
+    else:
+        o = np.array([[0.01, 0.02, 0.03]], np.float32)
+    f = np.zeros(len(e), np.uint8)
+    f[rng.uniform(size=len(e)) < 0.05] = synth.FLAG_NO_RETURN
+    return synth.RaySet(torch.from_numpy(o), torch.from_numpy(e), torch.from_numpy(f))
+
+
+@pytest.mark.parametrize("layers", ["occ_counts_ndt", "occ_mean"])
+@pytest.mark.parametrize("per_ray_origins", [False, True])
+def test_many_samples_in_one_voxel(layers, per_ray_origins):
+    """Samples of many rays in one voxel: the hit kernel applies a warp's hits
+    on a voxel as one n-step clamped update (saturating at l_max after a few
+    hits), and the counts, NDT moments and voxel-mean sums of every sample.
+    Bit-identical to the oracle's one-sample-at-a-time updates."""
+    L = W.OCC | W.COUNTS | W.NDT if layers == "occ_counts_ndt" else W.OCC | W.MEAN
+    p = W.room_params(layers=L, max_regions=1024, max_ndt_regions=1024, max_rays=4096, max_range=3.0)
+    gm, om = _pair(p)
+    for scan in range(3):
+        _integrate_both(gm, om, _shared_end_rays(10 * scan + 1, per_ray_origins))
+    compare_dense(gm, om, counts=layers == "occ_counts_ndt", mean=layers == "occ_mean")
+    if layers == "occ_counts_ndt":
+        compare_ndt(gm, om)
+
+
 @pytest.mark.parametrize("steps", [1, 4, 100000])
 def test_many_scans_over_saturated_space(steps):
     """Ten scans over the same stretch of tunnel drive most free voxels to the
