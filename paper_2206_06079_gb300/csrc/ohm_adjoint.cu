@@ -140,18 +140,9 @@ __global__ void __launch_bounds__(kBlock) k_tsdf_backward(DeviceMap m, DepthFram
       }
       if (ok) {
         // the band walk of the forward pass, recomputed
-        double t0 = __dsub_rn(len, m.tau_q);
-        if (t0 < 0.0) t0 = 0.0;
-        const double t1 = __dadd_rn(len, m.tau_q);
-        const double f0 = __ddiv_rn(t0, len), f1 = __ddiv_rn(t1, len);
         long long a[3], b[3];
         float u[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          a[k] = qo[k] + __double2ll_rn(__dmul_rn(d[k], f0));
-          b[k] = qo[k] + __double2ll_rn(__dmul_rn(d[k], f1));
-          u[k] = (float)__ddiv_rn(d[k], len);
-        }
+        tsdf_band(qo, d, len, m.tau_q, a, b, u);
         const float dm = (float)(len * m.voxel_size / (double)U);
         Walker w;
         walker_init(w, a, b, F, 0, 0);

@@ -5,6 +5,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 #include <cuda_runtime.h>
 
 // Loop unrolling hint for code compiled for both host and device.
@@ -833,6 +834,114 @@ __device__ __forceinline__ unsigned long long warp_reserve(unsigned long long* c
 }
 
 // Warp sum of a 32-bit value, added by one lane to two 64-bit counters; full warp.
+// ---------------------------------------------------------------------------
+// TSDF band of a ray (Sec. II-F) from the double length len of its fixed-point
+// difference d (ray_length) and the band half-width tau (fixed-point units):
+// with t0 = max(fl(len - tau), 0) and t1 = fl(len + tau),
+//     a_k = qo_k + rint(fl(d_k fl(t0 / len))),   b_k likewise with t1,
+//     u_k = float(fl(d_k / len)),
+// every operation in IEEE double as written.  The device's double divisions
+// are slow, so the five quotients go through one reciprocal
+// rho = fl(1 / len), and the result is taken when it provably equals the
+// one above.  With u = 2^-53 and |e_i| <= u:
+//   f' = fl(t rho) = (t / len)(1 + e1)(1 + e2), P' = fl(d_k f') = X (1 + e1)(1 + e2)(1 + e3)
+//   with X = d_k t / len, against P = fl(d_k fl(t / len)) = X (1 + e4)(1 + e5):
+//   |P' - P| < 5.01 u |X| < 6 ulp(P').  So rint(P) = rint(P') unless a
+//   half-integer lies within 6 ulp of P'; P' is taken when none lies within
+//   16 ulp (near_half_integer).
+//   q' = fl(d_k rho) = (d_k / len)(1 + e1)(1 + e6), q = fl(d_k / len):
+//   |q' - q| < 4 ulp(q'), so float(q) = float(q') unless a float rounding
+//   boundary (a midpoint between adjacent floats: the 29 bits below float
+//   precision equal 2^28) lies within 4 ulp; q' is taken when it lies more
+//   than 16 ulp away (near_float_midpoint).
+// Otherwise every quotient is formed as written.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ unsigned long long dbits(double x) {
+#ifdef __CUDA_ARCH__
+  return (unsigned long long)__double_as_longlong(x);
+#else
+  unsigned long long b;
+  std::memcpy(&b, &x, sizeof(b));
+  return b;
+#endif
+}
+__host__ __device__ __forceinline__ double dmul_rn(double a, double b) {
+#ifdef __CUDA_ARCH__
+  return __dmul_rn(a, b);
+#else
+  return a * b;
+#endif
+}
+__host__ __device__ __forceinline__ double ddiv_rn(double a, double b) {
+#ifdef __CUDA_ARCH__
+  return __ddiv_rn(a, b);
+#else
+  return a / b;
+#endif
+}
+__host__ __device__ __forceinline__ double drcp_rn(double a) {
+#ifdef __CUDA_ARCH__
+  return __drcp_rn(a);
+#else
+  return 1.0 / a;
+#endif
+}
+__host__ __device__ __forceinline__ long long d2ll_rn(double a) {
+#ifdef __CUDA_ARCH__
+  return __double2ll_rn(a);
+#else
+  return std::llrint(a);  // round to nearest even (the default rounding mode)
+#endif
+}
+
+// A half-integer k + 1/2 within 16 ulp of |x| (|x| < 2^52)?
+__host__ __device__ __forceinline__ bool near_half_integer(double x) {
+  const unsigned long long b = dbits(x) & 0x7fffffffffffffffULL;
+  const int e = (int)(b >> 52) - 1023;  // |x| in [2^e, 2^(e+1))
+  const unsigned long long m = b & ((1ULL << 52) - 1);
+  if (e >= 52) return false;  // an integer
+  if (e >= 0) {
+    const int w = 52 - e;  // fraction bits, in units of ulp(x)
+    const unsigned long long f = m & ((1ULL << w) - 1), h = 1ULL << (w - 1);
+    return (f > h ? f - h : h - f) <= 16;
+  }
+  if (e == -1) return m <= 16;                   // just above 1/2
+  if (e == -2) return m >= (1ULL << 52) - 32;    // just below 1/2
+  return false;
+}
+
+// A float rounding boundary within 16 ulp of the (normal) double q?
+__host__ __device__ __forceinline__ bool near_float_midpoint(double q) {
+  const unsigned long long low = dbits(q) & ((1ULL << 29) - 1), mid = 1ULL << 28;
+  return (low > mid ? low - mid : mid - low) <= 16;
+}
+
+__host__ __device__ inline void tsdf_band(const long long qo[3], const double d[3], double len, double tau,
+                                          long long a[3], long long b[3], float u[3]) {
+  double t0 = len - tau;
+  if (t0 < 0.0) t0 = 0.0;
+  const double t1 = len + tau;
+  const double rho = drcp_rn(len);
+  const double f0 = dmul_rn(t0, rho), f1 = dmul_rn(t1, rho);
+  bool exact = false;
+OHM_UNROLL
+  for (int k = 0; k < 3; ++k) {
+    const double p0 = dmul_rn(d[k], f0), p1 = dmul_rn(d[k], f1), q = dmul_rn(d[k], rho);
+    exact = exact || near_half_integer(p0) || near_half_integer(p1) || near_float_midpoint(q);
+    a[k] = qo[k] + d2ll_rn(p0);
+    b[k] = qo[k] + d2ll_rn(p1);
+    u[k] = (float)q;
+  }
+  if (!exact) return;
+  const double g0 = ddiv_rn(t0, len), g1 = ddiv_rn(t1, len);
+OHM_UNROLL
+  for (int k = 0; k < 3; ++k) {
+    a[k] = qo[k] + d2ll_rn(dmul_rn(d[k], g0));
+    b[k] = qo[k] + d2ll_rn(dmul_rn(d[k], g1));
+    u[k] = (float)ddiv_rn(d[k], len);
+  }
+}
+
 __device__ __forceinline__ void warp_add(unsigned long long* counter, unsigned long long* counter2, unsigned int value) {
   unsigned int total = __reduce_add_sync(0xffffffffu, value);
   if ((threadIdx.x & 31) == 0 && total != 0) {

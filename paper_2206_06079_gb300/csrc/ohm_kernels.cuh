@@ -887,17 +887,9 @@ __device__ __forceinline__ void prepare_tsdf_ray(const DeviceMap& m, const CallA
       ok = len > m.rmin_q && len <= m.rmax_q && in_extent(qo, F) && in_extent(qe, F);
     }
     if (ok) {
-      double t0 = __dsub_rn(len, m.tau_q);
-      if (t0 < 0.0) t0 = 0.0;
-      const double t1 = __dadd_rn(len, m.tau_q);
-      const double f0 = __ddiv_rn(t0, len), f1 = __ddiv_rn(t1, len);
+      tsdf_band(qo, d, len, m.tau_q, r.a, r.b, r.u);
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        r.a[k] = qo[k] + __double2ll_rn(__dmul_rn(d[k], f0));
-        r.b[k] = qo[k] + __double2ll_rn(__dmul_rn(d[k], f1));
-        r.e[k] = qe[k];
-        r.u[k] = (float)__ddiv_rn(d[k], len);
-      }
+      for (int k = 0; k < 3; ++k) r.e[k] = qe[k];
       r.flags = kRayValid;
       long long l1 = 0;
 #pragma unroll

@@ -110,3 +110,18 @@ def test_region_resolution_walk_covers_voxel_regions(checker):
             if not want or want[-1] != x:
                 want.append(x)
         assert r.tolist() == want
+
+
+def test_tsdf_band_reciprocal_equals_divisions(tmp_path):
+    """The TSDF band end points and direction formed through one reciprocal
+    (tsdf_band, compiled for the host) equal the direct double divisions on
+    random rays and on rays built to land on half-integers and float rounding
+    midpoints, where it falls back to the divisions."""
+    exe = str(tmp_path / "band_check")
+    subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-std=c++17", "-O2", "-x", "cu",
+                    os.path.join(HERE, "host", "band_check.cu"), "-o", exe], check=True, capture_output=True)
+    out = subprocess.run([exe], capture_output=True, text=True)
+    assert out.returncode == 0, (out.returncode, out.stderr[-500:])
+    tok = out.stdout.split()
+    cases, fallback = int(tok[1]), int(tok[3])
+    assert cases > 600000 and 0 < fallback < cases
