@@ -25,7 +25,9 @@
 // p (relative to its corner) and d = p_j - S / n,
 //   dL/dp_j = (1 / n) [ gm + (G + G^T) d ],  G = upper-triangular(gc),
 // then dL/de_sensor = R^T dL/dp_j and the twist as for the TSDF.
+#include <cstring>
 #include <string>
+#include <vector>
 
 #include "ohm_kernels.cuh"
 
@@ -39,18 +41,21 @@ struct DepthFrame {
   double R[9];
   double t[3];
   double z_min, z_max;
+  const double* pxy;  // (u - cx) / fx for u < width, then (v - cy) / fy for v < height
 };
 
 // Back-projection of one pixel, one rounding per double operation:
 // x = ((u - cx) / fx) z, y = ((v - cy) / fy) z, e_k = ((R_k0 x + R_k1 y) + R_k2 z) + t_k,
 // rounded to float.  A depth outside (z_min, z_max] gives a NO_RETURN ray at z_max.
+// The quotients depend on the column or the row only: they come from the
+// frame's table, formed on the host by the same double operations.
 __device__ __forceinline__ bool depth_ray(const DepthFrame& f, long long pix, float e[3], double pt[3]) {
   const int u = (int)(pix % f.width), v = (int)(pix / f.width);
   const double z = (double)f.depth[pix];
   const bool valid = z > f.z_min && z <= f.z_max;
   const double zz = valid ? z : f.z_max;
-  const double px = __ddiv_rn(__dsub_rn((double)u, f.cx), f.fx);
-  const double py = __ddiv_rn(__dsub_rn((double)v, f.cy), f.fy);
+  const double px = f.pxy[u];
+  const double py = f.pxy[f.width + v];
   const double x = __dmul_rn(px, zz), y = __dmul_rn(py, zz);
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
@@ -369,7 +374,42 @@ bool frame_from(const float* depth, int32_t width, int32_t height, const double*
   }
   f->z_min = z_min;
   f->z_max = z_max;
+  f->pxy = nullptr;
   return f->fx != 0.0 && f->fy != 0.0;
+}
+
+// The frame's per-column and per-row quotients, kept on the device for the
+// last image size and intrinsics (rebuilt when they change).
+cudaError_t frame_tables(ohm_map* map, DepthFrame* f, cudaStream_t s) {
+  const double key[6] = {(double)f->width, (double)f->height, f->fx, f->fy, f->cx, f->cy};
+  const long long n = (long long)f->width + f->height;
+  if (map->pxy && std::memcmp(key, map->pxy_key, sizeof(key)) == 0) {
+    f->pxy = map->pxy;
+    return cudaSuccess;
+  }
+  // earlier work of the map may still read the old table
+  cudaError_t e = map->work_done ? cudaStreamWaitEvent(s, map->work_done, 0) : cudaSuccess;
+  if (e == cudaSuccess && n > map->pxy_cap) {
+    if (map->pxy) {
+      e = cudaStreamSynchronize(s);
+      if (e == cudaSuccess) e = cudaFree(map->pxy);
+      map->pxy = nullptr;
+      map->pxy_cap = 0;
+    }
+    const long long cap = n > 4096 ? n : 4096;
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&map->pxy), sizeof(double) * cap);
+    if (e != cudaSuccess) return e;
+    map->pxy_cap = cap;
+  }
+  if (e != cudaSuccess) return e;
+  std::vector<double> t((size_t)n);
+  for (int u = 0; u < f->width; ++u) t[u] = ((double)u - f->cx) / f->fx;
+  for (int v = 0; v < f->height; ++v) t[f->width + v] = ((double)v - f->cy) / f->fy;
+  e = cudaMemcpyAsync(map->pxy, t.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  std::memcpy(map->pxy_key, key, sizeof(key));
+  f->pxy = map->pxy;
+  return cudaSuccess;
 }
 
 ohm_status afail(ohm_status code, const std::string& msg) {
@@ -407,6 +447,11 @@ ohm_status ohm_integrate_depth(ohm_map* map, const float* depth, int32_t width, 
   if (prev != map->device) cudaSetDevice(map->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int blocks = (int)((n + kBlock - 1) / kBlock < 4096 ? (n + kBlock - 1) / kBlock : 4096);
+  cudaError_t et = frame_tables(map, &f, s);
+  if (et != cudaSuccess) {
+    if (prev >= 0 && prev != map->device) cudaSetDevice(prev);
+    return afail(OHM_ERR_CUDA, std::string("integrate_depth: ") + cudaGetErrorString(et));
+  }
   k_depth_rays<<<blocks, kBlock, 0, s>>>(f, map->stage_origins, map->stage_endpoints, map->stage_flags);
   map->launches += 1;
   CallArgs a;
@@ -453,6 +498,7 @@ ohm_status ohm_tsdf_backward(ohm_map* map, const float* depth, int32_t width, in
   const long long n = (long long)width * height;
   const int qb = (int)(n_query > 0 ? ((n_query + kBlock - 1) / kBlock < 4096 ? (n_query + kBlock - 1) / kBlock : 4096) : 0);
   const int pb = (int)((n + kBlock - 1) / kBlock < 4096 ? (n + kBlock - 1) / kBlock : 4096);
+  if (e == cudaSuccess) e = frame_tables(map, &f, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(grad_twist, 0, 6 * sizeof(double), s);
   if (e == cudaSuccess && qb) {
     k_grad_scatter<<<qb, kBlock, 0, s>>>(map->d, query_points, grad_query, n_query, 0);

@@ -79,7 +79,7 @@ void free_map(ohm_map* m) {
                   d.ndt, d.tsdf, d.tsdf_cnt, d.tsdf_sum, d.grad, d.ndt_grad, d.status, d.calls, d.rays, d.decay_rays, d.trays, d.segs, d.touched,
                   d.stamp, d.born, d.ndt_born, d.free_slots, d.ndt_free, d.free_info, d.restore_keys,
                   m->stage_origins, m->stage_endpoints, m->stage_flags, m->hin_origins[0], m->hin_origins[1],
-                  m->hin_endpoints[0], m->hin_endpoints[1], m->hin_flags[0], m->hin_flags[1]};
+                  m->hin_endpoints[0], m->hin_endpoints[1], m->hin_flags[0], m->hin_flags[1], m->pxy};
   if (m->copy_stream) cudaStreamSynchronize(m->copy_stream);
   if (m->work_done) cudaEventDestroy(m->work_done);
   for (int s = 0; s < 2; ++s) {

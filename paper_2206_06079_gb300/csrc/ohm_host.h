@@ -49,6 +49,11 @@ struct ohm_map {
   double stage_ms[OHM_STAGE_COUNT];
   long long stage_launches[OHM_STAGE_COUNT];
   ohm::HostStore* store;    // evicted regions in pinned host memory
+  // depth frames: (u - cx) / fx per column and (v - cy) / fy per row, for the
+  // last image size and intrinsics (pxy_key: width, height, fx, fy, cx, cy)
+  double* pxy;
+  long long pxy_cap;
+  double pxy_key[6];
   cudaEvent_t work_done;    // recorded behind the last work any entry point enqueued on the map
 };
 

@@ -1047,12 +1047,14 @@ __device__ __forceinline__ void tsdf_apply_one(const DeviceMap& m, long long t) 
   const long long sum = m.tsdf_sum[off];
   m.tsdf_cnt[off] = 0;
   m.tsdf_sum[off] = 0;
+  // in float (D and W are stored as floats; W and W + c are integers below
+  // 2^24, exact): the rounding of D is far below the layer's 1e-5 m
+  // tolerance, and the device's double division is slow
   const float2 dw = m.tsdf[off];
-  const double W = (double)dw.y, D = (double)dw.x;
-  const double S = (double)sum * (1.0 / 4294967296.0);
-  const double Wn = W + (double)c;
-  const double Dn = (W * D + S) / Wn;
-  m.tsdf[off] = make_float2((float)Dn, (float)(Wn < (double)m.wmax ? Wn : (double)m.wmax));
+  const float S = (float)sum * 2.3283064365386962890625e-10f;  // 2^-32
+  const float Wn = dw.y + (float)c;
+  const float Dn = (dw.y * dw.x + S) / Wn;
+  m.tsdf[off] = make_float2(Dn, fminf(Wn, m.wmax));
 }
 
 // Voxel-mean update of one voxel given samples by the call: per axis
