@@ -498,6 +498,21 @@ def tsdf_leg(dev, frames=16, warmup=3, n_query=20000):
     fwd_ms = e0.elapsed_time(e1) / frames
     visits = (gm.stats()["total_visits"] - v0) / frames
     gm.close()
+    # per-stage device times: the same frames on a fresh map, events around every kernel
+    gs = ohm.Map(**W.tsdf_params(device=dev.index))
+    for d, P in fr[:warmup]:
+        gs.integrate_depth(d, K, P, sync=False)
+    gs.sync()
+    gs.profile(ohm.STAGES)
+    for d, P in fr[warmup:]:
+        gs.integrate_depth(d, K, P, sync=False)
+    gs.sync()
+    stages = {}
+    for name in ohm.STAGES:
+        ms, nl = gs.profile_read(name)
+        if nl:
+            stages[name] = ms / nl
+    gs.close()
     rng = np.random.default_rng(5)
     q = torch.from_numpy(rng.uniform([-3, -3, 0], [3, 3, 3], size=(n_query, 3)).astype(np.float32)).to(dev)
     gq = torch.from_numpy(rng.normal(size=n_query).astype(np.float32)).to(dev)
@@ -517,7 +532,7 @@ def tsdf_leg(dev, frames=16, warmup=3, n_query=20000):
     return {"workload": "640x480 depth frames, 0.05 m voxels, tau 0.2 m, TSDF layer", "rays_per_s": w * h / (fwd_ms / 1e3),
             "ms_per_frame": fwd_ms, "voxel_updates_per_s": visits / (fwd_ms / 1e3),
             "forward_backward_ms_per_frame": fb_ms, "backward_ms_per_frame": fb_ms - fwd_ms,
-            "frames": frames, "warmup": warmup, "adjoint_query_voxels": n_query}
+            "stages_ms": stages, "frames": frames, "warmup": warmup, "adjoint_query_voxels": n_query}
 
 
 def ndt_adjoint_leg(dev, scans=8, warmup=3, n_query=20000):
