@@ -75,7 +75,7 @@ long long next_pow2(long long x) {
 void free_map(ohm_map* m) {
   if (!m) return;
   ohm::DeviceMap& d = m->d;
-  void* ptrs[] = {d.htab, d.region_count, d.region_coords, d.occ, d.counts, d.decay, d.vmean, d.vmean_acc, d.mean_list, d.ndt_slot, d.ndt_count,
+  void* ptrs[] = {d.htab, d.region_count, d.region_coords, d.occ, d.counts, d.decay, d.vmean, d.vmean_acc, d.mean_list, d.ndt_slot, d.ndt_count, d.ndt_pending,
                   d.ndt, d.tsdf, d.tsdf_cnt, d.tsdf_sum, d.grad, d.ndt_grad, d.status, d.calls, d.rays, d.decay_rays, d.trays, d.segs, d.touched,
                   d.stamp, d.born, d.ndt_born, d.free_slots, d.ndt_free, d.free_info, d.restore_keys,
                   m->stage_origins, m->stage_endpoints, m->stage_flags, m->hin_origins[0], m->hin_origins[1],
@@ -268,6 +268,7 @@ ohm_status ohm_map_create(const ohm_map_params* params, ohm_map** out) {
   if (p.layers & OHM_LAYER_NDT) {
     chk(alloc(&d.ndt, (long long)d.max_ndt * 10 * V, 0));
     chk(alloc(&d.ndt_free, d.max_ndt, 0));
+    chk(alloc(&d.ndt_pending, p.max_rays, 0));
   }
   if (p.layers & OHM_LAYER_TSDF) {
     chk(alloc(&d.tsdf, R * V, 0));

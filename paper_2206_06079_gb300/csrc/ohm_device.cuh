@@ -123,6 +123,7 @@ struct CallCounters {
   int32_t origin_ok;                // 1 if origin_q is valid
   int32_t pad2;
   unsigned long long atomics;       // log-odds CAS operations the miss walk issued (single-map calls)
+  unsigned long long ndt_pending;   // entries of DeviceMap::ndt_pending written by the current call
 };
 
 // Everything a kernel needs, passed by value.
@@ -144,6 +145,7 @@ struct DeviceMap {
   int32_t* ndt_slot;             // [max_regions], -1 = no NDT layer yet
   int32_t* ndt_count;
   int32_t max_ndt;
+  int32_t* ndt_pending;          // [max_rays] sample rays whose region prepare could not give an NDT block
   long long* ndt;                // [max_ndt][10][32768]
   float2* tsdf;                  // [max_regions][32768] (D, W)
   uint32_t* tsdf_cnt;            // [max_regions][32768] per-call scratch, zero between calls
@@ -246,12 +248,15 @@ __device__ __forceinline__ int32_t alloc_ndt_block(const DeviceMap& m) {
 
 // Insert a region if absent, and mark it used by the current call.  The
 // inserting thread takes a pool slot; other threads only learn that the key
-// exists (slots are read after this kernel).  A key whose region was evicted
+// exists (slots are read after this kernel).  Returns the region's slot where
+// this thread knows it (it inserted the key, or found it with its slot), else
+// -1 (another thread is inserting it right now, it is evicted, or the call
+// failed).  A key whose region was evicted
 // to host memory is queued for restoring and the call is stopped (it will be
 // repeated once the region is back).  The first probe may read a stale cached
 // entry: a key once written never changes within a call, and a stale "empty"
 // only sends us to the CAS below.
-__device__ inline void insert_region(const DeviceMap& m, int rx, int ry, int rz) {
+__device__ inline int32_t insert_region(const DeviceMap& m, int rx, int ry, int rz) {
   const long long key = pack_region(rx, ry, rz);
   const int32_t seq = m.calls->seq;
   uint32_t h = hash_key(key) & m.hmask;
@@ -273,18 +278,19 @@ __device__ inline void insert_region(const DeviceMap& m, int rx, int ry, int rz)
         } else {
           atomicOr(m.status, kStatusCapacity);
         }
-        return;
+        return s;
       }
       if (prev != key) {
         h = (h + 1) & m.hmask;
         continue;
       }
-      return;  // another thread inserted it just now; it stamps the slot
+      return -1;  // another thread inserted it just now; it stamps the slot
     }
     if (k == key) {
       const long long slot = e.y;
       if (slot >= 0) {
         m.stamp[slot] = seq;
+        return (int32_t)slot;
       } else if (slot == kSlotEvicted || slot == kSlotRestoring) {
         if (atomicCAS((unsigned long long*)&m.htab[h].y, (unsigned long long)kSlotEvicted,
                       (unsigned long long)kSlotRestoring) == (unsigned long long)kSlotEvicted) {
@@ -293,11 +299,12 @@ __device__ inline void insert_region(const DeviceMap& m, int rx, int ry, int rz)
         }
         atomicOr(m.status, kStatusRestore);
       }
-      return;
+      return -1;
     }
     h = (h + 1) & m.hmask;
   }
   atomicOr(m.status, kStatusProbe);
+  return -1;
 }
 
 // ---------------------------------------------------------------------------

@@ -5,9 +5,10 @@
 //   k_begin          snapshot the pool counters (the rollback point)
 //   k_prepare_occ    per ray: fixed-point quantisation, max-range truncation,
 //                    region walk with hash insertion (the paper does this on
-//                    the CPU, Sec. III-B; here it is a device pass), and the
-//                    segment table (Sec. III-B ray segments)
-//   k_ndt_alloc      per sample: give its region an NDT layer
+//                    the CPU, Sec. III-B; here it is a device pass), the
+//                    segment table (Sec. III-B ray segments), and the NDT
+//                    block of the sample's region
+//   k_ndt_alloc      sample rays prepare left: give their regions an NDT layer
 //   k_prepare_tsdf   per ray: TSDF band end points and their regions
 //   k_walk_fast      per segment: exact voxel walk, miss update per voxel
 //                    (k_walk_miss for maps with the decay layer)
@@ -24,7 +25,12 @@ namespace ohm {
 #define OHM_GRID_STRIDE(i, n) \
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += (long long)gridDim.x * blockDim.x)
 
-__global__ void k_begin(DeviceMap m, CallArgs args) { begin_call(m, args); }
+// Chained like the kernels after it: its launch overlaps the tail of the
+// previous call's last kernel, and its body waits for that kernel.
+__global__ void k_begin(DeviceMap m, CallArgs args) {
+  chain_enter();
+  if (blockIdx.x == 0 && threadIdx.x == 0) begin_call(m, args);
+}
 
 __global__ void __launch_bounds__(kBlock, OHM_PREPARE_MIN_BLOCKS) k_prepare_occ(DeviceMap m, CallArgs args) {
   chain_enter();
@@ -32,10 +38,17 @@ __global__ void __launch_bounds__(kBlock, OHM_PREPARE_MIN_BLOCKS) k_prepare_occ(
   prepare_occ_ray(m, args, i, i < args.n);
 }
 
-__global__ void __launch_bounds__(kBlock) k_ndt_alloc(DeviceMap m, long long n) {
+// Blocks of the NDT pass: it has only the rays prepare could not settle (a
+// few per scan), read from the device-side count.
+constexpr int kNdtPendingGrid = 64;
+
+// The sample rays whose region slot prepare did not learn (another thread
+// was inserting the region at the time): their regions get NDT blocks here.
+__global__ void __launch_bounds__(kBlock) k_ndt_alloc(DeviceMap m) {
   chain_enter();
   if (latched(m)) return;
-  OHM_GRID_STRIDE(i, n) ndt_alloc_ray(m, i);
+  const long long n = (long long)m.calls->ndt_pending;
+  OHM_GRID_STRIDE(k, n) ndt_alloc_ray(m, m.ndt_pending[k]);
 }
 
 template <bool kOcc, bool kCounts, bool kDecay>
@@ -274,10 +287,10 @@ cudaError_t launch_integrate(ohm_map* map, const CallArgs& args, cudaStream_t st
   const long long per_ray_blocks = blocks_for(n) > 0 ? blocks_for(n) : 1;
   const int ray_grid = (int)(per_ray_blocks < grid ? per_ray_blocks : grid);
   const unsigned prb = (unsigned)per_ray_blocks;
-  OHM_LAUNCH(OHM_STAGE_BEGIN, k_begin<<<1, 1, 0, stream>>>(m, args));
+  OHM_LAUNCH(OHM_STAGE_BEGIN, launch_chained(k_begin, 1, stream, m, args));
   if (occ_like) {
     OHM_LAUNCH(OHM_STAGE_PREPARE, launch_chained(k_prepare_occ, prb, stream, m, args));
-    if (ndt) OHM_LAUNCH(OHM_STAGE_NDT_ALLOC, launch_chained(k_ndt_alloc, ray_grid, stream, m, n));
+    if (ndt) OHM_LAUNCH(OHM_STAGE_NDT_ALLOC, launch_chained(k_ndt_alloc, kNdtPendingGrid, stream, m));
   }
   if (tsdf) OHM_LAUNCH(OHM_STAGE_PREPARE_TSDF, launch_chained(k_prepare_tsdf, prb, stream, m, args));
   const bool dec = (m.layers & kLayerDecay) != 0;
@@ -318,7 +331,8 @@ cudaError_t launch_integrate(ohm_map* map, const CallArgs& args, cudaStream_t st
     OHM_LAUNCH(OHM_STAGE_TSDF_WALK, launch_chained(k_tsdf_walk, ray_grid, stream, m, n));
     OHM_LAUNCH(OHM_STAGE_TSDF_APPLY, launch_chained(k_tsdf_apply, grid, stream, m));
   }
-  OHM_LAUNCH(OHM_STAGE_END, launch_chained(k_end, grid, stream, m));
+  // one block per SM: the body only runs (a grid-stride rollback) after a failure
+  OHM_LAUNCH(OHM_STAGE_END, launch_chained(k_end, (unsigned)map->num_sms, stream, m));
   return cudaGetLastError();
 }
 

@@ -123,10 +123,14 @@ __device__ __forceinline__ void load_ray(const CallArgs& a, long long i, float o
 // is the common case (the region exists): it is stamped as insert_region
 // would.  Every other case goes through insert_region.  A ray visits a
 // region once, so a batch holds distinct keys.
-__device__ __forceinline__ void insert_ray_regions(const DeviceMap& m, const long long a[3], const long long b[3]) {
+//
+// Returns the slot of the last region (the one holding the end point) where
+// this thread learnt it, else -1 (see insert_region).
+__device__ __forceinline__ int32_t insert_ray_regions(const DeviceMap& m, const long long a[3], const long long b[3]) {
   Walker w;
   walker_init(w, a, b, m.frac_bits + kRegionShift, 0, 0);
   const int32_t seq = m.calls->seq;
+  int32_t last = -1;
   bool more = true;
   while (more) {
     long long key[kRegionBatch];
@@ -157,6 +161,7 @@ __device__ __forceinline__ void insert_ray_regions(const DeviceMap& m, const lon
       if (j < (int)n) {
         if (e[j].x == key[j] && e[j].y >= 0) {
           m.stamp[e[j].y] = seq;
+          last = (int32_t)e[j].y;
         } else {
           const unsigned long long k = (unsigned long long)key[j];
           const int32_t mask = (1 << 21) - 1;
@@ -164,9 +169,25 @@ __device__ __forceinline__ void insert_ray_regions(const DeviceMap& m, const lon
           const int rx = (int32_t)((uint32_t)((k >> 42) & mask) << 11) >> 11;
           const int ry = (int32_t)((uint32_t)((k >> 21) & mask) << 11) >> 11;
           const int rz = (int32_t)((uint32_t)(k & mask) << 11) >> 11;
-          insert_region(m, rx, ry, rz);
+          last = insert_region(m, rx, ry, rz);
         }
       }
+    }
+  }
+  return last;
+}
+
+// Give region `slot` an NDT block if it has none: one thread wins the claim
+// (-1 -> -2) and takes a block from the pool.
+__device__ __forceinline__ void ndt_claim(const DeviceMap& m, int32_t slot) {
+  if (*(volatile int32_t*)&m.ndt_slot[slot] != -1) return;
+  if (atomicCAS(&m.ndt_slot[slot], -1, -2) == -1) {
+    const int32_t id = alloc_ndt_block(m);
+    if (id >= 0) {
+      m.ndt_born[slot] = m.calls->seq;
+      m.ndt_slot[slot] = id;
+    } else {
+      atomicOr(m.status, kStatusCapacity);
     }
   }
 }
@@ -264,6 +285,7 @@ __device__ __forceinline__ void begin_call(const DeviceMap& m, const CallArgs& a
   m.calls->mean_touched = 0;
   m.calls->restores = 0;
   m.calls->atomics = 0;
+  m.calls->ndt_pending = 0;
   m.calls->rays = (unsigned long long)n;
   // a shared sensor origin is quantised once for the whole call
   bool ok = false;
@@ -330,6 +352,7 @@ __device__ __forceinline__ void prepare_occ_ray(const DeviceMap& m, const CallAr
   active = active && !latched(m);
   const int F = m.frac_bits;
   unsigned int nseg = 0, nvisit = 0;
+  bool ndt_listed = false;
   RayRec r;
   r.flags = 0;
   r.nseg = 0;
@@ -390,9 +413,29 @@ __device__ __forceinline__ void prepare_occ_ray(const DeviceMap& m, const CallAr
         m.decay_rays[i] = dr;
       }
       nvisit = (unsigned int)(1 + l1);
-      insert_ray_regions(m, qo, qe);
+      const int32_t last = insert_ray_regions(m, qo, qe);
+      // NDT-OM: the sample's region (the ray's last) gets its NDT block here
+      // when this thread learnt the region's slot; otherwise the ray is
+      // listed for the NDT pass after this kernel
+      if (sample && (m.layers & kLayerNdt)) {
+        if (last >= 0)
+          ndt_claim(m, last);
+        else
+          ndt_listed = true;
+      }
     }
     m.rays[i] = r;
+  }
+  if (m.layers & kLayerNdt) {
+    const unsigned full = 0xffffffffu;
+    const unsigned listed = __ballot_sync(full, ndt_listed);
+    if (listed) {
+      const int lane = threadIdx.x & 31;
+      unsigned long long base = 0;
+      if (lane == 0) base = atomicAdd(&m.calls->ndt_pending, (unsigned long long)__popc(listed));
+      base = __shfl_sync(full, base, 0);
+      if (ndt_listed) m.ndt_pending[base + __popc(listed & ((1u << lane) - 1u))] = (int32_t)i;
+    }
   }
   write_segments(m, i, nseg);
   warp_add(&m.calls->visits, &m.calls->total_visits, nvisit);
@@ -410,16 +453,7 @@ __device__ __forceinline__ void ndt_alloc_ray(const DeviceMap& m, long long i) {
     atomicOr(m.status, kStatusMissing);
     return;
   }
-  if (*(volatile int32_t*)&m.ndt_slot[slot] != -1) return;
-  if (atomicCAS(&m.ndt_slot[slot], -1, -2) == -1) {
-    const int32_t id = alloc_ndt_block(m);
-    if (id >= 0) {
-      m.ndt_born[slot] = m.calls->seq;
-      m.ndt_slot[slot] = id;
-    } else {
-      atomicOr(m.status, kStatusCapacity);
-    }
-  }
+  ndt_claim(m, slot);
 }
 
 // Miss phase (Sec. III-C phase one) for one segment: every voxel a ray passes
