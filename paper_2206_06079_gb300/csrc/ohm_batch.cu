@@ -46,7 +46,7 @@ struct BatchShared {
   int32_t n_maps;
 };
 
-enum PrefixKind { kRaysPadded, kRays, kSegments, kTouched, kMeanTouched };
+enum PrefixKind { kRaysPadded, kRays, kSegments, kTouched, kMeanTouched, kNdtPending };
 
 // Load the descriptors and build the prefix table of the requested kind
 // (segments: of the maps whose walk is `variant` only, unless it is kAnyWalk).
@@ -74,6 +74,8 @@ __device__ void batch_stage(BatchShared& sh, const BatchDesc* desc, const BatchS
         c = live && (variant == kAnyWalk || walk_variant(m.layers, m.miss, m.ndt_clear) == variant)
                 ? (long long)m.calls->segments
                 : 0;
+      else if (kind == kNdtPending)
+        c = live && (m.layers & kLayerNdt) ? (long long)m.calls->ndt_pending : 0;
       else if (kind == kMeanTouched)
         c = (m.layers & kLayerMean) ? mean_touched_count(m) : 0;  // failed maps too: their sums are cleared
       else
@@ -104,9 +106,12 @@ __device__ __forceinline__ CallArgs batch_args(const BatchStep* step, int i) {
 #define OHM_BATCH_STRIDE(g, total) \
   for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < (total); g += (long long)gridDim.x * blockDim.x)
 
+// Chained like the stage kernels after it (its launch overlaps the tail of the
+// previous step's last kernel).
 __global__ void k_batch_begin(const BatchDesc* desc, const BatchStep* step) {
+  chain_enter();
   const int i = threadIdx.x;
-  if (i < desc->n_maps) begin_call(desc->maps[i], batch_args(step, i));
+  if (blockIdx.x == 0 && i < desc->n_maps) begin_call(desc->maps[i], batch_args(step, i));
 }
 
 __global__ void __launch_bounds__(kBlock, OHM_PREPARE_MIN_BLOCKS) k_batch_prepare(const BatchDesc* desc, const BatchStep* step, int tsdf) {
@@ -128,15 +133,17 @@ __global__ void __launch_bounds__(kBlock, OHM_PREPARE_MIN_BLOCKS) k_batch_prepar
   }
 }
 
+// The sample rays each map's prepare listed (their region was being inserted
+// by another thread): their regions get NDT blocks here.
 __global__ void __launch_bounds__(kBlock) k_batch_ndt_alloc(const BatchDesc* desc, const BatchStep* step) {
   chain_enter();
   __shared__ BatchShared sh;
-  batch_stage(sh, desc, step, kRays);
+  batch_stage(sh, desc, step, kNdtPending);
   const long long total = sh.pref[sh.n_maps];
   OHM_BATCH_STRIDE(g, total) {
     const int mi = batch_find(sh, g);
     const DeviceMap& m = sh.maps[mi];
-    if (m.layers & kLayerNdt) ndt_alloc_ray(m, g - sh.pref[mi]);
+    ndt_alloc_ray(m, m.ndt_pending[g - sh.pref[mi]]);
   }
 }
 
@@ -310,13 +317,13 @@ cudaError_t enqueue_step(ohm_batch* b, cudaStream_t s, int* count) {
   using namespace ohm;
   const int grid = b->num_sms * b->walk_blocks_per_sm;
   const int ray_grid = b->num_sms * 4;
-  k_batch_begin<<<1, kMaxBatchMaps, 0, s>>>(b->d_desc, b->d_step);
+  launch_chained(k_batch_begin, 1, s, b->d_desc, b->d_step);
   int n = 1;
   if (b->any_occ || b->any_ndt || b->any_mean) {
     launch_chained(k_batch_prepare, ray_grid, s, b->d_desc, b->d_step, 0);
     ++n;
     if (b->any_ndt) {
-      launch_chained(k_batch_ndt_alloc, ray_grid, s, b->d_desc, b->d_step);
+      launch_chained(k_batch_ndt_alloc, (unsigned)b->num_sms, s, b->d_desc, b->d_step);
       ++n;
     }
   }
