@@ -482,7 +482,6 @@ __device__ __forceinline__ unsigned long long decay_position(long long dist, int
 template <bool kOcc, bool kCounts, bool kDecay>
 __device__ __forceinline__ void walk_segment(const DeviceMap& m, long long si, unsigned int& cas) {
   const int F = m.frac_bits;
-  const float miss = m.miss;
   const int2 sg = m.segs[si];
   const RayRec r = m.rays[sg.x];
   const int M = (r.flags >> kRayAxisShift) & 3;
@@ -724,6 +723,33 @@ __device__ __forceinline__ void walk_segment_fast(const DeviceMap& m, int2 sg, u
 #pragma unroll
       for (int j = 0; j < kFastBatchOf<kPipe>; ++j)
         if ((valid >> j) & 1u) miss_cas(m, occ + off[j], old[j], ops);
+      return;
+    }
+    if constexpr (!kPipe) {
+      // Plain loop: an unknown voxel (NaN) is first set to the prior 0 by a
+      // compare-and-swap whose result is not needed (one that loses finds a
+      // value another thread set), then takes its miss as one more add of
+      // delta, like a known voxel above l_min.  All of a call's misses of
+      // the voxel are then adds of delta to 0, in any order: the values 0,
+      // fl(0 + delta), ... of the clamped sequence that starts from the
+      // prior (the clamp on read as above).  Same-address atomics of one
+      // thread stay in order, so a thread's add never lands before its own
+      // compare-and-swap.  Nothing here waits for a result, which the plain
+      // loop (no second batch in flight) cannot hide; the pipelined loop
+      // hides that wait and does better with one atomic per unknown voxel.
+#pragma unroll
+      for (int j = 0; j < kFastBatchOf<kPipe>; ++j) {
+        if (!((valid >> j) & 1u)) continue;
+        const float l = __uint_as_float(old[j]);
+        if (l != l) {
+          atomicCAS(occ + off[j], old[j], 0u);
+          ++ops;
+        }
+        if (!(l <= m.l_min)) {
+          atomicAdd(reinterpret_cast<float*>(occ + off[j]), m.miss);
+          ++ops;
+        }
+      }
       return;
     }
     // adds go out at once; the compare-and-swaps that set unknown voxels
