@@ -65,6 +65,12 @@ __global__ void __launch_bounds__(kBlock, OHM_WALK_MIN_BLOCKS) k_walk_miss(Devic
 
 // The miss walk of maps without the decay layer (filtered walk, see
 // walk_segment_fast).
+// OHM_SINGLE_PIPE: the single-map walk runs the pipelined loop (the plain
+// loop of the multi-map batch, with its unchecked CAS initialisation, was
+// slower on tunnel scans at 4 and 5 blocks per SM).
+#ifndef OHM_SINGLE_PIPE
+#define OHM_SINGLE_PIPE true
+#endif
 template <bool kOcc, bool kCounts, bool kCas>
 __global__ void __launch_bounds__(kBlock, OHM_FAST_MIN_BLOCKS) k_walk_fast(DeviceMap m) {
   chain_enter();
@@ -77,7 +83,7 @@ __global__ void __launch_bounds__(kBlock, OHM_FAST_MIN_BLOCKS) k_walk_fast(Devic
   for (; si < nseg; si += stride) {
     // the next segment's table entry is loaded while this one walks
     const int2 next = si + stride < nseg ? m.segs[si + stride] : make_int2(-1, 0);
-    walk_segment_fast<kOcc, kCounts, kCas>(m, sg, ops, next.x >= 0 ? m.rays + next.x : nullptr);
+    walk_segment_fast<kOcc, kCounts, kCas, OHM_SINGLE_PIPE>(m, sg, ops, next.x >= 0 ? m.rays + next.x : nullptr);
     sg = next;
   }
   // every thread gets here: one atomic per warp for the call's atomic count
