@@ -375,7 +375,7 @@ def run_ours(args):
         extras["served"] = served_leg(dev, duration=8.0, pool_regions=1150)
         # offered load far above what one GPU serves: rays/s over the wall
         # time until the backlog is drained is the sustained maximum
-        extras["served_saturation"] = served_leg(dev, duration=3.0, rate_scale=24.0, pool_regions=1600)
+        extras["served_saturation"] = served_leg(dev, duration=3.0, rate_scale=40.0, pool_regions=1600)
 
     if rank == 0:
         clocks = ClockSampler.summarise(rows)

@@ -298,8 +298,9 @@ ohm_status ohm_probe_rate(int32_t device, int32_t kind, int64_t units, int64_t o
 /* Kernel stages of an integrate call, for per-stage GPU timing. */
 typedef enum {
   OHM_STAGE_BEGIN = 0,        /* rollback snapshot */
-  OHM_STAGE_PREPARE = 1,      /* quantise, truncate, region allocation, segment table */
-  OHM_STAGE_NDT_ALLOC = 2,    /* NDT layer allocation for regions receiving samples */
+  OHM_STAGE_PREPARE = 1,      /* quantise, truncate, region allocation, segment table, NDT
+                                 layer of each sample's region where the slot is known */
+  OHM_STAGE_NDT_ALLOC = 2,    /* NDT layer allocation for the sample regions prepare left */
   OHM_STAGE_PREPARE_TSDF = 3, /* TSDF band end points and their regions */
   OHM_STAGE_WALK = 4,         /* voxel walk, miss updates (Sec. III-C phase one) */
   OHM_STAGE_HITS = 5,         /* sample updates and NDT moments (phase two) */

@@ -108,7 +108,8 @@ __global__ void __launch_bounds__(kBlock) k_mean_apply(DeviceMap m) {
   OHM_GRID_STRIDE(t, nt) mean_apply_one(m, t, apply);
 }
 
-__global__ void __launch_bounds__(kBlock) k_prepare_tsdf(DeviceMap m, CallArgs args) {
+// Compiled for 4 blocks per SM (64 registers; 78 unbounded, which fits 3).
+__global__ void __launch_bounds__(kBlock, 4) k_prepare_tsdf(DeviceMap m, CallArgs args) {
   chain_enter();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   prepare_tsdf_ray(m, args, i, i < args.n);
