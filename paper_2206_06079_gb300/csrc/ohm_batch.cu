@@ -114,7 +114,10 @@ __global__ void k_batch_begin(const BatchDesc* desc, const BatchStep* step) {
   if (blockIdx.x == 0 && i < desc->n_maps) begin_call(desc->maps[i], batch_args(step, i));
 }
 
-__global__ void __launch_bounds__(kBlock, OHM_PREPARE_MIN_BLOCKS) k_batch_prepare(const BatchDesc* desc, const BatchStep* step, int tsdf) {
+// One instantiation per pass (occupancy-like layers, or the TSDF band), so
+// that each kernel holds only its own per-ray code.
+template <bool kTsdf>
+__global__ void __launch_bounds__(kBlock, OHM_PREPARE_MIN_BLOCKS) k_batch_prepare(const BatchDesc* desc, const BatchStep* step) {
   chain_enter();
   __shared__ BatchShared sh;
   batch_stage(sh, desc, step, kRaysPadded);
@@ -125,10 +128,10 @@ __global__ void __launch_bounds__(kBlock, OHM_PREPARE_MIN_BLOCKS) k_batch_prepar
     const long long i = g - sh.pref[mi];
     const CallArgs a = batch_args(step, mi);
     const bool active = i < a.n;
-    if (tsdf) {
+    if constexpr (kTsdf) {
       if (m.layers & kLayerTsdf) prepare_tsdf_ray(m, a, i, active);
-    } else if (m.layers & (kLayerOcc | kLayerCounts | kLayerNdt | kLayerDecay | kLayerMean)) {
-      prepare_occ_ray(m, a, i, active);
+    } else {
+      if (m.layers & (kLayerOcc | kLayerCounts | kLayerNdt | kLayerDecay | kLayerMean)) prepare_occ_ray(m, a, i, active);
     }
   }
 }
@@ -320,7 +323,7 @@ cudaError_t enqueue_step(ohm_batch* b, cudaStream_t s, int* count) {
   launch_chained(k_batch_begin, 1, s, b->d_desc, b->d_step);
   int n = 1;
   if (b->any_occ || b->any_ndt || b->any_mean) {
-    launch_chained(k_batch_prepare, ray_grid, s, b->d_desc, b->d_step, 0);
+    launch_chained(k_batch_prepare<false>, ray_grid, s, b->d_desc, b->d_step);
     ++n;
     if (b->any_ndt) {
       launch_chained(k_batch_ndt_alloc, (unsigned)b->num_sms, s, b->d_desc, b->d_step);
@@ -328,7 +331,7 @@ cudaError_t enqueue_step(ohm_batch* b, cudaStream_t s, int* count) {
     }
   }
   if (b->any_tsdf) {
-    launch_chained(k_batch_prepare, ray_grid, s, b->d_desc, b->d_step, 1);
+    launch_chained(k_batch_prepare<true>, ray_grid, s, b->d_desc, b->d_step);
     ++n;
   }
   // oversubscribed grid-stride launches, like the single-map walk
