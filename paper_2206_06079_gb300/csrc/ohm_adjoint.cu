@@ -138,17 +138,22 @@ __global__ void __launch_bounds__(kBlock) k_tsdf_backward(DeviceMap m, DepthFram
       for (int k = 0; k < 3; ++k) o[k] = __double2float_rn(f.t[k]);
       long long qo[3], qe[3];
       ok = ok && quantise_ray(m, o, e, qo, qe);
-      double d[3], len = 0.0;
+      // the band of the forward pass, recomputed the same way
+      long long a[3], b[3];
+      float u[3], lenf = 0.f;
       if (ok) {
-        len = ray_length(qo, qe, d);
-        ok = len > m.rmin_q && len <= m.rmax_q && in_extent(qo, F) && in_extent(qe, F);
+        bool in_range = false;
+        if (!tsdf_band_ff(qo, qe, m.band, &in_range, a, b, u, &lenf)) {
+          double d[3];
+          const double len = ray_length(qo, qe, d);
+          in_range = len > m.rmin_q && len <= m.rmax_q;
+          if (in_range && in_extent(qo, F) && in_extent(qe, F)) tsdf_band(qo, d, len, m.tau_q, a, b, u);
+          lenf = (float)len;
+        }
+        ok = in_range && in_extent(qo, F) && in_extent(qe, F);
       }
       if (ok) {
-        // the band walk of the forward pass, recomputed
-        long long a[3], b[3];
-        float u[3];
-        tsdf_band(qo, d, len, m.tau_q, a, b, u);
-        const float dm = (float)(len * m.voxel_size / (double)U);
+        const float dm = lenf * to_m;  // ray length in metres (chain rule only)
         Walker w;
         walker_init(w, a, b, F, 0, 0);
         int32_t slot = region_slot_of(m, w.vx, w.vy, w.vz);

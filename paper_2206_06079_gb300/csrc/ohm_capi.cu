@@ -312,6 +312,9 @@ ohm_status ohm_map_create(const ohm_map_params* params, ohm_map** out) {
   }
   d.rmin_q = p.min_range * scale;
   d.tau_q = p.tsdf_trunc * scale;
+  d.band.tau = ohm::ff_of_double(d.tau_q);
+  d.band.rmin = ohm::ff_of_double(d.rmin_q);
+  d.band.rmax = ohm::ff_of_double(d.rmax_q);
   d.voxel_size = p.voxel_size;
   d.frac_bits = p.frac_bits;
   d.layers = p.layers;

@@ -106,6 +106,17 @@ struct __align__(16) TsdfRec {
 };
 
 // Per-call counters in device memory.
+// A float-float value hi + lo with |lo| <= ulp(hi) / 2 (the arithmetic is
+// with the TSDF band below).
+struct FF {
+  float hi, lo;
+};
+
+// The TSDF band's constants as float-float (tsdf_band_ff).
+struct BandConsts {
+  FF tau, rmin, rmax;  // fixed-point units
+};
+
 struct CallCounters {
   unsigned long long segments;
   unsigned long long visits;
@@ -175,6 +186,7 @@ struct DeviceMap {
   double origin[3];
   double scale;                  // 2^F / voxel_size
   double rmax_q, rmin_q, tau_q;  // ranges in fixed-point units
+  BandConsts band;               // tau_q, rmin_q, rmax_q as float-float
   // a ray with |b - a|^2 <= rmax_in2 (fixed-point units^2) is certainly
   // within max_range
   unsigned long long rmax_in2;
@@ -947,6 +959,214 @@ OHM_UNROLL
     b[k] = qo[k] + d2ll_rn(dmul_rn(d[k], g1));
     u[k] = (float)ddiv_rn(d[k], len);
   }
+}
+
+// ---------------------------------------------------------------------------
+// Float-float (double-word) arithmetic: a value is an unevaluated sum hi + lo
+// of two floats with |lo| <= ulp(hi) / 2.  The error-free transformations
+// are Knuth's TwoSum, Dekker's FastTwoSum and the product's exact error from
+// one fused multiply-add (Dekker 1971; Ogita, Rump, Oishi 2005); the
+// compound operations follow the double-word algorithms whose relative error
+// bounds Joldes, Muller and Popescu (2017) prove: addition <= 3 u^2,
+// product <= 5 u^2, product by a float <= 2 u^2 (u = 2^-24).  Every step
+// rounds once, written with explicit-rounding intrinsics so that no
+// contraction changes it.
+// ---------------------------------------------------------------------------
+
+__host__ __device__ __forceinline__ float fadd_rn(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fadd_rn(a, b);
+#else
+  return a + b;
+#endif
+}
+__host__ __device__ __forceinline__ float fsub_rn(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fsub_rn(a, b);
+#else
+  return a - b;
+#endif
+}
+__host__ __device__ __forceinline__ float fdiv_rn(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fdiv_rn(a, b);
+#else
+  return a / b;
+#endif
+}
+__host__ __device__ __forceinline__ float fsqrt_rn(float a) {
+#ifdef __CUDA_ARCH__
+  return __fsqrt_rn(a);
+#else
+  return std::sqrt(a);
+#endif
+}
+
+// s + e = a + b exactly.
+__host__ __device__ __forceinline__ FF two_sum(float a, float b) {
+  const float s = fadd_rn(a, b);
+  const float bb = fsub_rn(s, a);
+  const float e = fadd_rn(fsub_rn(a, fsub_rn(s, bb)), fsub_rn(b, bb));
+  return {s, e};
+}
+// s + e = a + b exactly, for |a| >= |b| (or a = 0).
+__host__ __device__ __forceinline__ FF fast_two_sum(float a, float b) {
+  const float s = fadd_rn(a, b);
+  return {s, fsub_rn(b, fsub_rn(s, a))};
+}
+// p + e = a b exactly.
+__host__ __device__ __forceinline__ FF two_prod(float a, float b) {
+  const float p = fmul_rn(a, b);
+  return {p, fma_rn(a, b, -p)};
+}
+__host__ __device__ __forceinline__ FF ff_add(FF x, FF y) {
+  const FF s = two_sum(x.hi, y.hi), t = two_sum(x.lo, y.lo);
+  const FF v = fast_two_sum(s.hi, fadd_rn(s.lo, t.hi));
+  return fast_two_sum(v.hi, fadd_rn(v.lo, t.lo));
+}
+__host__ __device__ __forceinline__ FF ff_neg(FF x) { return {-x.hi, -x.lo}; }
+__host__ __device__ __forceinline__ FF ff_mul(FF x, FF y) {
+  const FF c = two_prod(x.hi, y.hi);
+  const float t = fma_rn(x.lo, y.hi, fma_rn(x.hi, y.lo, fmul_rn(x.lo, y.lo)));
+  return fast_two_sum(c.hi, fadd_rn(c.lo, t));
+}
+__host__ __device__ __forceinline__ FF ff_mul_f(FF x, float y) {
+  const FF c = two_prod(x.hi, y);
+  return fast_two_sum(c.hi, fma_rn(x.lo, y, c.lo));
+}
+// sqrt(x) for x > 0: the float root r and one Newton correction
+// (x - r^2) / (2 r), with x - r^2 formed from the exact square of r.
+// Relative error below 4 u^2 for x exact (the truncated Newton term is
+// under u^2 / 2, the residual's two roundings and the quotient's add 3 u^2).
+__host__ __device__ __forceinline__ FF ff_sqrt(FF x) {
+  const float r = fsqrt_rn(x.hi);
+  const FF p = two_prod(r, r);
+  const float res = fadd_rn(fsub_rn(fsub_rn(x.hi, p.hi), p.lo), x.lo);  // x.hi - p.hi exact (Sterbenz)
+  return fast_two_sum(r, fdiv_rn(res, fadd_rn(r, r)));
+}
+// 1 / x for x > 0: the float reciprocal r and one Newton correction r (1 - x r).
+// Relative error below 6 u^2 (the truncated Newton term under u^2, the
+// residual's roundings and x.lo r about 4 u^2, the correction's product u^2).
+__host__ __device__ __forceinline__ FF ff_rcp(FF x) {
+  const float r = fdiv_rn(1.0f, x.hi);
+  const FF p = two_prod(x.hi, r);
+  const float e = fsub_rn(fsub_rn(fsub_rn(1.0f, p.hi), p.lo), fmul_rn(x.lo, r));  // 1 - p.hi exact (Sterbenz)
+  return fast_two_sum(r, fmul_rn(r, e));
+}
+// A double as float-float (hi = float(v), lo = float(v - hi)): within
+// 2^-48 |v| of v; an infinite or huge v keeps lo = 0.
+__host__ __device__ __forceinline__ FF ff_of_double(double v) {
+  const float hi = (float)v;
+  if (!(hi - hi == 0.0f)) return {hi, 0.0f};
+  return {hi, (float)(v - (double)hi)};
+}
+
+// rint(x) of a float-float x with |x| < 2^25, as an integer, when every value
+// within e of x rounds to it (no half-integer in [x - e, x + e]); else false.
+__host__ __device__ __forceinline__ bool ff_rint(FF x, float e, long long* out) {
+  const float n = rintf(x.hi);                         // an integer within 1/2 of x.hi
+  const float f = fadd_rn(fsub_rn(x.hi, n), x.lo);     // x - n, one rounding (|f| <= 1.5)
+  const float m = e + 1e-6f;                           // covers the rounding of f
+  long long k = (long long)n;
+  if (fabsf(f) < 0.5f - m) {
+  } else if (f > 0.5f + m && f < 1.5f - m) {
+    k += 1;
+  } else if (f < -0.5f - m && f > -1.5f + m) {
+    k -= 1;
+  } else {
+    return false;
+  }
+  *out = k;
+  return true;
+}
+
+// float(q) of a float-float q when every value within e of q rounds to the
+// same float (no midpoint between adjacent floats in [q - e, q + e]); else false.
+__host__ __device__ __forceinline__ bool ff_to_float(FF q, float e, float* out) {
+  if (q.hi == 0.0f) {
+    if (q.lo != 0.0f || e > 0.0f) return false;
+    *out = 0.0f;
+    return true;
+  }
+  // the nearest midpoints lie half a gap to either neighbour of |hi|; the
+  // gaps are exact float differences of adjacent floats
+  const float a = fabsf(q.hi);
+  uint32_t ab;
+  std::memcpy(&ab, &a, sizeof(ab));
+  const uint32_t up_bits = ab + 1u, down_bits = ab - 1u;
+  float up, down;
+  std::memcpy(&up, &up_bits, sizeof(up));
+  std::memcpy(&down, &down_bits, sizeof(down));
+  const float half_gap = 0.5f * fminf(up - a, a - down);
+  if (!(fabsf(q.lo) + e < half_gap)) return false;
+  *out = q.hi;
+  return true;
+}
+// ---------------------------------------------------------------------------
+// The TSDF band of tsdf_band (with its range test len > rmin, len <= rmax on
+// the double length of ray_length) settled in float-float arithmetic, for
+// rays with |d_k| < 2^24 (every d_k exact as a float).  The double
+// evaluation's roundings stay below u^2 / 16 of each quantity (u = 2^-24);
+// the float-float one's, from the bounds above (relative errors add, to
+// first order): S = sum d_k^2 to 6.1 u^2 (all terms positive), len =
+// sqrt(S) to 7.1 u^2, 1 / len to 13.1 u^2, t = len -+ tau (tau within u^2
+// of the double) to 3 u^2 |t| + 8.1 u^2 (len + tau), g = t rho to that over
+// len plus 18.1 u^2 g, and the products by d_k to 2 u^2.  With
+// (len + tau) / len = g1, the end points d_k g differ from the double's by
+// less than 32 u^2 |d_k| (1 + g0 + g1), d_k / len by less than 16 u^2
+// |d_k / len|, len by less than 7.2 u^2 len, t0 by less than 12 u^2
+// (len + tau).  Each rounding decision (range test, t0 > 0, rint, float) is
+// taken only when the float-float value is farther than 2^-40 = 256 u^2 of
+// that scale from where the decision changes; otherwise the function returns
+// false and the caller evaluates in double.  The GB300's FP64 pipe runs a
+// warp instruction in 64 cycles of a scheduler, the FP32 pipe in one or two.
+// ---------------------------------------------------------------------------
+
+// len_out (optional): the ray length's high part.
+__host__ __device__ inline bool tsdf_band_ff(const long long qo[3], const long long qe[3], const BandConsts& c,
+                                             bool* in_range, long long a[3], long long b[3], float u[3],
+                                             float* len_out = nullptr) {
+  constexpr float kMargin = 9.094947e-13f;  // 2^-40
+  float d[3];
+OHM_UNROLL
+  for (int k = 0; k < 3; ++k) {
+    const long long dk = qe[k] - qo[k];
+    if (dk <= -(1LL << 24) || dk >= (1LL << 24)) return false;
+    d[k] = (float)dk;
+  }
+  const FF S = ff_add(ff_add(two_prod(d[0], d[0]), two_prod(d[1], d[1])), two_prod(d[2], d[2]));
+  if (!(S.hi > 0.0f)) return false;
+  const FF len = ff_sqrt(S);
+  if (len_out) *len_out = len.hi;
+  // range test
+  const float tol_len = kMargin * len.hi;
+  const FF over_min = ff_add(len, ff_neg(c.rmin)), over_max = ff_add(len, ff_neg(c.rmax));
+  if (!(fabsf(over_min.hi) > tol_len + kMargin * fabsf(c.rmin.hi))) return false;
+  if (!(fabsf(over_max.hi) > tol_len + kMargin * fabsf(c.rmax.hi))) return false;
+  *in_range = over_min.hi > 0.0f && over_max.hi < 0.0f;
+  if (!*in_range) return true;
+  // band ends as fractions of the ray: t0 = max(len - tau, 0), t1 = len + tau
+  const float tol_t = kMargin * (len.hi + c.tau.hi);
+  const FF t0 = ff_add(len, ff_neg(c.tau));
+  if (!(fabsf(t0.hi) > tol_t)) return false;
+  const bool t0_pos = t0.hi > 0.0f;
+  const FF t1 = ff_add(len, c.tau);
+  const FF rho = ff_rcp(len);
+  const FF g0 = t0_pos ? ff_mul(t0, rho) : FF{0.0f, 0.0f};
+  const FF g1 = ff_mul(t1, rho);
+  const float gsum = 1.0f + g0.hi + g1.hi;
+OHM_UNROLL
+  for (int k = 0; k < 3; ++k) {
+    const float tol_p = kMargin * fabsf(d[k]) * gsum;
+    long long pa, pb;
+    if (!ff_rint(ff_mul_f(g0, d[k]), tol_p, &pa)) return false;
+    if (!ff_rint(ff_mul_f(g1, d[k]), tol_p, &pb)) return false;
+    const FF q = ff_mul_f(rho, d[k]);
+    if (!ff_to_float(q, kMargin * fabsf(q.hi), &u[k])) return false;
+    a[k] = qo[k] + pa;
+    b[k] = qo[k] + pb;
+  }
+  return true;
 }
 
 __device__ __forceinline__ void warp_add(unsigned long long* counter, unsigned long long* counter2, unsigned int value) {

@@ -941,13 +941,19 @@ __device__ __forceinline__ void prepare_tsdf_ray(const DeviceMap& m, const CallA
     load_ray(args, i, o, e, &flag);
     long long qo[3], qe[3];
     bool ok = quantise_call_ray(m, args, o, e, qo, qe) && (flag & kFlagNoReturn) == 0;
-    double d[3], len = 0.0;
     if (ok) {
-      len = ray_length(qo, qe, d);
-      ok = len > m.rmin_q && len <= m.rmax_q && in_extent(qo, F) && in_extent(qe, F);
+      // the range test and the band in float-float; in double where that
+      // cannot settle them (tsdf_band_ff)
+      bool in_range = false;
+      if (!tsdf_band_ff(qo, qe, m.band, &in_range, r.a, r.b, r.u)) {
+        double d[3];
+        const double len = ray_length(qo, qe, d);
+        in_range = len > m.rmin_q && len <= m.rmax_q;
+        if (in_range && in_extent(qo, F) && in_extent(qe, F)) tsdf_band(qo, d, len, m.tau_q, r.a, r.b, r.u);
+      }
+      ok = in_range && in_extent(qo, F) && in_extent(qe, F);
     }
     if (ok) {
-      tsdf_band(qo, d, len, m.tau_q, r.a, r.b, r.u);
 #pragma unroll
       for (int k = 0; k < 3; ++k) r.e[k] = qe[k];
       r.flags = kRayValid;

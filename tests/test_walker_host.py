@@ -125,3 +125,23 @@ def test_tsdf_band_reciprocal_equals_divisions(tmp_path):
     tok = out.stdout.split()
     cases, fallback = int(tok[1]), int(tok[3])
     assert cases > 600000 and 0 < fallback < cases
+
+
+def test_tsdf_band_float_float_equals_double(tmp_path):
+    """The TSDF range test and band settled in float-float arithmetic
+    (tsdf_band_ff, compiled for the host) equal the double evaluation on every
+    case they settle: random rays (of which they must settle nearly all), rays
+    built to land an end point on a half-integer, lengths at the range limits
+    and at tau, where they must decline.  Float ops are compiled without
+    contraction, as the device code writes every rounding explicitly."""
+    exe = str(tmp_path / "band_ff_check")
+    subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-std=c++17", "-O2", "-Xcompiler",
+                    "-ffp-contract=off", "-x", "cu", os.path.join(HERE, "host", "band_ff_check.cu"), "-o", exe],
+                   check=True, capture_output=True)
+    out = subprocess.run([exe], capture_output=True, text=True)
+    assert out.returncode == 0, (out.returncode, out.stderr[-500:])
+    tok = out.stdout.split()
+    cases, settled, rnd, rnd_settled = int(tok[1]), int(tok[3]), int(tok[5]), int(tok[7])
+    assert cases > 1500000 and rnd > 590000
+    assert rnd_settled > 0.999 * rnd      # the float-float path decides nearly every ordinary ray
+    assert settled < 0.5 * cases          # and declines the built near-ties
