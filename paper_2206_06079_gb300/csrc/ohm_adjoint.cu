@@ -185,8 +185,9 @@ __global__ void __launch_bounds__(kBlock) k_tsdf_backward(DeviceMap m, DepthFram
         }
         // The chain rule from here on is plain float arithmetic (its inputs
         // are floats; the gradients are checked to 1e-3 relative), summed
-        // over pixels in double.  The band above is recomputed in double
-        // exactly as the forward pass, since it decides the voxel set.
+        // over pixels in double.  The band above is recomputed exactly as
+        // the forward pass forms it (the same float-float settlement, else
+        // the same double evaluation), since it decides the voxel set.
         const float rdm = 1.0f / dm;
         float ge[3], go[3];
 #pragma unroll
